@@ -1,0 +1,281 @@
+"""FP64 cone projections and membership tests (oracle; test infrastructure).
+
+The cone of the primal slack is ``K = {0}^z x R+^l x SOC... x PSD... x Kexp...``
+(Sec. 2, Sec. 6.1).  The ADMM iteration projects the y-part of ``u`` onto the
+dual cone ``K*`` (Eq. "e-hsdnice": ``C = R^n x K* x R+``), so both
+``proj_K`` and ``proj_Kdual`` are provided.
+
+Conventions (the paper does not fix them):
+  * SOC(k) = {(t, x) in R x R^(k-1) : ||x||_2 <= t}, head first.
+  * PSD blocks are stored in svec form: the lower triangle, column by
+    column, with off-diagonal entries multiplied by sqrt 2, so svec is an
+    isometry and the Euclidean projection in svec space is the Frobenius
+    projection of the matrix.
+  * Exponential triples are ordered (x, y, z) as in the definition of Kexp
+    (Sec. 6.1).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SQRT2 = math.sqrt(2.0)
+E = math.e
+
+
+# ---------------------------------------------------------------------------
+# svec / smat
+# ---------------------------------------------------------------------------
+
+def svec(M: np.ndarray) -> np.ndarray:
+    k = M.shape[0]
+    parts = []
+    for j in range(k):
+        col = np.array(M[j:, j], dtype=float)
+        col[1:] *= SQRT2
+        parts.append(col)
+    return np.concatenate(parts)
+
+
+def smat(v: np.ndarray, k: int) -> np.ndarray:
+    M = np.zeros((k, k))
+    pos = 0
+    for j in range(k):
+        col = np.array(v[pos:pos + k - j], dtype=float)
+        col[1:] /= SQRT2
+        M[j:, j] = col
+        M[j, j:] = col
+        pos += k - j
+    return M
+
+
+# ---------------------------------------------------------------------------
+# single-block projections
+# ---------------------------------------------------------------------------
+
+def proj_nonneg(v):
+    return np.maximum(v, 0.0)
+
+
+def proj_soc(v):
+    """Euclidean projection onto SOC (the textbook three-case formula)."""
+    v = np.asarray(v, dtype=float)
+    t, x = v[0], v[1:]
+    nx = float(np.linalg.norm(x))
+    if nx <= t:
+        return v.copy()
+    if nx <= -t:
+        return np.zeros_like(v)
+    a = 0.5 * (t + nx)
+    out = np.empty_like(v)
+    out[0] = a
+    out[1:] = (a / nx) * x
+    return out
+
+
+def proj_psd(v, k):
+    """Sec. 6.1: eigendecompose the symmetric matrix and clip negative
+    eigenvalues to zero; returned in svec form."""
+    M = smat(v, k)
+    lam, Q = np.linalg.eigh(M)
+    P = (Q * np.maximum(lam, 0.0)) @ Q.T
+    return svec(0.5 * (P + P.T))
+
+
+def in_exp(v, tol=0.0):
+    """Membership in Kexp = {y > 0, y e^(x/y) <= z} U {x <= 0, y = 0, z >= 0},
+    up to a distance ``tol * max(1, ||v||)``: accepted when a point of Kexp
+    that close is exhibited (v with x moved down to the boundary value
+    y ln(z/y); v with z moved up to y e^(x/y); or v moved onto the face
+    {x <= 0, y = 0, z >= 0})."""
+    x, y, z = (float(t) for t in v)
+    slack = tol * max(1.0, math.sqrt(x * x + y * y + z * z))
+    if y > 0.0 and z > 0.0 and x <= y * math.log(z / y) + slack:
+        return True
+    if y > 0.0 and x / y < 700.0 and y * math.exp(x / y) <= z + slack:
+        return True
+    face = math.sqrt(max(x, 0.0) ** 2 + y * y + min(z, 0.0) ** 2)
+    return face <= slack
+
+
+def in_exp_dual(v, tol=0.0):
+    """Membership in Kexp* = {u < 0, -u e^(v/u) <= e w} U {(0, v, w): v, w >= 0}
+    (Sec. 6.1, the factor ``e`` read as Euler's number), up to a distance
+    ``tol * max(1, ||v||)``: v with its second entry moved up to the boundary
+    value u (1 + ln(w/(-u))); v with w moved up to -u e^(v/u) / e; or v moved
+    onto the face {u = 0, v >= 0, w >= 0}."""
+    u, vv, w = (float(t) for t in v)
+    slack = tol * max(1.0, math.sqrt(u * u + vv * vv + w * w))
+    if u < 0.0 and w > 0.0 and vv >= u * (1.0 + math.log(w / -u)) - slack:
+        return True
+    if u < 0.0 and vv / u < 700.0 and -u * math.exp(vv / u) <= math.e * (w + slack):
+        return True
+    face = math.sqrt(u * u + min(vv, 0.0) ** 2 + min(w, 0.0) ** 2)
+    return face <= slack
+
+
+def _exp_h(rho, r0, s0, t0):
+    """Residual of the third coordinate of ``p - d`` on the one-parameter
+    family where the first two coordinates of ``v`` are matched.
+
+    With p = y (rho, 1, e^rho) on the boundary of Kexp and its complementary
+    ray d = mu (-1, rho - 1, e^-rho) on the boundary of Kexp*, the equations
+    r0 = y rho + mu and s0 = y - mu (rho - 1) give
+        y  = ((rho - 1) r0 + s0) / (rho^2 - rho + 1),
+        mu = (r0 - rho s0)       / (rho^2 - rho + 1),
+    and the projection is found where y e^rho - mu e^-rho = t0."""
+    den = rho * rho - rho + 1.0
+    y = ((rho - 1.0) * r0 + s0) / den
+    mu = (r0 - rho * s0) / den
+    with np.errstate(over="ignore", invalid="ignore"):
+        return y * np.exp(rho) - mu * np.exp(-rho) - t0, y
+
+
+def proj_exp(v):
+    """Euclidean projection onto Kexp.
+
+    The paper only cites the method (Sec. 6.1); this follows the projection's
+    optimality conditions directly: p = Pi(v) iff p in K, p - v in K* and
+    p.(p - v) = 0.  Cases: v already in K; -v in K* (v in the polar cone,
+    projection 0); x <= 0 and y <= 0 (projection onto the face
+    {x <= 0, y = 0, z >= 0}); otherwise p lies on the curved boundary and the
+    one-dimensional root of ``_exp_h`` is found by bisection on the interval
+    where y > 0 and mu > 0 (h < 0 at the end where y -> 0 because -v is not
+    in K*, h > 0 at the end where mu -> 0 because v is not in K)."""
+    r0, s0, t0 = (float(t) for t in v)
+    if in_exp((r0, s0, t0)):
+        return np.array([r0, s0, t0])
+    if in_exp_dual((-r0, -s0, -t0)):
+        return np.zeros(3)
+    if r0 <= 0.0 and s0 <= 0.0:
+        return np.array([r0, 0.0, max(t0, 0.0)])
+    # interval of rho on which y > 0 and mu > 0
+    lo, hi = -math.inf, math.inf
+    if r0 > 0.0:
+        lo = 1.0 - s0 / r0          # y -> 0 here
+    if s0 > 0.0:
+        hi = r0 / s0                # mu -> 0 here
+    if not math.isfinite(lo):
+        step = 1.0
+        lo = hi - step
+        while _exp_h(lo, r0, s0, t0)[0] >= 0.0:
+            step *= 2.0
+            lo = hi - step
+    if not math.isfinite(hi):
+        step = 1.0
+        hi = lo + step
+        while _exp_h(hi, r0, s0, t0)[0] <= 0.0:
+            step *= 2.0
+            hi = lo + step
+    for _ in range(400):
+        mid = 0.5 * (lo + hi)
+        if mid <= lo or mid >= hi:
+            break
+        h, _y = _exp_h(mid, r0, s0, t0)
+        if h < 0.0:
+            lo = mid
+        else:
+            hi = mid
+    rho = 0.5 * (lo + hi)
+    # p = y (rho, 1, e^rho) and p = v + mu (-1, rho - 1, e^-rho) are equal at
+    # the root; return the one whose rounding error bound is smaller (y
+    # cancels near the end where y -> 0, mu near the end where mu -> 0).
+    den = rho * rho - rho + 1.0
+    y = ((rho - 1.0) * r0 + s0) / den
+    mu = (r0 - rho * s0) / den
+    ray_p = np.array([rho, 1.0, math.exp(rho)])
+    ray_d = np.array([-1.0, rho - 1.0, math.exp(-rho)])
+    err_p = (abs(rho - 1.0) * abs(r0) + abs(s0)) / den * np.linalg.norm(ray_p)
+    err_d = (abs(r0) + abs(rho) * abs(s0)) / den * np.linalg.norm(ray_d) + math.sqrt(r0 * r0 + s0 * s0 + t0 * t0)
+    if err_p <= err_d:
+        return y * ray_p
+    return np.array([r0, s0, t0]) + mu * ray_d
+
+
+def proj_exp_dual(v):
+    """Moreau (Eq. "e-moreau" applied to K*): Pi_{K*}(w) = w + Pi_K(-w)."""
+    v = np.asarray(v, dtype=float)
+    return v + proj_exp(-v)
+
+
+# ---------------------------------------------------------------------------
+# whole-cone projections and membership
+# ---------------------------------------------------------------------------
+
+def proj_K(v, cone):
+    """Euclidean projection onto K (block by block)."""
+    v = np.asarray(v, dtype=float)
+    out = np.empty_like(v)
+    for kind, off, size, order in cone.blocks():
+        seg = v[off:off + size]
+        if kind == "zero":
+            out[off:off + size] = 0.0
+        elif kind == "nonneg":
+            out[off:off + size] = proj_nonneg(seg)
+        elif kind == "soc":
+            out[off:off + size] = proj_soc(seg)
+        elif kind == "psd":
+            out[off:off + size] = proj_psd(seg, order)
+        elif kind == "exp":
+            out[off:off + size] = proj_exp(seg)
+    return out
+
+
+def proj_Kdual(v, cone):
+    """Euclidean projection onto K*: the dual of {0} is R (free), the
+    nonnegative, second-order and PSD cones are self-dual, Kexp* via Moreau."""
+    v = np.asarray(v, dtype=float)
+    out = np.empty_like(v)
+    for kind, off, size, order in cone.blocks():
+        seg = v[off:off + size]
+        if kind == "zero":
+            out[off:off + size] = seg
+        elif kind == "nonneg":
+            out[off:off + size] = proj_nonneg(seg)
+        elif kind == "soc":
+            out[off:off + size] = proj_soc(seg)
+        elif kind == "psd":
+            out[off:off + size] = proj_psd(seg, order)
+        elif kind == "exp":
+            out[off:off + size] = proj_exp_dual(seg)
+    return out
+
+
+def _in_soc(seg, tol):
+    return np.linalg.norm(seg[1:]) <= seg[0] + tol * max(1.0, abs(seg[0]))
+
+
+def _in_psd(seg, order, tol):
+    lam = np.linalg.eigvalsh(smat(seg, order))
+    return lam.min() >= -tol * max(1.0, np.abs(lam).max())
+
+
+def in_K(v, cone, tol=1e-9):
+    for kind, off, size, order in cone.blocks():
+        seg = np.asarray(v[off:off + size], dtype=float)
+        if kind == "zero" and np.abs(seg).max() > tol:
+            return False
+        if kind == "nonneg" and seg.min() < -tol:
+            return False
+        if kind == "soc" and not _in_soc(seg, tol):
+            return False
+        if kind == "psd" and not _in_psd(seg, order, tol):
+            return False
+        if kind == "exp" and not in_exp(seg, tol):
+            return False
+    return True
+
+
+def in_Kdual(v, cone, tol=1e-9):
+    for kind, off, size, order in cone.blocks():
+        seg = np.asarray(v[off:off + size], dtype=float)
+        if kind == "nonneg" and seg.min() < -tol:
+            return False
+        if kind == "soc" and not _in_soc(seg, tol):
+            return False
+        if kind == "psd" and not _in_psd(seg, order, tol):
+            return False
+        if kind == "exp" and not in_exp_dual(seg, tol):
+            return False
+    return True
