@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark of the GPU splitting conic solver on the large mixed-cone program.
+
+Workload (default): n = 1e6 variables, m = 2e6 rows, nnz(A) = 2e7 with
+power-law row lengths, cones zero 1e5 / SOC 2e4 blocks of 3..50 / exp 1e4 /
+nonnegative rest, built by the Sec. 6.6 generator (seed 0).  A step is one
+ADMM iteration of Eq. "e-SCS" (subspace projection by warm-started PCG,
+cone projection, dual update) on that problem; the metric is ADMM
+iterations per second with A resident in HBM, FP32 sparse products and CG,
+FP64 iterates and checks.  The JSON line also carries the time to the 1e-4
+tolerances, the end-to-end rate through the C ABI with host buffers, the
+roofline of the dominant kernel, the CPU oracle's rate and the SM clocks.
+
+``--impl reference`` times the FP64 CPU oracle (the paper's indirect method
+restated in numpy/scipy) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ADMM iters/s and time-to-1e-4 (s); SpMV/CG HBM GB/s vs peak; warm/batched vs plain"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--workload", choices=["mixed", "mixed_small", "lp"], default="mixed")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true", help="skip the time-to-1e-4 solve")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def make_problem(workload, seed):
+    from paper_1312_3039_gb300 import synth
+    if workload == "mixed":
+        return synth.mixed(seed), ("mixed-cone program n=1e6 m=2e6 nnz=2e7 (power-law rows; zero 1e5, "
+                                   "SOC 2e4 blocks of 3-50, exp 1e4, nonneg rest)")
+    if workload == "mixed_small":
+        return synth.mixed_small(seed, scale=50), "mixed-cone program n=2e4 m=4e4 nnz=4e5 (same recipe)"
+    return synth.lp(seed), "sparse LP n=200 m=400 (zero 100, nonneg 300), 5% density"
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def spmv_bytes(P, it, cg, elt=4):
+    """Algorithmic bytes of the SpMV launches (kind 0: with A, kind 1: with
+    A^T) over ``it`` ADMM iterations with ``cg`` CG steps in total.  Each
+    launch streams its CSR arrays once (elt-byte values, 4-byte column
+    indices and row pointers), gathers its input vector once from L2 (counted
+    once: elt bytes per entry) and moves its epilogue's vectors."""
+    m, n, nnz = P.m, P.n, P.A.nnz
+    mat_a = (elt + 4) * nnz + 4 * (m + 1)
+    mat_at = (elt + 4) * nnz + 4 * (n + 1)
+    k1 = mat_a + elt * n + (8 + 8 + 8) * m + elt * m             # z gathered; u_y, v_s, b read; y_acc written
+    k3 = mat_a + elt * n + elt * m                                # p gathered; q written
+    k2 = mat_at + elt * m + (8 + 8 + elt + elt) * n + 2 * elt * n  # y_acc gathered; u_x, c, z, diag read; r, p written
+    k4 = mat_at + elt * m + 4 * elt * n + 2 * elt * n             # q gathered; p, z, r, diag read; z, r written
+    return {0: it * k1 + cg * k3, 1: it * k2 + cg * k4, "per_launch": {"A_cg": k3, "At_cg": k4}}
+
+
+def cpu_oracle_rate(P, seconds, steps=None):
+    """Time the FP64 oracle's indirect method on this problem (single thread).
+    Returns (iterations, elapsed seconds, setup seconds)."""
+    from oracle import admm
+    t0 = time.perf_counter()
+    S = admm.HSDSolver(P.A, P.b, P.c, P.cone, admm.Settings(linsys="indirect"))
+    setup = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    it = 0
+    while True:
+        S.step()
+        it += 1
+        el = time.perf_counter() - t1
+        if steps is not None:
+            if it >= steps:
+                break
+        elif el >= seconds:
+            break
+    return it, time.perf_counter() - t1, setup, S
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    P, desc = make_problem(args.workload, args.seed)
+    from oracle import admm
+    t0 = time.perf_counter()
+    S = admm.HSDSolver(P.A, P.b, P.c, P.cone, admm.Settings(linsys="indirect"))
+    setup = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        S.step()
+    t1 = time.perf_counter()
+    for _ in range(args.steps):
+        S.step()
+    el = time.perf_counter() - t1
+    value = args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (Sec. 6.6 generator, seed %d)" % args.seed,
+        "config": {"workload": desc, "precision": "fp64", "linsys": "indirect CG (oracle)"},
+        "cpu_baseline": {"value": value, "unit": "iter/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} ADMM iterations after {args.warmup} warm-up "
+                                   f"(setup {setup:.1f} s not timed)"},
+        "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_1312_3039_gb300 import scs
+
+    P, desc = make_problem(args.workload, args.seed)
+    stream = torch.cuda.current_stream()
+    common = dict(precision=1, device=local, cuda_stream=stream.cuda_stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t)
+        return float(t.item())
+
+    S = scs.Solver(P.A, P.b, P.c, P.cone, time_limit_s=120.0, **common)
+    # warm-up iterations, then exactly `steps` timed iterations
+    S.iterate(args.warmup)
+    torch.cuda.synchronize()
+    barrier()
+    it0, cg0 = S.counters()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    S.iterate(args.steps, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    it1, cg1 = S.counters()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    iters_done = sum_over_ranks(it1 - it0)
+    value = iters_done / (ms / 1e3)
+    cg_steps = cg1 - cg0
+    launches = 4 * (it1 - it0) + 3 * cg_steps
+
+    # roofline of the dominant kernel (CUDA events around each SpMV launch)
+    S.iterate_profiled(5)
+    prof = {k: S.kernel_time(k) for k in (0, 1, 2)}
+    it_p, cg_p = S.counters()
+    # counters include the profiled iterations: take CG steps of those 5 from the launch counts
+    cg_prof = prof[0][1] - 5
+    byt = spmv_bytes(P, 5, cg_prof)
+    kind = 0 if prof[0][0] >= prof[1][0] else 1
+    achieved = byt[kind] / (prof[kind][0] / 1e3) / 1e9
+    peak, peak_src = measured_hbm_peak()
+    names = {0: "spmv_A (q = A p, y_acc init)", 1: "spmv_At (A^T q + CG update)"}
+    roofline = {"bound": "hbm", "kernel": names[kind], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
+                "algorithmic_bytes_per_cg_launch": byt["per_launch"]["A_cg" if kind == 0 else "At_cg"],
+                "avg_launch_us": 1e3 * prof[kind][0] / prof[kind][1],
+                "other_kernel_avg_us": 1e3 * prof[1 - kind][0] / max(prof[1 - kind][1], 1),
+                "projection_avg_us": 1e3 * prof[2][0] / max(prof[2][1], 1)}
+
+    # time to the 1e-4 tolerances from a cold start, data resident
+    solve = None
+    if not args.no_solve:
+        st, x, y, s, info = S.solve()
+        solve = {"status": int(st), "iters": info["iters"], "seconds": info["solve_s"],
+                 "avg_cg_per_iter": info["cg_iters"] / max(info["iters"], 1),
+                 "pobj": info["pobj"], "p_star": P.p_star,
+                 "rel_err_vs_p_star": abs(info["pobj"] - P.p_star) / (1 + abs(P.p_star)) if P.p_star else None,
+                 "setup_s": info["setup_s"]}
+    S.close()
+
+    # end to end through the C ABI with host buffers: scs_init from the host
+    # CSC, `steps` iterations of scs_solve (tolerances 0), outputs to host
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        S2 = scs.Solver(P.A, P.b, P.c, P.cone, max_iters=args.steps, eps_pri=0.0, eps_dual=0.0, eps_gap=0.0,
+                        eps_infeas=0.0, eps_unbdd=0.0, **common)
+        st, x, y, s, info = S2.solve()
+        S2.close()
+        torch.cuda.synchronize()
+        el = max_over_ranks(time.perf_counter() - t0)
+        h2d = 8 * (P.n + 1) + 12 * P.A.nnz + 8 * P.m + 8 * P.n
+        d2h = 8 * (P.n + 2 * P.m)
+        e2e = {"value": sum_over_ranks(args.steps) / el, "unit": "iter/s",
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "seconds": el, "includes": "scs_init (host CSC->CSR, H2D, equilibration, M^-1 h) + scs_solve "
+                                          f"({args.steps} iterations) + D2H of x, y, s"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        it, el, setup, _ = cpu_oracle_rate(P, args.cpu_seconds)
+        cpu = {"value": it / el, "unit": "iter/s", "cores": 1, "kind": "oracle",
+               "sample": f"{it} ADMM iterations of the FP64 oracle (indirect CG, scipy sparse, one thread) on "
+                         f"the same problem after its setup ({setup:.1f} s, not timed)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (Sec. 6.6 generator, seed %d)" % args.seed,
+            "config": {"workload": desc, "precision": "fp32 A/CG, fp64 iterates and checks",
+                       "l2": "inputs larger than L2 (A and A^T in CSR: %.0f MB)" % (2 * 8 * P.A.nnz / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "cg_steps_per_iter": cg_steps / max(it1 - it0, 1)},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk, "time_to_1e4": solve,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

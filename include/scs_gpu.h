@@ -1,0 +1,184 @@
+/*
+ * scs_gpu.h -- C ABI of the GB300 splitting conic solver.
+ *
+ * Solves the primal-dual pair of cone programs (Sec. 2, Eq. "e-coneprob")
+ *
+ *     minimize  c^T x   subject to  A x + s = b,  s in K
+ *     maximize -b^T y   subject to  -A^T y + r = c,  r = 0,  y in K*
+ *
+ * by ADMM on the homogeneous self-dual embedding (Sec. 2.3, Eq. "e-hsd";
+ * iteration Eq. "e-SCS" with over-relaxation, Sec. 3.3), projecting onto the
+ * subspace with the indirect method of Sec. 4.1 (Jacobi-preconditioned CG on
+ * I + A^T A, warm-started, stopped at zeta^k = (1/k)^cg_rate, Sec. 6.1) and
+ * onto the cone block by block.  Data are equilibrated as in Sec. 5 and
+ * termination follows Sec. 3.5 / Sec. 5 ("Scaled termination criteria").
+ *
+ * Every step of the iteration runs in CUDA kernels on one GPU; the host only
+ * validates input, builds the sparse layouts, launches and reads a status
+ * word every `check_interval` iterations.
+ *
+ * Conventions
+ *   - All symbols are extern "C"; no C++ exception crosses the ABI.  Every
+ *     call returns a status (or NULL plus *err) and never aborts the process.
+ *   - Row order of K: `z` zero rows, `l` nonnegative rows, SOC blocks of sizes
+ *     q[0..nq) (head first: {(t, x): ||x|| <= t}), PSD blocks of orders
+ *     s[0..ns) in svec form (lower triangle column by column, off-diagonal
+ *     entries times sqrt 2), `ep` exponential triples (x, y, z) with
+ *     Kexp = closure{y > 0, y e^(x/y) <= z} (Sec. 6.1).
+ *   - Host pointers unless stated.  Inputs are copied during the call; the
+ *     caller keeps ownership.  A work object owns all device memory it uses
+ *     until scs_finish.
+ *   - One work object must not be used by two threads at once; distinct work
+ *     objects are independent (each has its own CUDA stream unless one is
+ *     given in the settings).
+ */
+#ifndef SCS_GPU_H
+#define SCS_GPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes (Sec. 2.3: tau > 0 gives a solution, kappa > 0 a certificate) */
+enum {
+    SCS_SOLVED = 1,                 /* optimality tests of Sec. 3.5 passed                */
+    SCS_SOLVED_INACCURATE = 2,      /* max_iters / time limit reached, tau dominant       */
+    SCS_UNFINISHED = 0,
+    SCS_INFEASIBLE = -1,            /* y/(-b^T y) certifies primal infeasibility (Sec. 2.2) */
+    SCS_UNBOUNDED = -2,             /* x/(-c^T x) certifies dual infeasibility (Sec. 2.2)   */
+    SCS_INFEASIBLE_INACCURATE = -3,
+    SCS_UNBOUNDED_INACCURATE = -4,
+    SCS_INVALID_INPUT = -10,
+    SCS_DEVICE_ERROR = -11,
+    SCS_TIMEOUT = -12,
+    SCS_NUMERICAL = -13,
+    SCS_UNSUPPORTED = -14           /* cone type or size this build does not handle       */
+};
+
+/* A in compressed sparse column form, 0-based.  colptr has n+1 entries,
+ * rowidx/val have colptr[n] entries; row indices inside a column need not be
+ * sorted; duplicate entries are summed; nnz must be below 2^31. */
+typedef struct {
+    int32_t m, n;
+    const int64_t *colptr;
+    const int32_t *rowidx;
+    const double *val;
+} scs_csc;
+
+/* K = {0}^z x R+^l x SOC(q_0) x ... x PSD(s_0) x ... x Kexp^ep (Sec. 6.1). */
+typedef struct {
+    int32_t z, l;
+    const int32_t *q;
+    int32_t nq;
+    const int32_t *s;
+    int32_t ns;
+    int32_t ep;
+} scs_cone;
+
+typedef struct {
+    double eps_pri, eps_dual, eps_gap;    /* Sec. 3.5 tolerances                        */
+    double eps_infeas, eps_unbdd;         /* Sec. 3.5 certificate tolerances            */
+    double alpha;                         /* relaxation, Sec. 3.3; in (0, 2)            */
+    double cg_rate;                       /* zeta^k = (1/k)^cg_rate; <= 0 disables it   */
+    double cg_tol_rel;                    /* CG also stops at cg_tol_rel * ||u^k + v^k|| */
+    double time_limit_s;                  /* <= 0: none                                 */
+    int32_t max_iters;
+    int32_t check_interval;               /* termination test every this many iterations */
+    int32_t cg_max_iters;                 /* cap on CG steps per ADMM iteration          */
+    int32_t normalize;                    /* 1: equilibrate (Sec. 5); 0: use data as is   */
+    int32_t scale_passes;                 /* equilibration passes                       */
+    int32_t precision;                    /* 0: FP64 throughout; 1: FP32 A and CG, FP64
+                                             iterates, residuals, gap and certificates */
+    int32_t use_graph;                    /* 1: one CUDA graph per iteration with the CG
+                                             loop as a device-side conditional node     */
+    int32_t verbose;
+    int32_t device;                       /* CUDA device ordinal                        */
+    void *cuda_stream;                    /* cudaStream_t to run on, or NULL            */
+} scs_settings;
+
+typedef struct {
+    int32_t status;
+    int32_t iters;                        /* ADMM iterations done                        */
+    int32_t cg_iters;                     /* CG steps over the solve                     */
+    int32_t matvecs;                      /* 2 * iters + 2 * cg_iters: one A and one A^T
+                                             product per iteration outside CG, two per
+                                             CG step (Table 5's count)                  */
+    double pobj, dobj;                    /* c^T x and -b^T y of the returned point      */
+    double res_pri, res_dual, gap;        /* unscaled ||Ax+s-b||, ||A^T y+c||, |c^T x+b^T y| */
+    double tau, kappa;
+    double setup_s, solve_s;              /* wall time of scs_init and of scs_solve      */
+} scs_info;
+
+typedef struct scs_work scs_work;
+
+/* Fill *s with defaults: eps 1e-4, alpha 1.5, cg_rate 1.5, cg_tol_rel 0,
+ * max_iters 10000, check_interval 20, cg_max_iters 50, normalize 1,
+ * scale_passes 10, precision 1, use_graph 1, device 0. */
+void scs_default_settings(scs_settings *s);
+
+/* Validate and copy A, b (m), c (n) and the cone to the device, equilibrate
+ * (Sec. 5), form the Jacobi preconditioner diag(I + A^T A) and the cached
+ * p = M^-1 h and 1 + h^T p (Sec. 4.1), set u0 = (0,0,1), v0 = (0,0,1)
+ * (Sec. 3.4).  Returns NULL and sets *err (if err is not NULL) to an SCS_*
+ * status on failure; scs_last_error() then describes it. */
+scs_work *scs_init(const scs_csc *A, const double *b, const double *c,
+                   const scs_cone *k, const scs_settings *st, int32_t *err);
+
+/* Run the iteration from the current starting point (cold, or the one set by
+ * scs_warm_start) until a Sec. 3.5 test passes, max_iters or the time limit.
+ * x (n), y (m), s (m) receive, in host memory, the solution (status 1, 2) or
+ * the certificate (status -1: y with b^T y = -1, x and s NaN; status -2: x
+ * with c^T x = -1, s = -A x, y NaN).  Any output pointer may be NULL.  info
+ * may be NULL.  The next call starts cold unless scs_warm_start is called. */
+int32_t scs_solve(scs_work *w, double *x, double *y, double *s, scs_info *info);
+
+/* Sec. 4.2 warm start: the next scs_solve starts from u0 = (x, y, 1),
+ * v0 = (0, s, 0) (mapped into the scaled problem).  Host arrays of length n,
+ * m, m; NULL entries are taken as zero.  The cached factor data and the CG
+ * warm-start vector are kept. */
+int32_t scs_warm_start(scs_work *w, const double *x, const double *y, const double *s);
+
+/* Free everything the work object owns.  NULL is accepted. */
+void scs_finish(scs_work *w);
+
+/* ---- extensions (not in the paper's interface) ---------------------------- */
+
+/* Reset the iterates to u0 = (0,0,1), v0 = (0,0,1) and the CG warm start to 0. */
+int32_t scs_reset(scs_work *w);
+
+/* Run exactly `iters` ADMM iterations from the current iterates, without
+ * termination tests (benchmarking, resume).  Asynchronous on the work's
+ * stream unless `sync` is nonzero. */
+int32_t scs_iterate(scs_work *w, int32_t iters, int32_t sync);
+
+/* Copy the raw scaled iterates u = (x, y, tau) and v = (0, s, kappa), each of
+ * length n + m + 1, to host arrays (either may be NULL). */
+int32_t scs_get_iterates(scs_work *w, double *u, double *v);
+
+/* Copy the scaling (Sec. 5) to host arrays D (m) and E (n), and sigma, rho. */
+int32_t scs_get_scaling(scs_work *w, double *D, double *E, double *sigma, double *rho);
+
+/* Per-kernel device time since the last call (CUDA events on the work's
+ * stream, collected only by scs_iterate_profiled).  kind: 0 = SpMV with A in
+ * the CG loop, 1 = SpMV with A^T in the CG loop, 2 = cone projection.
+ * Writes the summed milliseconds and the launch count. */
+int32_t scs_iterate_profiled(scs_work *w, int32_t iters);
+int32_t scs_kernel_time(scs_work *w, int32_t kind, double *ms, int64_t *launches);
+
+/* Iteration counters since the last reset / warm start / solve start: ADMM
+ * iterations and CG steps (synchronises the work's stream). */
+int32_t scs_counters(scs_work *w, int32_t *iters, int64_t *cg_iters);
+
+/* Sizes of the work object's problem and the device bytes it holds. */
+int32_t scs_dims(scs_work *w, int32_t *m, int32_t *n, int64_t *nnz, int64_t *device_bytes);
+
+/* Human-readable description of the most recent error on this thread. */
+const char *scs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCS_GPU_H */

@@ -1,0 +1,657 @@
+// Host side of the device solver: owns the device buffers of one problem,
+// performs the setup (equilibration, preconditioner, cached M^-1 h), records
+// one ADMM iteration as a CUDA graph whose CG loop is a device-driven
+// conditional WHILE node, and runs the solve loop with a termination test
+// every `check_interval` iterations.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/scs_gpu.h"
+#include "engine_base.h"
+#include "kernels.cuh"
+
+namespace scs {
+
+template <typename T>
+class Engine : public EngineBase {
+   public:
+    Engine(const HostProblem &P, const scs_settings &st) : st_(st) {
+        const auto t0 = std::chrono::steady_clock::now();
+        m_ = P.m;
+        n_ = P.n;
+        N_ = n_ + m_ + 1;
+        nnz_ = P.nnz;
+        SCS_CUDA(cudaSetDevice(st.device));
+        device_ = st.device;
+        cudaDeviceProp prop;
+        SCS_CUDA(cudaGetDeviceProperties(&prop, device_));
+        sms_ = prop.multiProcessorCount;
+        if (st.cuda_stream) {
+            stream_ = static_cast<cudaStream_t>(st.cuda_stream);
+        } else {
+            SCS_CUDA(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking));
+            own_stream_ = true;
+        }
+        SCS_CUDA(cudaStreamCreateWithFlags(&body_stream_, cudaStreamNonBlocking));
+        cur_ = stream_;
+        SCS_CUDA(cudaMallocHost(&Sh_, sizeof(Scalars)));
+        setup(P);
+        setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+
+    ~Engine() override {
+        cudaSetDevice(device_);
+        if (exec_) cudaGraphExecDestroy(exec_);
+        if (graph_) cudaGraphDestroy(graph_);
+        for (auto &e : ev_) cudaEventDestroy(e);
+        for (void *p : allocs_) cudaFree(p);
+        if (Sh_) cudaFreeHost(Sh_);
+        if (body_stream_) cudaStreamDestroy(body_stream_);
+        if (own_stream_ && stream_) cudaStreamDestroy(stream_);
+    }
+
+    // -------------------------------------------------------------------
+    int reset() override {
+        SCS_CUDA(cudaSetDevice(device_));
+        set_initial_point();
+        SCS_CUDA(cudaStreamSynchronize(stream_));
+        warm_pending_ = false;
+        return 0;
+    }
+
+    int warm_start(const double *x, const double *y, const double *s) override {
+        SCS_CUDA(cudaSetDevice(device_));
+        // Sec. 4.2: u0 = (x, y, 1), v0 = (0, s, 0) in the scaled problem:
+        // x^ = sigma E^-1 x, y^ = rho D^-1 y, s^ = sigma D s
+        std::vector<double> u(N_, 0.0), v(N_, 0.0);
+        for (int j = 0; j < n_; ++j) u[j] = x ? sigma_ * x[j] / Eh_[j] : 0.0;
+        for (int i = 0; i < m_; ++i) {
+            u[n_ + i] = y ? rho_ * y[i] / Dh_[i] : 0.0;
+            v[n_ + i] = s ? sigma_ * Dh_[i] * s[i] : 0.0;
+        }
+        u[N_ - 1] = 1.0;
+        v[N_ - 1] = 0.0;
+        SCS_CUDA(cudaMemcpyAsync(u_, u.data(), sizeof(double) * N_, cudaMemcpyHostToDevice, stream_));
+        SCS_CUDA(cudaMemcpyAsync(v_, v.data(), sizeof(double) * N_, cudaMemcpyHostToDevice, stream_));
+        reset_counters();
+        SCS_CUDA(cudaStreamSynchronize(stream_));
+        warm_pending_ = true;
+        return 0;
+    }
+
+    int iterate(int iters, int sync) override {
+        SCS_CUDA(cudaSetDevice(device_));
+        run_iters(iters);
+        if (sync) SCS_CUDA(cudaStreamSynchronize(stream_));
+        return 0;
+    }
+
+    int iterate_profiled(int iters) override {
+        SCS_CUDA(cudaSetDevice(device_));
+        if (ev_.empty()) {
+            ev_.resize(2);
+            for (auto &e : ev_) SCS_CUDA(cudaEventCreate(&e));
+        }
+        for (int it = 0; it < iters; ++it) {
+            timed(0, [&] { launch_K1(); });
+            timed(1, [&] { launch_K2(CondHandle{0, 0}); });
+            for (int c = 0; c < st_.cg_max_iters; ++c) {
+                timed(0, [&] { launch_K3(); });
+                timed(1, [&] { launch_K4(); });
+                launch_K5(CondHandle{0, 0});
+                SCS_CUDA(cudaMemcpyAsync(Sh_, S_, sizeof(Scalars), cudaMemcpyDeviceToHost, stream_));
+                SCS_CUDA(cudaStreamSynchronize(stream_));
+                if (!Sh_->active) break;
+            }
+            launch_K6();
+            timed(2, [&] { launch_K7(); });
+        }
+        SCS_CUDA(cudaStreamSynchronize(stream_));
+        return 0;
+    }
+
+    int kernel_time(int kind, double *ms, int64_t *launches) override {
+        if (kind < 0 || kind > 2) return SCS_INVALID_INPUT;
+        if (ms) *ms = prof_ms_[kind];
+        if (launches) *launches = prof_n_[kind];
+        prof_ms_[kind] = 0.0;
+        prof_n_[kind] = 0;
+        return 0;
+    }
+
+    int get_iterates(double *u, double *v) override {
+        SCS_CUDA(cudaSetDevice(device_));
+        SCS_CUDA(cudaStreamSynchronize(stream_));
+        if (u) SCS_CUDA(cudaMemcpy(u, u_, sizeof(double) * N_, cudaMemcpyDeviceToHost));
+        if (v) SCS_CUDA(cudaMemcpy(v, v_, sizeof(double) * N_, cudaMemcpyDeviceToHost));
+        return 0;
+    }
+
+    int get_scaling(double *D, double *E, double *sigma, double *rho) override {
+        if (D) std::memcpy(D, Dh_.data(), sizeof(double) * m_);
+        if (E) std::memcpy(E, Eh_.data(), sizeof(double) * n_);
+        if (sigma) *sigma = sigma_;
+        if (rho) *rho = rho_;
+        return 0;
+    }
+
+    void dims(int32_t *m, int32_t *n, int64_t *nnz, int64_t *bytes) override {
+        if (m) *m = m_;
+        if (n) *n = n_;
+        if (nnz) *nnz = nnz_;
+        if (bytes) *bytes = bytes_;
+    }
+
+    int counters(int32_t *iters, int64_t *cg_iters) override {
+        SCS_CUDA(cudaSetDevice(device_));
+        SCS_CUDA(cudaMemcpyAsync(Sh_, S_, sizeof(Scalars), cudaMemcpyDeviceToHost, stream_));
+        SCS_CUDA(cudaStreamSynchronize(stream_));
+        if (iters) *iters = Sh_->k;
+        if (cg_iters) *cg_iters = Sh_->cg_total;
+        return 0;
+    }
+
+    int solve(double *x, double *y, double *s, scs_info *info) override {
+        SCS_CUDA(cudaSetDevice(device_));
+        const auto t0 = std::chrono::steady_clock::now();
+        if (!warm_pending_) set_initial_point();
+        warm_pending_ = false;
+        int status = 0;
+        bool timed_out = false;
+        int k = 0;
+        const int ci = st_.check_interval > 0 ? st_.check_interval : 1;
+        for (;;) {
+            const int chunk = std::min(ci, st_.max_iters - k);
+            if (chunk > 0) run_iters(chunk);
+            k += chunk > 0 ? chunk : 0;
+            launch_check();
+            SCS_CUDA(cudaMemcpyAsync(Sh_, S_, sizeof(Scalars), cudaMemcpyDeviceToHost, stream_));
+            SCS_CUDA(cudaStreamSynchronize(stream_));
+            status = Sh_->status;
+            if (status != 0 || k >= st_.max_iters) break;
+            if (st_.time_limit_s > 0) {
+                const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                if (el > st_.time_limit_s) { timed_out = true; break; }
+            }
+        }
+        if (status == 0) status = inaccurate_status();
+        (void)timed_out;
+        // outputs
+        output_kernel<<<grid_for(n_ + 2 * m_), kBlock, 0, stream_>>>(n_, m_, status, u_, v_, D_, E_, ax_, S_,
+                                                                    out_, out_ + n_, out_ + n_ + m_);
+        SCS_CUDA(cudaGetLastError());
+        if (x) SCS_CUDA(cudaMemcpyAsync(x, out_, sizeof(double) * n_, cudaMemcpyDeviceToHost, stream_));
+        if (y) SCS_CUDA(cudaMemcpyAsync(y, out_ + n_, sizeof(double) * m_, cudaMemcpyDeviceToHost, stream_));
+        if (s) SCS_CUDA(cudaMemcpyAsync(s, out_ + n_ + m_, sizeof(double) * m_, cudaMemcpyDeviceToHost, stream_));
+        SCS_CUDA(cudaMemcpyAsync(Sh_, S_, sizeof(Scalars), cudaMemcpyDeviceToHost, stream_));
+        SCS_CUDA(cudaStreamSynchronize(stream_));
+        if (info) {
+            info->status = status;
+            info->iters = Sh_->k;
+            info->cg_iters = static_cast<int32_t>(Sh_->cg_total);
+            info->matvecs = 2 * Sh_->k + 2 * static_cast<int32_t>(Sh_->cg_total);
+            info->tau = Sh_->tau;
+            info->kappa = Sh_->kappa;
+            info->res_pri = Sh_->res_pri;
+            info->res_dual = Sh_->res_dual;
+            info->gap = Sh_->gap;
+            if (status == 1 || status == 2) {
+                info->pobj = Sh_->pobj;
+                info->dobj = Sh_->dobj;
+            } else if (status == -1 || status == -3) {
+                info->pobj = NAN;
+                info->dobj = 1.0;
+            } else if (status == -2 || status == -4) {
+                info->pobj = -1.0;
+                info->dobj = NAN;
+            } else {
+                info->pobj = info->dobj = NAN;
+            }
+            info->setup_s = setup_s;
+            info->solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        }
+        return status;
+    }
+
+    // internals (public so that extended device lambdas may be defined in them)
+    // ------------------------------------------------------------------ memory
+    template <typename U>
+    U *dalloc(size_t count) {
+        void *p = nullptr;
+        if (count == 0) count = 1;
+        SCS_CUDA(cudaMalloc(&p, sizeof(U) * count));
+        allocs_.push_back(p);
+        bytes_ += static_cast<int64_t>(sizeof(U) * count);
+        return static_cast<U *>(p);
+    }
+    void dfree(void *p) {
+        for (size_t i = 0; i < allocs_.size(); ++i)
+            if (allocs_[i] == p) {
+                cudaFree(p);
+                allocs_.erase(allocs_.begin() + i);
+                return;
+            }
+    }
+    template <typename U>
+    U *upload(const std::vector<U> &h) {
+        U *d = dalloc<U>(h.size());
+        if (!h.empty()) SCS_CUDA(cudaMemcpyAsync(d, h.data(), sizeof(U) * h.size(), cudaMemcpyHostToDevice, stream_));
+        return d;
+    }
+    int grid_for(int64_t len) const {
+        int64_t g = (len + kBlock - 1) / kBlock;
+        const int64_t cap = static_cast<int64_t>(sms_) * 8;
+        if (g > cap) g = cap;
+        if (g < 1) g = 1;
+        return static_cast<int>(g);
+    }
+
+    // ------------------------------------------------------------------ setup
+    void setup(const HostProblem &P) {
+        // sparse layouts
+        std::vector<int32_t> blkA, blkAt;
+        stream_blocks(P.a_rowptr.data(), m_, blkA);
+        stream_blocks(P.at_rowptr.data(), n_, blkAt);
+        int32_t *a_rowptr = upload(P.a_rowptr), *a_col = upload(P.a_col);
+        int32_t *at_rowptr = upload(P.at_rowptr), *at_col = upload(P.at_col);
+        double *a_val64 = upload(P.a_val), *at_val64 = upload(P.at_val);
+        int32_t *a_blk = upload(blkA), *at_blk = upload(blkAt);
+        const int max_blocks = std::max({(int)blkA.size(), (int)blkAt.size(), sms_ * 8, 1});
+        rb_.partials = dalloc<double>(static_cast<size_t>(max_blocks) * kMaxRed);
+        rb_.counter = dalloc<unsigned>(kSiteCount);
+        SCS_CUDA(cudaMemsetAsync(rb_.counter, 0, sizeof(unsigned) * kSiteCount, stream_));
+        S_ = dalloc<Scalars>(1);
+
+        // vectors
+        u_ = dalloc<double>(N_);
+        v_ = dalloc<double>(N_);
+        b_ = upload(P.b);
+        c_ = upload(P.c);
+        D_ = dalloc<double>(m_);
+        E_ = dalloc<double>(n_);
+        p_ = dalloc<double>(n_ + m_);
+        ax_ = dalloc<double>(m_);
+        out_ = dalloc<double>(n_ + 2 * m_);
+        z_ = dalloc<T>(n_);
+        r_ = dalloc<T>(n_);
+        pv_ = dalloc<T>(n_);
+        diag_ = dalloc<T>(n_);
+        q_ = dalloc<T>(m_);
+        yacc_ = dalloc<T>(m_);
+        double *tmp_m = dalloc<double>(m_), *tmp_n = dalloc<double>(n_);
+        double *red_out = dalloc<double>(4);
+
+        fill(D_, m_, 1.0);
+        fill(E_, n_, 1.0);
+
+        // cone tables (row offsets within y)
+        ConeDev K{};
+        K.z = P.z;
+        K.l = P.l;
+        K.nq = static_cast<int>(P.q.size());
+        K.ep = P.ep;
+        std::vector<int32_t> qoff, avg_off, avg_len;
+        int32_t off = P.z + P.l;
+        for (int32_t qs : P.q) {
+            qoff.push_back(off);
+            avg_off.push_back(off);
+            avg_len.push_back(qs);
+            off += qs;
+        }
+        for (int32_t ss : P.s) {     // PSD blocks: scaled as one block each
+            avg_off.push_back(off);
+            avg_len.push_back(ss * (ss + 1) / 2);
+            off += ss * (ss + 1) / 2;
+        }
+        K.exp_off = off;
+        for (int e = 0; e < P.ep; ++e) {
+            avg_off.push_back(off + 3 * e);
+            avg_len.push_back(3);
+        }
+        K.q_off = upload(qoff);
+        K.q_len = upload(P.q);
+        K.nb_elem = (n_ + K.z + K.l + kBlock - 1) / kBlock;
+        if (K.nb_elem < 1) K.nb_elem = 1;
+        K.nb_soc = (K.nq + kWarps - 1) / kWarps;
+        K.nb_exp = (K.ep + kBlock - 1) / kBlock;
+        cone_ = K;
+        const int32_t *d_avg_off = upload(avg_off), *d_avg_len = upload(avg_len);
+        const int navg = static_cast<int>(avg_off.size());
+
+        // ---- equilibration, Sec. 5 (FP64) ----
+        if (st_.normalize) {
+            for (int pass = 0; pass < st_.scale_passes; ++pass) {
+                row_sumsq_kernel<<<grid_for((int64_t)m_ * 32), kBlock, 0, stream_>>>(a_rowptr, a_val64, m_, tmp_m);
+                row_sumsq_kernel<<<grid_for((int64_t)n_ * 32), kBlock, 0, stream_>>>(at_rowptr, at_val64, n_, tmp_n);
+                sqrt_kernel<<<grid_for(m_), kBlock, 0, stream_>>>(tmp_m, m_);
+                sqrt_kernel<<<grid_for(n_), kBlock, 0, stream_>>>(tmp_n, n_);
+                if (navg)
+                    block_mean_kernel<<<grid_for((int64_t)navg * 32), kBlock, 0, stream_>>>(tmp_m, d_avg_off,
+                                                                                            d_avg_len, navg);
+                inv_sqrt_clamp_kernel<<<grid_for(m_), kBlock, 0, stream_>>>(tmp_m, m_, 1e-4, 1e4, tmp_m, D_);
+                inv_sqrt_clamp_kernel<<<grid_for(n_), kBlock, 0, stream_>>>(tmp_n, n_, 1e-4, 1e4, tmp_n, E_);
+                scale_vals_kernel<<<grid_for((int64_t)m_ * 32), kBlock, 0, stream_>>>(a_rowptr, a_col, a_val64, m_,
+                                                                                      tmp_m, tmp_n);
+                scale_vals_kernel<<<grid_for((int64_t)n_ * 32), kBlock, 0, stream_>>>(at_rowptr, at_col, at_val64,
+                                                                                      n_, tmp_n, tmp_m);
+                SCS_CUDA(cudaGetLastError());
+            }
+            // sigma = 1 / max(||D b||, 1e-4); rho = mean_i ||row_i(A^)|| / max(||E c||, 1e-4)
+            row_sumsq_kernel<<<grid_for((int64_t)m_ * 32), kBlock, 0, stream_>>>(a_rowptr, a_val64, m_, tmp_m);
+            sqrt_kernel<<<grid_for(m_), kBlock, 0, stream_>>>(tmp_m, m_);
+            const double *Db = D_, *bb = b_, *Ec = E_, *cc = c_, *tm = tmp_m;
+            reduce_kernel<<<grid_for(m_), kBlock, 0, stream_>>>(
+                [=] __device__(int i) { return tm[i]; }, m_, rb_, red_out + 0);
+            reduce_kernel<<<grid_for(m_), kBlock, 0, stream_>>>(
+                [=] __device__(int i) { const double t = Db[i] * bb[i]; return t * t; }, m_, rb_, red_out + 1);
+            reduce_kernel<<<grid_for(n_), kBlock, 0, stream_>>>(
+                [=] __device__(int i) { const double t = Ec[i] * cc[i]; return t * t; }, n_, rb_, red_out + 2);
+            double h[3];
+            SCS_CUDA(cudaMemcpyAsync(h, red_out, sizeof(h), cudaMemcpyDeviceToHost, stream_));
+            SCS_CUDA(cudaStreamSynchronize(stream_));
+            double mean_row = m_ ? h[0] / m_ : 1.0;
+            if (!(mean_row > 0.0)) mean_row = 1.0;
+            sigma_ = 1.0 / std::max(std::sqrt(h[1]), 1e-4);
+            rho_ = mean_row / std::max(std::sqrt(h[2]), 1e-4);
+        } else {
+            sigma_ = 1.0;
+            rho_ = 1.0;
+        }
+        {
+            double *bd = b_, *cd = c_;
+            const double *Dd = D_, *Ed = E_;
+            const double sg = sigma_, rh = rho_;
+            foreach_kernel<<<grid_for(m_), kBlock, 0, stream_>>>([=] __device__(int i) { bd[i] *= sg * Dd[i]; }, m_);
+            foreach_kernel<<<grid_for(n_), kBlock, 0, stream_>>>([=] __device__(int j) { cd[j] *= rh * Ed[j]; }, n_);
+        }
+        // Jacobi preconditioner diag(I + A^T A) = 1 + ||col_j(A^)||^2
+        row_sumsq_kernel<<<grid_for((int64_t)n_ * 32), kBlock, 0, stream_>>>(at_rowptr, at_val64, n_, tmp_n);
+        {
+            T *dg = diag_;
+            const double *tn = tmp_n;
+            foreach_kernel<<<grid_for(n_), kBlock, 0, stream_>>>(
+                [=] __device__(int j) { dg[j] = static_cast<T>(1.0 + tn[j]); }, n_);
+        }
+        // values in the iteration's precision
+        const T *a_val, *at_val;
+        if (std::is_same<T, double>::value) {
+            a_val = reinterpret_cast<const T *>(a_val64);
+            at_val = reinterpret_cast<const T *>(at_val64);
+        } else {
+            T *av = dalloc<T>(nnz_), *atv = dalloc<T>(nnz_);
+            const double *a64 = a_val64, *at64 = at_val64;
+            foreach_kernel<<<grid_for(nnz_), kBlock, 0, stream_>>>(
+                [=] __device__(int k) { av[k] = static_cast<T>(a64[k]); atv[k] = static_cast<T>(at64[k]); },
+                (int)nnz_);
+            a_val = av;
+            at_val = atv;
+        }
+        A_ = Csr<T>{a_rowptr, a_col, a_val, a_blk, (int32_t)blkA.size() - 1, m_};
+        At_ = Csr<T>{at_rowptr, at_col, at_val, at_blk, (int32_t)blkAt.size() - 1, n_};
+        SCS_CUDA(cudaGetLastError());
+        SCS_CUDA(cudaStreamSynchronize(stream_));
+        if (!std::is_same<T, double>::value) {
+            // FP64 copies are kept for the termination tests
+            A64_ = Csr<double>{a_rowptr, a_col, a_val64, a_blk, (int32_t)blkA.size() - 1, m_};
+            At64_ = Csr<double>{at_rowptr, at_col, at_val64, at_blk, (int32_t)blkAt.size() - 1, n_};
+        } else {
+            A64_ = Csr<double>{a_rowptr, a_col, a_val64, a_blk, (int32_t)blkA.size() - 1, m_};
+            At64_ = Csr<double>{at_rowptr, at_col, at_val64, at_blk, (int32_t)blkAt.size() - 1, n_};
+        }
+
+        // host copies of the scaling (warm start, scs_get_scaling)
+        Dh_.resize(m_);
+        Eh_.resize(n_);
+        SCS_CUDA(cudaMemcpy(Dh_.data(), D_, sizeof(double) * m_, cudaMemcpyDeviceToHost));
+        SCS_CUDA(cudaMemcpy(Eh_.data(), E_, sizeof(double) * n_, cudaMemcpyDeviceToHost));
+
+        // scalars
+        Scalars sh{};
+        sh.relax = st_.alpha;
+        sh.eps_pri = st_.eps_pri;
+        sh.eps_dual = st_.eps_dual;
+        sh.eps_gap = st_.eps_gap;
+        sh.eps_infeas = st_.eps_infeas;
+        sh.eps_unbdd = st_.eps_unbdd;
+        double nb = 0, nc = 0;
+        for (double t : P.b) nb += t * t;
+        for (double t : P.c) nc += t * t;
+        sh.nb = std::sqrt(nb);
+        sh.nc = std::sqrt(nc);
+        sh.sigma = sigma_;
+        sh.rho = rho_;
+        sh.hp1 = 1.0;
+        // cached p = M^-1 h solved tightly (Sec. 4.1): CG from zero with the
+        // right-hand side r = h, i.e. u = (c^, b^, 0), v = 0
+        sh.cg_rate = 0.0;
+        sh.cg_tol_rel = std::is_same<T, double>::value ? 1e-14 : 1e-7;
+        sh.cg_max = std::max(10 * st_.cg_max_iters, 500);
+        SCS_CUDA(cudaMemcpyAsync(S_, &sh, sizeof(Scalars), cudaMemcpyHostToDevice, stream_));
+        SCS_CUDA(cudaMemsetAsync(u_, 0, sizeof(double) * N_, stream_));
+        SCS_CUDA(cudaMemsetAsync(v_, 0, sizeof(double) * N_, stream_));
+        SCS_CUDA(cudaMemcpyAsync(u_, c_, sizeof(double) * n_, cudaMemcpyDeviceToDevice, stream_));
+        SCS_CUDA(cudaMemcpyAsync(u_ + n_, b_, sizeof(double) * m_, cudaMemcpyDeviceToDevice, stream_));
+        SCS_CUDA(cudaMemsetAsync(z_, 0, sizeof(T) * n_, stream_));
+        launch_K1();
+        launch_K2(CondHandle{0, 0});
+        for (int c = 0; c < sh.cg_max; c += 16) {
+            for (int j = 0; j < 16; ++j) {
+                launch_K3();
+                launch_K4();
+                launch_K5(CondHandle{0, 0});
+            }
+            SCS_CUDA(cudaMemcpyAsync(Sh_, S_, sizeof(Scalars), cudaMemcpyDeviceToHost, stream_));
+            SCS_CUDA(cudaStreamSynchronize(stream_));
+            if (!Sh_->active) break;
+        }
+        {
+            double *pd = p_;
+            const T *zz = z_, *ya = yacc_;
+            const int n = n_;
+            foreach_kernel<<<grid_for(n_ + m_), kBlock, 0, stream_>>>(
+                [=] __device__(int i) { pd[i] = i < n ? static_cast<double>(zz[i]) : static_cast<double>(ya[i - n]); },
+                n_ + m_);
+            const double *cc = c_, *bb = b_;
+            reduce_kernel<<<grid_for(n_ + m_), kBlock, 0, stream_>>>(
+                [=] __device__(int i) { return (i < n ? cc[i] : bb[i - n]) * pd[i]; }, n_ + m_, rb_, red_out + 3);
+        }
+        double hp;
+        SCS_CUDA(cudaMemcpyAsync(&hp, red_out + 3, sizeof(double), cudaMemcpyDeviceToHost, stream_));
+        SCS_CUDA(cudaStreamSynchronize(stream_));
+        sh.hp1 = 1.0 + hp;
+        sh.cg_rate = st_.cg_rate;
+        sh.cg_tol_rel = st_.cg_tol_rel;
+        sh.cg_max = st_.cg_max_iters;
+        SCS_CUDA(cudaMemcpy(S_, &sh, sizeof(Scalars), cudaMemcpyHostToDevice));
+        dfree(tmp_m);
+        dfree(tmp_n);
+        set_initial_point();
+        if (st_.use_graph) build_graph();
+        SCS_CUDA(cudaStreamSynchronize(stream_));
+    }
+
+    void fill(double *d, int len, double val) {
+        foreach_kernel<<<grid_for(len), kBlock, 0, stream_>>>([=] __device__(int i) { d[i] = val; }, len);
+    }
+
+    void reset_counters() {
+        // k = 0, cg_total = 0, status = 0 (fields of the device scalars)
+        const int zero = 0;
+        const int64_t zero64 = 0;
+        SCS_CUDA(cudaMemcpyAsync(&S_->k, &zero, sizeof(int), cudaMemcpyHostToDevice, stream_));
+        SCS_CUDA(cudaMemcpyAsync(&S_->status, &zero, sizeof(int), cudaMemcpyHostToDevice, stream_));
+        SCS_CUDA(cudaMemcpyAsync(&S_->cg_total, &zero64, sizeof(int64_t), cudaMemcpyHostToDevice, stream_));
+        SCS_CUDA(cudaStreamSynchronize(stream_));
+    }
+
+    // Sec. 3.4: u0 = (0, 0, 1), v0 = (0, 0, 1); CG warm start from zero
+    void set_initial_point() {
+        SCS_CUDA(cudaMemsetAsync(u_, 0, sizeof(double) * N_, stream_));
+        SCS_CUDA(cudaMemsetAsync(v_, 0, sizeof(double) * N_, stream_));
+        SCS_CUDA(cudaMemsetAsync(z_, 0, sizeof(T) * n_, stream_));
+        double *uu = u_, *vv = v_;
+        const int N = N_;
+        foreach_kernel<<<1, 32, 0, stream_>>>([=] __device__(int) { uu[N - 1] = 1.0; vv[N - 1] = 1.0; }, 1);
+        SCS_CUDA(cudaGetLastError());
+        reset_counters();
+    }
+
+    int inaccurate_status() const {
+        const Scalars &s = *Sh_;
+        if (!std::isfinite(s.tau) || !std::isfinite(s.kappa)) return SCS_NUMERICAL;
+        if (s.tau > 0 && s.tau >= s.kappa) return SCS_SOLVED_INACCURATE;
+        if (s.bty < 0 && s.bty <= s.ctx) return SCS_INFEASIBLE_INACCURATE;
+        if (s.ctx < 0) return SCS_UNBOUNDED_INACCURATE;
+        return s.tau > 0 ? SCS_SOLVED_INACCURATE : SCS_INFEASIBLE_INACCURATE;
+    }
+
+    // ------------------------------------------------------------ launches
+    void launch_K1() {
+        EpiAInit<T> e{u_, v_, b_, yacc_, S_, n_, N_, 0.0};
+        spmv_stream_kernel<T, T, T, EpiAInit<T>><<<A_.nblk, kBlock, 0, cur_>>>(A_, z_, e, rb_);
+    }
+    void launch_K2(CondHandle h) {
+        EpiAtInit<T> e{u_, v_, c_, diag_, z_, r_, pv_, S_, h, N_, 0.0};
+        spmv_stream_kernel<T, T, T, EpiAtInit<T>><<<At_.nblk, kBlock, 0, cur_>>>(At_, yacc_, e, rb_);
+    }
+    void launch_K3() {
+        EpiACG<T> e{q_, S_};
+        spmv_stream_kernel<T, T, T, EpiACG<T>><<<A_.nblk, kBlock, 0, cur_>>>(A_, pv_, e, rb_);
+    }
+    void launch_K4() {
+        EpiAtCG<T> e{diag_, z_, r_, pv_, S_, T(0)};
+        spmv_stream_kernel<T, T, T, EpiAtCG<T>><<<At_.nblk, kBlock, 0, cur_>>>(At_, q_, e, rb_);
+    }
+    void launch_K5(CondHandle h) {
+        cg_update_kernel<T><<<grid_for(std::max(n_, m_)), kBlock, 0, cur_>>>(n_, m_, q_, yacc_, r_, diag_, pv_, S_,
+                                                                              h, rb_);
+    }
+    void launch_K6() {
+        smw_kernel<T><<<grid_for(n_ + m_), kBlock, 0, cur_>>>(n_, m_, c_, b_, z_, yacc_, S_, rb_);
+    }
+    void launch_K7() {
+        ProjArgs<T> a{n_, m_, N_, u_, v_, p_, z_, yacc_, S_};
+        const int grid = cone_.nb_elem + cone_.nb_soc + cone_.nb_exp;
+        relax_project_kernel<T><<<grid, kBlock, 0, cur_>>>(a, cone_);
+    }
+    void launch_check() {
+        EpiChkA ea{u_, v_, b_, D_, ax_, S_, n_, N_, 0.0};
+        spmv_stream_kernel<double, double, double, EpiChkA><<<A64_.nblk, kBlock, 0, stream_>>>(A64_, u_, ea, rb_);
+        EpiChkAt eb{u_, v_, c_, E_, S_, N_, 0.0};
+        spmv_stream_kernel<double, double, double, EpiChkAt><<<At64_.nblk, kBlock, 0, stream_>>>(At64_, u_ + n_, eb,
+                                                                                                  rb_);
+        SCS_CUDA(cudaGetLastError());
+    }
+
+    template <typename F>
+    void timed(int kind, F f) {
+        SCS_CUDA(cudaEventRecord(ev_[0], stream_));
+        f();
+        SCS_CUDA(cudaEventRecord(ev_[1], stream_));
+        SCS_CUDA(cudaEventSynchronize(ev_[1]));
+        float ms = 0.f;
+        SCS_CUDA(cudaEventElapsedTime(&ms, ev_[0], ev_[1]));
+        prof_ms_[kind] += ms;
+        prof_n_[kind] += 1;
+    }
+
+    // one ADMM iteration without a graph: the CG steps beyond convergence
+    // return at once (they read the device flag S->active)
+    void launch_iteration_plain() {
+        launch_K1();
+        launch_K2(CondHandle{0, 0});
+        for (int c = 0; c < st_.cg_max_iters; ++c) {
+            launch_K3();
+            launch_K4();
+            launch_K5(CondHandle{0, 0});
+        }
+        launch_K6();
+        launch_K7();
+    }
+
+    void run_iters(int iters) {
+        for (int it = 0; it < iters; ++it) {
+            if (exec_) {
+                SCS_CUDA(cudaGraphLaunch(exec_, stream_));
+            } else {
+                launch_iteration_plain();
+            }
+        }
+        SCS_CUDA(cudaGetLastError());
+    }
+
+    // Graph of one iteration: K1 -> K2 -> WHILE(active){K3 -> K4 -> K5} -> K6 -> K7.
+    void build_graph() {
+        SCS_CUDA(cudaGraphCreate(&graph_, 0));
+        cudaGraphConditionalHandle h;
+        SCS_CUDA(cudaGraphConditionalHandleCreate(&h, graph_, 1, cudaGraphCondAssignDefault));
+        CondHandle ch{h, 1};
+        SCS_CUDA(cudaStreamBeginCaptureToGraph(stream_, graph_, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        cur_ = stream_;
+        launch_K1();
+        launch_K2(ch);
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        cudaGraph_t cap_graph;
+        SCS_CUDA(cudaStreamGetCaptureInfo(stream_, &cs, nullptr, &cap_graph, &deps, nullptr, &ndeps));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cnode;
+        SCS_CUDA(cudaGraphAddNode(&cnode, cap_graph, deps, nullptr, ndeps, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        SCS_CUDA(cudaStreamUpdateCaptureDependencies(stream_, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+        SCS_CUDA(cudaStreamBeginCaptureToGraph(body_stream_, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        cur_ = body_stream_;
+        launch_K3();
+        launch_K4();
+        launch_K5(ch);
+        cudaGraph_t body_out;
+        SCS_CUDA(cudaStreamEndCapture(body_stream_, &body_out));
+        cur_ = stream_;
+        launch_K6();
+        launch_K7();
+        cudaGraph_t done_graph;
+        SCS_CUDA(cudaStreamEndCapture(stream_, &done_graph));
+        SCS_CUDA(cudaGraphInstantiate(&exec_, graph_, 0));
+        cur_ = stream_;
+    }
+
+    // ------------------------------------------------------------------ state
+    scs_settings st_;
+    int device_ = 0, sms_ = 1;
+    int m_ = 0, n_ = 0, N_ = 0;
+    int64_t nnz_ = 0, bytes_ = 0;
+    cudaStream_t stream_ = nullptr, body_stream_ = nullptr, cur_ = nullptr;
+    bool own_stream_ = false, warm_pending_ = false;
+    std::vector<void *> allocs_;
+    Csr<T> A_{}, At_{};
+    Csr<double> A64_{}, At64_{};
+    ConeDev cone_{};
+    ReduceBuf rb_{};
+    Scalars *S_ = nullptr, *Sh_ = nullptr;
+    double *u_ = nullptr, *v_ = nullptr, *b_ = nullptr, *c_ = nullptr, *D_ = nullptr, *E_ = nullptr;
+    double *p_ = nullptr, *ax_ = nullptr, *out_ = nullptr;
+    T *z_ = nullptr, *r_ = nullptr, *pv_ = nullptr, *diag_ = nullptr, *q_ = nullptr, *yacc_ = nullptr;
+    std::vector<double> Dh_, Eh_;
+    double sigma_ = 1.0, rho_ = 1.0;
+    cudaGraph_t graph_ = nullptr;
+    cudaGraphExec_t exec_ = nullptr;
+    std::vector<cudaEvent_t> ev_;
+    double prof_ms_[3] = {0, 0, 0};
+    int64_t prof_n_[3] = {0, 0, 0};
+};
+
+}  // namespace scs

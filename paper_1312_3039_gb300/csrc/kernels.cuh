@@ -1,0 +1,526 @@
+// Kernels of one ADMM iteration on the homogeneous self-dual embedding.
+//
+// Notation (Sec. 2.3, Sec. 4.1): u = (u_x, u_y, u_tau) in R^(n+m+1),
+// v = (0, v_s, v_kappa) (v_x stays 0 and is never touched), A^ = D A E is the
+// equilibrated data with b^, c^ (Sec. 5).  One iteration of Eq. "e-SCS" with
+// over-relaxation (Sec. 3.3):
+//   w      = u + v
+//   r      = w_xy - w_tau h,  h = (c^, b^)
+//   z      = M^-1 r, M = [I A^T; -A I]  via  z_x = (I + A^T A)^-1 (r_x - A^T r_y)
+//            (Jacobi PCG warm-started from the previous z_x, Sec. 4.1) and
+//            z_y = r_y + A z_x
+//   u~_xy  = z - p gamma,  gamma = h^T z / (1 + h^T p),  u~_tau = w_tau + gamma
+//   u_bar  = alpha u~ + (1 - alpha) u
+//   u+     = Pi_C(u_bar - v),  v+ = v - u_bar + u+
+//
+// Arrangement on the device (2 + 2K sparse products per iteration for K CG
+// steps, the count of Table 5):
+//   K1  SpMV A   : y_acc = r_y + A z_prev                    (r_y formed per row)
+//   K2  SpMV A^T : r0 = r_x - z_prev - A^T y_acc  (= t - (I + A^T A) z_prev),
+//                  p0 = r0 / diag, CG dots, CG tolerance zeta^k
+//   CG step (while not converged):
+//   K3  SpMV A   : q = A p,  alpha = r.s / (p.p + q.q)   (p^T (I + A^T A) p)
+//   K4  SpMV A^T : z += alpha p,  r -= alpha (p + A^T q),  new r.s, ||r||
+//   K5  update   : y_acc += alpha q (keeps y_acc = r_y + A z),  p = s + beta p
+//   K6  SMW      : gamma = (c^.z_x + b^.y_acc) / (1 + h^T p)
+//   K7  relax + project onto C + dual update (fused, per cone type)
+// Each reduction is a deterministic grid sum whose last CTA updates the
+// scalars (and, inside a CUDA graph, the CG loop's conditional handle).
+#pragma once
+
+#include <math.h>
+
+#include "common.cuh"
+#include "cones.cuh"
+#include "spmv.cuh"
+
+namespace scs {
+
+struct CondHandle {
+    cudaGraphConditionalHandle h;
+    int valid;
+    __device__ __forceinline__ void set(unsigned v) const {
+        if (valid) cudaGraphSetConditional(h, v);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// K1: rows of A.  y_acc_i = (u_y + v_s - w_tau b^)_i + (A^ z)_i
+// ---------------------------------------------------------------------------
+template <typename T>
+struct EpiAInit {
+    static constexpr int NV = 1;
+    static constexpr int kSite = kSiteAInit;
+    const double *u, *v, *b;
+    T *yacc;
+    Scalars *S;
+    int n, N;
+    double wtau;
+    __device__ bool skip() const { return false; }
+    __device__ void begin() { wtau = u[N - 1] + v[N - 1]; }
+    __device__ void row(int i, T s, double (&red)[NV]) {
+        const double w = u[n + i] + v[n + i];
+        yacc[i] = static_cast<T>(w - wtau * b[i] + static_cast<double>(s));
+        red[0] += w * w;
+    }
+    __device__ void finish(const double (&t)[NV]) { S->ww_y = t[0]; }
+};
+
+// ---------------------------------------------------------------------------
+// K2: rows of A^T.  r0_j = (u_x - w_tau c^)_j - z_j - (A^T y_acc)_j
+// ---------------------------------------------------------------------------
+template <typename T>
+struct EpiAtInit {
+    static constexpr int NV = 4;
+    static constexpr int kSite = kSiteAtInit;
+    const double *u, *v, *c;
+    const T *diag;
+    T *z, *r, *p;
+    Scalars *S;
+    CondHandle cond;
+    int N;
+    double wtau;
+    __device__ bool skip() const { return false; }
+    __device__ void begin() { wtau = u[N - 1] + v[N - 1]; }
+    __device__ void row(int j, T s, double (&red)[NV]) {
+        const double ux = u[j];
+        const T rj = static_cast<T>(ux - wtau * c[j] - static_cast<double>(z[j]) - static_cast<double>(s));
+        const T sj = rj / diag[j];
+        r[j] = rj;
+        p[j] = sj;
+        red[0] += static_cast<double>(rj) * sj;
+        red[1] += static_cast<double>(rj) * rj;
+        red[2] += static_cast<double>(sj) * sj;
+        red[3] += ux * ux;
+    }
+    __device__ void finish(const double (&t)[NV]) {
+        const double ww = t[3] + S->ww_y + wtau * wtau;
+        double tol = 0.0;
+        if (S->cg_rate > 0.0) tol = pow(1.0 / (double)(S->k + 1), S->cg_rate);
+        tol = fmax(tol, S->cg_tol_rel * sqrt(ww));
+        S->tol = tol;
+        S->wtau = wtau;
+        S->rz = t[0];
+        S->rr = t[1];
+        S->pp = t[2];
+        S->cg_it = 0;
+        const int done = !(sqrt(t[1]) > tol) || S->cg_max <= 0;
+        S->done = done;
+        S->active = !done;
+        cond.set(!done);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// K3: rows of A.  q = A^ p
+// ---------------------------------------------------------------------------
+template <typename T>
+struct EpiACG {
+    static constexpr int NV = 1;
+    static constexpr int kSite = kSiteACG;
+    T *q;
+    Scalars *S;
+    __device__ bool skip() const { return !S->active; }
+    __device__ void begin() {}
+    __device__ void row(int i, T s, double (&red)[NV]) {
+        q[i] = s;
+        red[0] += static_cast<double>(s) * s;
+    }
+    __device__ void finish(const double (&t)[NV]) {
+        S->qq = t[0];
+        S->alpha = S->rz / (S->pp + t[0]);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// K4: rows of A^T.  (I + A^T A) p = p + A^T q; z += alpha p; r -= alpha G p
+// ---------------------------------------------------------------------------
+template <typename T>
+struct EpiAtCG {
+    static constexpr int NV = 2;
+    static constexpr int kSite = kSiteAtCG;
+    const T *diag;
+    T *z, *r, *p;
+    Scalars *S;
+    T alpha;
+    __device__ bool skip() const { return !S->active; }
+    __device__ void begin() { alpha = static_cast<T>(S->alpha); }
+    __device__ void row(int j, T s, double (&red)[NV]) {
+        const T pj = p[j];
+        const T gp = pj + s;
+        z[j] = z[j] + alpha * pj;
+        const T rj = r[j] - alpha * gp;
+        r[j] = rj;
+        const T sj = rj / diag[j];
+        red[0] += static_cast<double>(rj) * sj;
+        red[1] += static_cast<double>(rj) * rj;
+    }
+    __device__ void finish(const double (&t)[NV]) {
+        S->cg_it += 1;
+        S->cg_total += 1;
+        S->rr = t[1];
+        const int done = !(sqrt(t[1]) > S->tol) || S->cg_it >= S->cg_max;
+        S->done = done;
+        S->beta = t[0] / S->rz;
+        S->rz = t[0];
+    }
+};
+
+// ---------------------------------------------------------------------------
+// K5: y_acc += alpha q;  p = r / diag + beta p
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kBlock) cg_update_kernel(int n, int m, const T *__restrict__ q,
+                                                           T *__restrict__ yacc, const T *__restrict__ r,
+                                                           const T *__restrict__ diag, T *__restrict__ p,
+                                                           Scalars *S, CondHandle cond, ReduceBuf rb) {
+    if (!S->active) return;
+    const T alpha = static_cast<T>(S->alpha);
+    const T beta = static_cast<T>(S->beta);
+    const int done = S->done;
+    double red[1] = {0.0};
+    const int total = n > m ? n : m;
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < total; i += gridDim.x * kBlock) {
+        if (i < m) yacc[i] = yacc[i] + alpha * q[i];
+        if (i < n && !done) {
+            const T pj = r[i] / diag[i] + beta * p[i];
+            p[i] = pj;
+            red[0] += static_cast<double>(pj) * pj;
+        }
+    }
+    double tot[1];
+    if (grid_sum<1>(red, rb, kSiteCGUpd, tot)) {
+        if (threadIdx.x == 0) {
+            if (!done) S->pp = tot[0];
+            S->active = !done;
+            cond.set(!done);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K6: gamma = h^T z / (1 + h^T p)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kBlock) smw_kernel(int n, int m, const double *__restrict__ c,
+                                                     const double *__restrict__ b, const T *__restrict__ z,
+                                                     const T *__restrict__ yacc, Scalars *S, ReduceBuf rb) {
+    double red[1] = {0.0};
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < n + m; i += gridDim.x * kBlock) {
+        red[0] += i < n ? c[i] * static_cast<double>(z[i]) : b[i - n] * static_cast<double>(yacc[i - n]);
+    }
+    double tot[1];
+    if (grid_sum<1>(red, rb, kSiteSmw, tot)) {
+        if (threadIdx.x == 0) S->gamma = tot[0] / S->hp1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K7: relax, project onto C = R^n x K* x R+, update v  (one launch)
+//   block ranges: [0, nb_elem)      x-part, zero rows, nonnegative rows, tau
+//                 [.., + nb_soc)    one warp per second-order block
+//                 [.., + nb_exp)    one thread per exponential triple
+// ---------------------------------------------------------------------------
+struct ConeDev {
+    int z, l;              // zero and nonnegative row counts
+    int nq;                // second-order blocks
+    const int32_t *q_off;  // row offset (within y) of each SOC block
+    const int32_t *q_len;
+    int ep;                // exponential triples
+    int exp_off;           // row offset of the first triple
+    int nb_elem, nb_soc, nb_exp;
+};
+
+template <typename T>
+struct ProjArgs {
+    int n, m, N;
+    double *u, *v;
+    const double *p;       // cached M^-1 h (n + m)
+    const T *z;            // z_x
+    const T *yacc;         // z_y
+    Scalars *S;
+};
+
+template <typename T>
+__device__ __forceinline__ double relaxed(const ProjArgs<T> &a, int idx, double gamma, double alpha) {
+    // u~ = z - p gamma; u_bar = alpha u~ + (1 - alpha) u
+    const double zi = idx < a.n ? static_cast<double>(a.z[idx]) : static_cast<double>(a.yacc[idx - a.n]);
+    const double ut = zi - a.p[idx] * gamma;
+    return alpha * ut + (1.0 - alpha) * a.u[idx];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) relax_project_kernel(ProjArgs<T> a, ConeDev K) {
+    const double gamma = a.S->gamma;
+    const double alpha = a.S->relax;
+    const int bid = blockIdx.x;
+    if (bid < K.nb_elem) {
+        const int nlin = a.n + K.z + K.l;
+        const int idx = bid * kBlock + threadIdx.x;
+        if (idx < nlin) {
+            const double ub = relaxed(a, idx, gamma, alpha);
+            if (idx < a.n) {
+                a.u[idx] = ub;                       // R^n: identity, v_x stays 0
+            } else {
+                const double t = ub - a.v[idx];
+                const double up = (idx < a.n + K.z) ? t : fmax(t, 0.0);   // K* of {0} is R
+                a.u[idx] = up;
+                a.v[idx] = up - t;
+            }
+        }
+        if (bid == 0 && threadIdx.x == 0) {
+            // tau: u~_tau = w_tau + gamma
+            const int it = a.N - 1;
+            const double ut = a.S->wtau + gamma;
+            const double ub = alpha * ut + (1.0 - alpha) * a.u[it];
+            const double t = ub - a.v[it];
+            const double up = fmax(t, 0.0);
+            a.u[it] = up;
+            a.v[it] = up - t;
+            a.S->k += 1;
+        }
+        return;
+    }
+    const int sb = bid - K.nb_elem;
+    if (sb < K.nb_soc) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int blk = sb * kWarps + warp;
+        if (blk >= K.nq) return;
+        const int off = a.n + K.q_off[blk];
+        const int len = K.q_len[blk];
+        // t = u_bar - v over the block; project onto SOC (self-dual)
+        double t0 = 0.0, xx = 0.0;
+        for (int e = lane; e < len; e += 32) {
+            const double t = relaxed(a, off + e, gamma, alpha) - a.v[off + e];
+            if (e == 0) t0 = t; else xx += t * t;
+        }
+        xx = warp_sum(xx);
+        t0 = __shfl_sync(0xffffffffu, t0, 0);
+        const double nx = sqrt(xx);
+        double scale_head, scale_tail;     // projection = (scale_head, scale_tail * x)
+        if (nx <= t0) { scale_head = t0; scale_tail = 1.0; }
+        else if (nx <= -t0) { scale_head = 0.0; scale_tail = 0.0; }
+        else {
+            const double h = 0.5 * (t0 + nx);
+            scale_head = h;
+            scale_tail = h / nx;
+        }
+        for (int e = lane; e < len; e += 32) {
+            const double t = relaxed(a, off + e, gamma, alpha) - a.v[off + e];
+            const double up = e == 0 ? scale_head : scale_tail * t;
+            a.u[off + e] = up;
+            a.v[off + e] = up - t;
+        }
+        return;
+    }
+    const int eb = sb - K.nb_soc;
+    if (eb < K.nb_exp) {
+        const int tri = eb * kBlock + threadIdx.x;
+        if (tri >= K.ep) return;
+        const int off = a.n + K.exp_off + 3 * tri;
+        double t[3];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) t[e] = relaxed(a, off + e, gamma, alpha) - a.v[off + e];
+        double pu, pv, pw;
+        proj_exp_dual(t[0], t[1], t[2], pu, pv, pw);
+        a.u[off] = pu; a.v[off] = pu - t[0];
+        a.u[off + 1] = pv; a.v[off + 1] = pv - t[1];
+        a.u[off + 2] = pw; a.v[off + 2] = pw - t[2];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Termination (Sec. 3.5 with Sec. 5's scaled residuals), FP64 throughout.
+//   KC1 rows of A  : a = A^ u_x + v_s;  ||D^-1 (a - tau b^)||, ||D^-1 a||, b^.u_y
+//   KC2 rows of A^T: d = A^T u_y;  ||E^-1 (d + tau c^)||, ||E^-1 d||, c^.u_x
+// The last CTA of KC2 evaluates the tests in the order optimality, primal
+// infeasibility, dual infeasibility and writes S->status.
+// ---------------------------------------------------------------------------
+struct EpiChkA {
+    static constexpr int NV = 3;
+    static constexpr int kSite = kSiteChkA;
+    const double *u, *v, *b, *D;
+    double *ax;
+    Scalars *S;
+    int n, N;
+    double tau;
+    __device__ bool skip() const { return false; }
+    __device__ void begin() { tau = u[N - 1]; }
+    __device__ void row(int i, double s, double (&red)[NV]) {
+        ax[i] = s;
+        const double a = s + v[n + i];
+        const double pr = (a - tau * b[i]) / D[i];
+        const double ub = a / D[i];
+        red[0] += pr * pr;
+        red[1] += ub * ub;
+        red[2] += b[i] * u[n + i];
+    }
+    __device__ void finish(const double (&t)[NV]) {
+        S->pri2 = t[0];
+        S->unb2 = t[1];
+        S->bty = t[2];
+    }
+};
+
+struct EpiChkAt {
+    static constexpr int NV = 3;
+    static constexpr int kSite = kSiteChkAt;
+    const double *u, *v, *c, *E;
+    Scalars *S;
+    int N;
+    double tau;
+    __device__ bool skip() const { return false; }
+    __device__ void begin() { tau = u[N - 1]; }
+    __device__ void row(int j, double s, double (&red)[NV]) {
+        const double du = (s + tau * c[j]) / E[j];
+        const double in = s / E[j];
+        red[0] += du * du;
+        red[1] += in * in;
+        red[2] += c[j] * u[j];
+    }
+    __device__ void finish(const double (&t)[NV]) {
+        S->dual2 = t[0];
+        S->inf2 = t[1];
+        S->ctx = t[2];
+        const double tau_ = u[N - 1], kappa = v[N - 1];
+        const double sg = S->sigma, rh = S->rho;
+        S->tau = tau_;
+        S->kappa = kappa;
+        int status = 0;
+        if (tau_ > 0.0) {
+            const double pri = sqrt(S->pri2) / (tau_ * sg);
+            const double dual = sqrt(t[0]) / (tau_ * rh);
+            const double cx = t[2] / (tau_ * rh * sg);
+            const double by = S->bty / (tau_ * rh * sg);
+            const double gap = fabs(cx + by);
+            S->res_pri = pri;
+            S->res_dual = dual;
+            S->gap = gap;
+            S->pobj = cx;
+            S->dobj = -by;
+            if (pri <= S->eps_pri * (1.0 + S->nb) && dual <= S->eps_dual * (1.0 + S->nc) &&
+                gap <= S->eps_gap * (1.0 + fabs(cx) + fabs(by)))
+                status = 1;
+        } else {
+            S->res_pri = S->res_dual = S->gap = INFINITY;
+            S->pobj = S->dobj = NAN;
+        }
+        if (!status && S->nb > 0.0 && S->bty < 0.0 &&
+            sqrt(t[1]) <= (-S->bty / (sg * S->nb)) * S->eps_infeas)
+            status = -1;
+        if (!status && S->nc > 0.0 && t[2] < 0.0 &&
+            sqrt(S->unb2) <= (-t[2] / (rh * S->nc)) * S->eps_unbdd)
+            status = -2;
+        if (!isfinite(tau_) || !isfinite(kappa) || !isfinite(S->pri2) || !isfinite(t[0]) ||
+            !isfinite(S->unb2) || !isfinite(t[1]))
+            status = -13;
+        S->status = status;
+    }
+};
+
+// Solution or certificate in the caller's units (Sec. 5 unscaling, Sec. 2.3 cases).
+static __global__ void __launch_bounds__(kBlock) output_kernel(int n, int m, int status, const double *__restrict__ u,
+                                                        const double *__restrict__ v, const double *__restrict__ D,
+                                                        const double *__restrict__ E, const double *__restrict__ ax,
+                                                        const Scalars *S, double *__restrict__ x,
+                                                        double *__restrict__ y, double *__restrict__ s) {
+    const int N = n + m + 1;
+    const double tau = u[N - 1];
+    const double sg = S->sigma, rh = S->rho;
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < n + 2 * m; i += gridDim.x * kBlock) {
+        if (status == 1 || status == 2) {
+            if (i < n) x[i] = E[i] * u[i] / (tau * sg);
+            else if (i < n + m) y[i - n] = D[i - n] * u[i] / (tau * rh);
+            else s[i - n - m] = v[i - m] / (D[i - n - m] * tau * sg);
+        } else if (status == -1 || status == -3) {
+            const double f = sg / (-S->bty);       // b^T (D u_y) = b^.u_y / sigma
+            if (i < n) x[i] = NAN;
+            else if (i < n + m) y[i - n] = D[i - n] * u[i] * f;
+            else s[i - n - m] = NAN;
+        } else if (status == -2 || status == -4) {
+            const double f = rh / (-S->ctx);       // c^T (E u_x) = c^.u_x / rho
+            if (i < n) x[i] = E[i] * u[i] * f;
+            else if (i < n + m) y[i - n] = NAN;
+            else s[i - n - m] = -ax[i - n - m] * f / D[i - n - m];   // s = -A x
+        } else {
+            if (i < n) x[i] = NAN;
+            else if (i < n + m) y[i - n] = NAN;
+            else s[i - n - m] = NAN;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// setup kernels (FP64): equilibration (Sec. 5) and conversions
+// ---------------------------------------------------------------------------
+static __global__ void row_sumsq_kernel(const int32_t *__restrict__ rowptr, const double *__restrict__ val, int rows,
+                                 double *__restrict__ out) {
+    const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * kBlock) >> 5;
+    for (int r = warp; r < rows; r += nw) {
+        double s = 0.0;
+        for (int k = rowptr[r] + lane; k < rowptr[r + 1]; k += 32) s += val[k] * val[k];
+        s = warp_sum(s);
+        if (lane == 0) out[r] = s;
+    }
+}
+
+static __global__ void scale_vals_kernel(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                  double *__restrict__ val, int rows, const double *__restrict__ drow,
+                                  const double *__restrict__ ecol) {
+    const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * kBlock) >> 5;
+    for (int r = warp; r < rows; r += nw) {
+        const double d = drow[r];
+        for (int k = rowptr[r] + lane; k < rowptr[r + 1]; k += 32) val[k] *= d * ecol[col[k]];
+    }
+}
+
+static __global__ void sqrt_kernel(double *__restrict__ nrm, int len) {
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < len; i += gridDim.x * kBlock) nrm[i] = sqrt(nrm[i]);
+}
+
+// over each cone block that D must keep scalar: replace the norms by their mean
+
+static __global__ void block_mean_kernel(double *__restrict__ nrm, const int32_t *__restrict__ bo,
+                                  const int32_t *__restrict__ bl, int nblocks) {
+    const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * kBlock) >> 5;
+    for (int b = warp; b < nblocks; b += nw) {
+        double s = 0.0;
+        for (int i = lane; i < bl[b]; i += 32) s += nrm[bo[b] + i];
+        s = warp_sum(s);
+        const double mean = s / bl[b];
+        for (int i = lane; i < bl[b]; i += 32) nrm[bo[b] + i] = mean;
+    }
+}
+
+// d = 1 / sqrt(clamp(norm)); acc *= d
+static __global__ void inv_sqrt_clamp_kernel(const double *__restrict__ nrm, int len, double lo, double hi,
+                                      double *__restrict__ d, double *__restrict__ acc) {
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < len; i += gridDim.x * kBlock) {
+        double t = nrm[i];
+        if (t < lo) t = 1.0;
+        if (t > hi) t = hi;
+        const double s = 1.0 / sqrt(t);
+        d[i] = s;
+        acc[i] *= s;
+    }
+}
+
+template <typename F>
+__global__ void __launch_bounds__(kBlock) reduce_kernel(F f, int len, ReduceBuf rb, double *out) {
+    double red[1] = {0.0};
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < len; i += gridDim.x * kBlock) red[0] += f(i);
+    double tot[1];
+    if (grid_sum<1>(red, rb, kSiteMisc, tot)) {
+        if (threadIdx.x == 0) *out = tot[0];
+    }
+}
+
+template <typename F>
+__global__ void __launch_bounds__(kBlock) foreach_kernel(F f, int len) {
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < len; i += gridDim.x * kBlock) f(i);
+}
+
+}  // namespace scs

@@ -1,0 +1,243 @@
+"""Python binding of the C ABI in ``include/scs_gpu.h`` (argument marshalling only).
+
+Every step of the solve runs in the CUDA library ``libscs_gb300.so``; this
+module converts arrays, fills the C structs and calls the entry points of the
+same names.  There is no fallback: if the library is missing, loading fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libscs_gb300.so")
+
+SOLVED = 1
+SOLVED_INACCURATE = 2
+UNFINISHED = 0
+INFEASIBLE = -1
+UNBOUNDED = -2
+INFEASIBLE_INACCURATE = -3
+UNBOUNDED_INACCURATE = -4
+INVALID_INPUT = -10
+DEVICE_ERROR = -11
+TIMEOUT = -12
+NUMERICAL = -13
+UNSUPPORTED = -14
+
+
+class CSC(C.Structure):
+    _fields_ = [("m", C.c_int32), ("n", C.c_int32), ("colptr", C.POINTER(C.c_int64)),
+                ("rowidx", C.POINTER(C.c_int32)), ("val", C.POINTER(C.c_double))]
+
+
+class ConeC(C.Structure):
+    _fields_ = [("z", C.c_int32), ("l", C.c_int32), ("q", C.POINTER(C.c_int32)), ("nq", C.c_int32),
+                ("s", C.POINTER(C.c_int32)), ("ns", C.c_int32), ("ep", C.c_int32)]
+
+
+class Settings(C.Structure):
+    _fields_ = [("eps_pri", C.c_double), ("eps_dual", C.c_double), ("eps_gap", C.c_double),
+                ("eps_infeas", C.c_double), ("eps_unbdd", C.c_double), ("alpha", C.c_double),
+                ("cg_rate", C.c_double), ("cg_tol_rel", C.c_double), ("time_limit_s", C.c_double),
+                ("max_iters", C.c_int32), ("check_interval", C.c_int32), ("cg_max_iters", C.c_int32),
+                ("normalize", C.c_int32), ("scale_passes", C.c_int32), ("precision", C.c_int32),
+                ("use_graph", C.c_int32), ("verbose", C.c_int32), ("device", C.c_int32),
+                ("cuda_stream", C.c_void_p)]
+
+
+class Info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("cg_iters", C.c_int32),
+                ("matvecs", C.c_int32), ("pobj", C.c_double), ("dobj", C.c_double),
+                ("res_pri", C.c_double), ("res_dual", C.c_double), ("gap", C.c_double),
+                ("tau", C.c_double), ("kappa", C.c_double), ("setup_s", C.c_double),
+                ("solve_s", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib_handle = None
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib_handle
+    if _lib_handle is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} not built; run `python -m paper_1312_3039_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        P, D, I32, I64 = C.c_void_p, C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_int64)
+        L.scs_default_settings.argtypes = [C.POINTER(Settings)]
+        L.scs_default_settings.restype = None
+        L.scs_init.argtypes = [C.POINTER(CSC), D, D, C.POINTER(ConeC), C.POINTER(Settings), C.POINTER(I32)]
+        L.scs_init.restype = P
+        L.scs_solve.argtypes = [P, D, D, D, C.POINTER(Info)]
+        L.scs_solve.restype = I32
+        L.scs_warm_start.argtypes = [P, D, D, D]
+        L.scs_warm_start.restype = I32
+        L.scs_finish.argtypes = [P]
+        L.scs_finish.restype = None
+        L.scs_reset.argtypes = [P]
+        L.scs_reset.restype = I32
+        L.scs_iterate.argtypes = [P, I32, I32]
+        L.scs_iterate.restype = I32
+        L.scs_iterate_profiled.argtypes = [P, I32]
+        L.scs_iterate_profiled.restype = I32
+        L.scs_kernel_time.argtypes = [P, I32, D, I64]
+        L.scs_kernel_time.restype = I32
+        L.scs_get_iterates.argtypes = [P, D, D]
+        L.scs_get_iterates.restype = I32
+        L.scs_get_scaling.argtypes = [P, D, D, D, D]
+        L.scs_get_scaling.restype = I32
+        L.scs_dims.argtypes = [P, C.POINTER(I32), C.POINTER(I32), I64, I64]
+        L.scs_dims.restype = I32
+        L.scs_counters.argtypes = [P, C.POINTER(I32), I64]
+        L.scs_counters.restype = I32
+        L.scs_last_error.argtypes = []
+        L.scs_last_error.restype = C.c_char_p
+        _lib_handle = L
+    return _lib_handle
+
+
+def last_error() -> str:
+    return lib().scs_last_error().decode()
+
+
+def default_settings(**kw) -> Settings:
+    s = Settings()
+    lib().scs_default_settings(C.byref(s))
+    for k, v in kw.items():
+        if not hasattr(s, k):
+            raise AttributeError(k)
+        setattr(s, k, v)
+    return s
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+class ScsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"status {code}: {msg}")
+        self.code = code
+
+
+class Solver:
+    """One problem on the GPU: ``scs_init`` at construction, ``scs_finish`` at close."""
+
+    def __init__(self, A, b, c, cone, settings: Settings | None = None, **kw):
+        import scipy.sparse as sp
+        A = sp.csc_matrix(A)
+        self.m, self.n = A.shape
+        self._colptr = np.ascontiguousarray(A.indptr, dtype=np.int64)
+        self._rowidx = np.ascontiguousarray(A.indices, dtype=np.int32)
+        self._val = np.ascontiguousarray(A.data, dtype=np.float64)
+        self._b = np.ascontiguousarray(b, dtype=np.float64)
+        self._c = np.ascontiguousarray(c, dtype=np.float64)
+        self._q = np.ascontiguousarray(list(getattr(cone, "q", ())) or [0], dtype=np.int32)
+        self._s = np.ascontiguousarray(list(getattr(cone, "s", ())) or [0], dtype=np.int32)
+        csc = CSC(self.m, self.n, self._colptr.ctypes.data_as(C.POINTER(C.c_int64)),
+                  self._rowidx.ctypes.data_as(C.POINTER(C.c_int32)),
+                  self._val.ctypes.data_as(C.POINTER(C.c_double)))
+        kc = ConeC(int(cone.z), int(cone.l), self._q.ctypes.data_as(C.POINTER(C.c_int32)),
+                   len(getattr(cone, "q", ())), self._s.ctypes.data_as(C.POINTER(C.c_int32)),
+                   len(getattr(cone, "s", ())), int(cone.ep))
+        st = settings if settings is not None else default_settings()
+        for k, v in kw.items():
+            setattr(st, k, v)
+        self.settings = st
+        err = C.c_int32(0)
+        self._w = lib().scs_init(C.byref(csc), _dptr(self._b), _dptr(self._c), C.byref(kc), C.byref(st),
+                                 C.byref(err))
+        if not self._w:
+            raise ScsError(err.value, last_error())
+
+    def _check(self, rc):
+        if rc < 0 and rc <= INVALID_INPUT:
+            raise ScsError(rc, last_error())
+        return rc
+
+    def solve(self):
+        """Return ``(status, x, y, s, info_dict)``."""
+        x = np.empty(self.n)
+        y = np.empty(self.m)
+        s = np.empty(self.m)
+        info = Info()
+        st = lib().scs_solve(self._w, _dptr(x), _dptr(y), _dptr(s), C.byref(info))
+        self._check(st)
+        return st, x, y, s, info.as_dict()
+
+    def warm_start(self, x=None, y=None, s=None):
+        x = None if x is None else np.ascontiguousarray(x, dtype=np.float64)
+        y = None if y is None else np.ascontiguousarray(y, dtype=np.float64)
+        s = None if s is None else np.ascontiguousarray(s, dtype=np.float64)
+        return self._check(lib().scs_warm_start(self._w, _dptr(x), _dptr(y), _dptr(s)))
+
+    def reset(self):
+        return self._check(lib().scs_reset(self._w))
+
+    def iterate(self, iters, sync=True):
+        return self._check(lib().scs_iterate(self._w, int(iters), 1 if sync else 0))
+
+    def iterate_profiled(self, iters):
+        return self._check(lib().scs_iterate_profiled(self._w, int(iters)))
+
+    def kernel_time(self, kind):
+        ms = C.c_double(0)
+        n = C.c_int64(0)
+        self._check(lib().scs_kernel_time(self._w, int(kind), C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def iterates(self):
+        N = self.n + self.m + 1
+        u = np.empty(N)
+        v = np.empty(N)
+        self._check(lib().scs_get_iterates(self._w, _dptr(u), _dptr(v)))
+        return u, v
+
+    def scaling(self):
+        D = np.empty(self.m)
+        E = np.empty(self.n)
+        sg = C.c_double(0)
+        rh = C.c_double(0)
+        self._check(lib().scs_get_scaling(self._w, _dptr(D), _dptr(E), C.byref(sg), C.byref(rh)))
+        return D, E, sg.value, rh.value
+
+    def counters(self):
+        it = C.c_int32(0)
+        cg = C.c_int64(0)
+        self._check(lib().scs_counters(self._w, C.byref(it), C.byref(cg)))
+        return it.value, cg.value
+
+    def dims(self):
+        m, n = C.c_int32(0), C.c_int32(0)
+        nnz, by = C.c_int64(0), C.c_int64(0)
+        self._check(lib().scs_dims(self._w, C.byref(m), C.byref(n), C.byref(nnz), C.byref(by)))
+        return m.value, n.value, nnz.value, by.value
+
+    def close(self):
+        if getattr(self, "_w", None):
+            lib().scs_finish(self._w)
+            self._w = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def solve(A, b, c, cone, **kw):
+    """One-shot solve; returns ``(status, x, y, s, info)``."""
+    with Solver(A, b, c, cone, **kw) as S:
+        return S.solve()

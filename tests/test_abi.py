@@ -1,0 +1,78 @@
+"""The C-ABI library builds, loads and exports every entry point declared in
+include/scs_gpu.h; host-side validation rejects bad input before touching a
+GPU.  No compute call is made here (these run without a GPU)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "scs_gpu.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1312_3039_gb300 import build, scs
+    build.build()
+    return scs.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(scs_[a-z_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_functions()
+    assert len(names) >= 13
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_struct_layouts_match_header(tmp_path):
+    from paper_1312_3039_gb300 import scs
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include "scs_gpu.h"\nint main(void){printf("%zu %zu %zu %zu\\n",'
+                   'sizeof(scs_settings), sizeof(scs_info), sizeof(scs_csc), sizeof(scs_cone));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(t) for t in subprocess.check_output([str(exe)]).split()]
+    want = [ctypes.sizeof(scs.Settings), ctypes.sizeof(scs.Info), ctypes.sizeof(scs.CSC), ctypes.sizeof(scs.ConeC)]
+    assert got == want
+
+
+def test_default_settings(L):
+    from paper_1312_3039_gb300 import scs
+    s = scs.default_settings()
+    assert s.alpha == 1.5 and s.cg_rate == 1.5 and s.check_interval == 20
+    assert s.eps_pri == s.eps_dual == s.eps_gap == 1e-4
+    assert s.precision == 1 and s.normalize == 1
+
+
+@pytest.mark.parametrize("case", ["cone_rows", "row_index", "nonfinite", "alpha", "colptr"])
+def test_invalid_input_rejected_on_host(L, case):
+    from paper_1312_3039_gb300 import scs, synth
+    P = synth.lp(0, n=6, m=10, n_zero=2, density=0.5)
+    A, b, c, cone = P.A.copy(), P.b.copy(), P.c.copy(), P.cone
+    kw = {}
+    if case == "cone_rows":
+        cone = synth.Cone(z=2, l=7)
+    elif case == "row_index":
+        A = sp.csc_matrix(A)
+        A.indices[0] = 99
+    elif case == "nonfinite":
+        b[3] = np.nan
+    elif case == "alpha":
+        kw["alpha"] = 2.5
+    elif case == "colptr":
+        A = sp.csc_matrix(A)
+        A.indptr[2] = A.indptr[3] + 1
+    with pytest.raises(scs.ScsError) as ei:
+        scs.Solver(A, b, c, cone, **kw)
+    assert ei.value.code == scs.INVALID_INPUT

@@ -1,0 +1,190 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+* FP64 mode with a tight CG (cg_rate 0, cg_tol_rel 1e-13) follows the
+  oracle's exact-solve trajectory: ||u_gpu - u_orc|| / ||u_orc|| <= 1e-9 and
+  the same for v, at every one of the first 50 iterations (the iteration is
+  nonexpansive, Eq. "e-nonexpansive", so per-step solve errors of ~1e-13
+  cannot grow).
+* Full solves (FP64 and mixed FP32/FP64, the paper's CG schedule) reach the
+  Sec. 3.5 tests; the returned point is checked on the CPU against the
+  original data, and its objective against the oracle's within 1e-4
+  relative (plus the generator's known optimum).
+* Infeasible / unbounded problems return valid certificates (Sec. 2.2).
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import admm, cones
+from paper_1312_3039_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def scs():
+    from paper_1312_3039_gb300 import build, scs as _scs
+    build.build()
+    return _scs
+
+
+TIGHT = dict(precision=0, cg_rate=0.0, cg_tol_rel=1e-13, cg_max_iters=500)
+
+
+def trajectory_parity(scs, P, iters=50, tol=1e-9, **gpu_kw):
+    orc = admm.HSDSolver(P.A, P.b, P.c, P.cone, admm.Settings())
+    kw = dict(TIGHT)
+    kw.update(gpu_kw)
+    with scs.Solver(P.A, P.b, P.c, P.cone, **kw) as g:
+        D, E, sigma, rho = g.scaling()
+        np.testing.assert_allclose(D, orc.D, rtol=1e-12)
+        np.testing.assert_allclose(E, orc.E, rtol=1e-12)
+        assert abs(sigma - orc.sigma) <= 1e-12 * orc.sigma
+        assert abs(rho - orc.rho) <= 1e-12 * orc.rho
+        worst = 0.0
+        for k in range(iters):
+            g.iterate(1)
+            orc.step()
+            u, v = g.iterates()
+            eu = np.linalg.norm(u - orc.u) / np.linalg.norm(orc.u)
+            ev = np.linalg.norm(v - orc.v) / max(np.linalg.norm(orc.v), 1e-300)
+            worst = max(worst, eu, ev)
+            assert eu <= tol and ev <= tol, (k + 1, eu, ev)
+    return worst
+
+
+def test_lp_trajectory_fp64(scs):
+    trajectory_parity(scs, synth.lp(0))
+
+
+def test_lp_trajectory_fp64_alpha1_no_scaling(scs):
+    P = synth.lp(1)
+    orc_settings = admm.Settings(alpha=1.0, normalize=False)
+    orc = admm.HSDSolver(P.A, P.b, P.c, P.cone, orc_settings)
+    with scs.Solver(P.A, P.b, P.c, P.cone, alpha=1.0, normalize=0, **TIGHT) as g:
+        for k in range(50):
+            g.iterate(1)
+            orc.step()
+            u, v = g.iterates()
+            assert np.linalg.norm(u - orc.u) <= 1e-9 * np.linalg.norm(orc.u)
+            assert np.linalg.norm(v - orc.v) <= 1e-9 * max(np.linalg.norm(orc.v), 1e-300)
+
+
+def test_soc_exp_trajectory_fp64(scs):
+    P = synth.random_cone(11, n=40, cone=synth.Cone(z=5, l=20, q=(3, 7, 1, 2, 40), ep=8))
+    trajectory_parity(scs, P)
+
+
+def test_mixed_small_trajectory_fp64(scs):
+    trajectory_parity(scs, synth.mixed_small(0, scale=500))
+
+
+def test_plain_launch_path_matches_graph(scs):
+    """The un-graphed launch sequence gives the same iterates as the graph."""
+    P = synth.random_cone(12, n=30, cone=synth.Cone(z=3, l=15, q=(4, 5), ep=3))
+    with scs.Solver(P.A, P.b, P.c, P.cone, **TIGHT) as g1, \
+            scs.Solver(P.A, P.b, P.c, P.cone, use_graph=0, **TIGHT) as g2:
+        g1.iterate(30)
+        g2.iterate(30)
+        u1, v1 = g1.iterates()
+        u2, v2 = g2.iterates()
+        np.testing.assert_allclose(u1, u2, rtol=0, atol=1e-12 * np.linalg.norm(u1))
+
+
+def check_solution(P, x, y, s, eps=1e-4):
+    nb, nc = np.linalg.norm(P.b), np.linalg.norm(P.c)
+    assert np.linalg.norm(P.A @ x + s - P.b) <= eps * (1 + nb) * 1.0001
+    assert np.linalg.norm(P.A.T @ y + P.c) <= eps * (1 + nc) * 1.0001
+    cx, by = P.c @ x, P.b @ y
+    assert abs(cx + by) <= eps * (1 + abs(cx) + abs(by)) * 1.0001
+    assert cones.in_K(s, P.cone, 1e-7)
+    assert cones.in_Kdual(y, P.cone, 1e-7)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_lp_solve(scs, precision, seed):
+    P = synth.lp(seed)
+    ref = admm.solve(P.A, P.b, P.c, P.cone, admm.Settings())
+    st, x, y, s, info = scs.solve(P.A, P.b, P.c, P.cone, precision=precision)
+    assert st == scs.SOLVED, info
+    check_solution(P, x, y, s)
+    assert abs(info["pobj"] - ref.pobj) <= 1e-4 * (1 + abs(ref.pobj)) * 10
+    assert abs(info["pobj"] - P.p_star) <= 1e-3 * (1 + abs(P.p_star))
+    assert info["matvecs"] == 2 * info["iters"] + 2 * info["cg_iters"]
+    assert info["iters"] % 20 == 0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_mixed_small_solve(scs, precision):
+    P = synth.mixed_small(1, scale=500)
+    st, x, y, s, info = scs.solve(P.A, P.b, P.c, P.cone, precision=precision)
+    assert st == scs.SOLVED, info
+    check_solution(P, x, y, s)
+    assert abs(info["pobj"] - P.p_star) <= 2e-3 * (1 + abs(P.p_star))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_infeasible_certificate(scs, precision):
+    P = synth.lp(0, variant="infeasible")
+    st, x, y, s, info = scs.solve(P.A, P.b, P.c, P.cone, precision=precision)
+    assert st == scs.INFEASIBLE, info
+    assert abs(P.b @ y + 1.0) < 1e-9
+    assert np.linalg.norm(P.A.T @ y) <= 1e-3
+    assert cones.in_Kdual(y, P.cone, 1e-6)
+    assert np.all(np.isnan(x)) and np.all(np.isnan(s))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_unbounded_certificate(scs, precision):
+    P = synth.lp(0, variant="unbounded")
+    st, x, y, s, info = scs.solve(P.A, P.b, P.c, P.cone, precision=precision)
+    assert st == scs.UNBOUNDED, info
+    assert abs(P.c @ x + 1.0) < 1e-9
+    np.testing.assert_allclose(s, -(P.A @ x), atol=1e-9)
+    assert cones.in_K(s, P.cone, 1e-5)
+    assert np.all(np.isnan(y))
+
+
+def test_warm_start_from_solution(scs):
+    P = synth.lp(3)
+    with scs.Solver(P.A, P.b, P.c, P.cone, precision=0) as g:
+        st, x, y, s, info = g.solve()
+        assert st == scs.SOLVED
+        g.warm_start(x, y, s)
+        st2, x2, y2, s2, info2 = g.solve()
+        assert st2 == scs.SOLVED
+        assert info2["iters"] <= 20 < info["iters"]
+        # a third call starts cold again
+        st3, *_rest, info3 = g.solve()
+        assert info3["iters"] == info["iters"]
+
+
+def test_long_rows_and_empty_rows(scs):
+    """Rows longer than one shared-memory stream block (2048 nonzeros) take
+    the whole-CTA path; empty rows and columns go through every kernel."""
+    rng = np.random.default_rng(5)
+    n, m = 3000, 3200
+    A = sp.lil_matrix((m, n))
+    A[7, :] = rng.standard_normal(n)            # one dense row of 3000 entries
+    A[40, :2500] = rng.standard_normal(2500)
+    B = synth.bernoulli_sparse(rng, m, n, 0.002).tolil()
+    B[7, :] = 0
+    B[40, :] = 0
+    B[100:120, :] = 0                           # empty rows
+    A = sp.csc_matrix(A + B)
+    cone = synth.Cone(z=50, l=m - 50 - 12, q=(5, 4), ep=1)
+    P = synth.from_pair(A, cone, rng)
+    trajectory_parity(scs, P, iters=25)
+
+
+def test_tiny_and_ragged(scs):
+    """n = 1 and odd sizes that leave ragged tails in every kernel."""
+    for seed, (n, cone) in enumerate([(1, synth.Cone(z=1, l=2)),
+                                      (3, synth.Cone(l=5, q=(2,))),
+                                      (7, synth.Cone(z=2, l=3, q=(1, 3), ep=2)),
+                                      (257, synth.Cone(z=13, l=300, q=(33,), ep=5))]):
+        P = synth.random_cone(20 + seed, n=n, cone=cone, density=0.5 if n < 10 else 0.05)
+        trajectory_parity(scs, P, iters=20)
