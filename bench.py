@@ -206,7 +206,10 @@ def run_gb300(args):
     from paper_1312_3039_gb300 import scs
 
     P, desc = make_problem(args.workload, args.seed)
-    stream = torch.cuda.current_stream()
+    # a stream of our own (the default stream's handle is 0, which the library
+    # would replace by a private stream that torch's events do not see)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     common = dict(precision=1, device=local, cuda_stream=stream.cuda_stream)
 
     def barrier():

@@ -82,6 +82,8 @@ typedef struct {
     double eps_infeas, eps_unbdd;         /* Sec. 3.5 certificate tolerances            */
     double alpha;                         /* relaxation, Sec. 3.3; in (0, 2)            */
     double cg_rate;                       /* zeta^k = (1/k)^cg_rate; <= 0 disables it   */
+    double cg_adapt;                      /* and at cg_adapt * ||(u^k, v^k) - (u^k-1, v^k-1)||
+                                             (0 disables; see scs_default_settings)     */
     double cg_tol_rel;                    /* CG also stops at cg_tol_rel * ||u^k + v^k|| */
     double time_limit_s;                  /* <= 0: none                                 */
     int32_t max_iters;
@@ -113,7 +115,8 @@ typedef struct {
 
 typedef struct scs_work scs_work;
 
-/* Fill *s with defaults: eps 1e-4, alpha 1.5, cg_rate 1.5, cg_tol_rel 0,
+/* Fill *s with defaults: eps 1e-4, alpha 1.5, cg_rate 1.5, cg_adapt 0.3,
+ * cg_tol_rel 0,
  * max_iters 10000, check_interval 20, cg_max_iters 50, normalize 1,
  * scale_passes 10, precision 1, use_graph 1, device 0. */
 void scs_default_settings(scs_settings *s);

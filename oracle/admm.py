@@ -21,6 +21,13 @@ Follows, in order:
         preconditioned CG warm-started from the previous z_x, stopped when
         the residual is below zeta^k = (1/k)^cg_rate (Sec. 3.3 Eq.
         "e-approx-proj-resid", Sec. 6.1), then z_y = w_y + A z_x.
+        Reading: the tolerance is also capped at cg_adapt times the length
+        ||(u^k - u^(k-1), v^k - v^(k-1))|| of the previous ADMM step (after a
+        warm start: max(eps) * ||(u0, v0)||).  A cap below zeta^k keeps the
+        tolerances summable, as Sec. 3.3 requires, while tracking the
+        accuracy the iteration has reached: with the absolute schedule alone
+        a certificate test that needs ~1e-6 relative accuracy is not met
+        before k ~ 1e4, and a warm start is undone by the loose first solves.
   * Termination (Sec. 3.5) on the scaled data (Sec. 5, "Scaled termination
     criteria"), every ``check_interval`` iterations, tested in the order
     optimality, primal infeasibility, dual infeasibility.
@@ -65,6 +72,7 @@ class Settings:
     scale_passes: int = 10
     linsys: str = "direct"          # "direct" | "indirect"
     cg_rate: float = 1.5            # zeta^k = (1/k)^cg_rate; <= 0 disables it
+    cg_adapt: float = 0.3           # also at most cg_adapt * (last ADMM step length); 0 disables
     cg_tol_rel: float = 0.0         # floor: cg_tol_rel * ||w||
     cg_max_iters: int = 1000
 
@@ -132,6 +140,7 @@ class HSDSolver:
         self.u[-1] = 1.0
         self.v[-1] = 1.0
         self.k = 0
+        self.dstep = math.inf
 
     def warm_start(self, x, y, s):
         """Sec. 4.2: u0 = (x, y, 1), v0 = (0, s, 0), mapped into the scaled
@@ -141,6 +150,9 @@ class HSDSolver:
                                  self.rho * np.asarray(y) / self.D, [1.0]])
         self.v = np.concatenate([np.zeros(n), self.sigma * self.D * np.asarray(s), [0.0]])
         self.k = 0
+        st = self.st
+        self.dstep = max(st.eps_pri, st.eps_dual, st.eps_gap) * float(
+            np.linalg.norm(np.concatenate([self.u, self.v])))
 
     # -- linear system ----------------------------------------------------
     def _solve_M(self, r, k):
@@ -156,9 +168,13 @@ class HSDSolver:
             tol = 1e-14 * max(np.linalg.norm(t), 1e-300)
             zx = self._pcg(t, np.zeros(n), tol, max(self.st.cg_max_iters, 10 * n))
         else:
-            tol = 0.0
+            tol = math.inf
             if self.st.cg_rate > 0:
                 tol = (1.0 / k) ** self.st.cg_rate
+            if self.st.cg_adapt > 0:
+                tol = min(tol, self.st.cg_adapt * self.dstep)
+            if not math.isfinite(tol):
+                tol = 0.0
             tol = max(tol, self.st.cg_tol_rel * self._wnorm)
             zx = self._pcg(t, self.z_prev, tol, self.st.cg_max_iters)
             self.z_prev = zx.copy()
@@ -223,6 +239,7 @@ class HSDSolver:
         ubar = a * ut + (1.0 - a) * self.u
         u_new = self.proj_C(ubar - self.v)
         v_new = self.v - ubar + u_new
+        self.dstep = float(np.sqrt(np.sum((u_new - self.u) ** 2) + np.sum((v_new - self.v) ** 2)))
         self.u, self.v = u_new, v_new
 
     # -- termination (Sec. 3.5 and Sec. 5) -----------------------------------

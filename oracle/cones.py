@@ -184,10 +184,13 @@ def proj_exp(v):
     den = rho * rho - rho + 1.0
     y = ((rho - 1.0) * r0 + s0) / den
     mu = (r0 - rho * s0) / den
-    ray_p = np.array([rho, 1.0, math.exp(rho)])
-    ray_d = np.array([-1.0, rho - 1.0, math.exp(-rho)])
-    err_p = (abs(rho - 1.0) * abs(r0) + abs(s0)) / den * np.linalg.norm(ray_p)
-    err_d = (abs(r0) + abs(rho) * abs(s0)) / den * np.linalg.norm(ray_d) + math.sqrt(r0 * r0 + s0 * s0 + t0 * t0)
+    with np.errstate(over="ignore"):
+        ray_p = np.array([rho, 1.0, np.exp(rho)])
+        ray_d = np.array([-1.0, rho - 1.0, np.exp(-rho)])
+    with np.errstate(over="ignore", invalid="ignore"):
+        err_p = (abs(rho - 1.0) * abs(r0) + abs(s0)) / den * np.sqrt(ray_p @ ray_p)
+        err_d = ((abs(r0) + abs(rho) * abs(s0)) / den * np.sqrt(ray_d @ ray_d)
+                 + math.sqrt(r0 * r0 + s0 * s0 + t0 * t0))
     if err_p <= err_d:
         return y * ray_p
     return np.array([r0, s0, t0]) + mu * ray_d

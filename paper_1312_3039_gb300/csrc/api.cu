@@ -139,6 +139,7 @@ int validate_settings(const scs_settings &s) {
         set_error("iteration counts out of range");
         return SCS_INVALID_INPUT;
     }
+    if (!(s.cg_adapt >= 0.0) || !(s.cg_tol_rel >= 0.0)) { set_error("negative CG tolerance setting"); return SCS_INVALID_INPUT; }
     if (s.precision != 0 && s.precision != 1) { set_error("precision must be 0 or 1"); return SCS_INVALID_INPUT; }
     return 0;
 }
@@ -173,6 +174,7 @@ void scs_default_settings(scs_settings *s) {
     s->eps_infeas = s->eps_unbdd = 1e-4;
     s->alpha = 1.5;
     s->cg_rate = 1.5;
+    s->cg_adapt = 0.3;
     s->cg_tol_rel = 0.0;
     s->time_limit_s = 0.0;
     s->max_iters = 10000;

@@ -26,7 +26,8 @@ struct Scalars {
     double gamma;       // h^T z / (1 + h^T p)
     double hp1;         // 1 + h^T p   (Sec. 4.1, cached)
     // settings mirrored on the device
-    double cg_rate, cg_tol_rel, relax;
+    double cg_rate, cg_adapt, cg_tol_rel, relax;
+    double dstep;       // ||(u, v) - (u, v)_previous|| of the last ADMM step
     // termination quantities (scaled problem, Sec. 5)
     double pri2, unb2, bty, dual2, inf2, ctx;
     double res_pri, res_dual, gap, pobj, dobj, tau, kappa;
@@ -109,7 +110,7 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NV], ReduceBuf rb, int site
 // grid-sum call sites (each has its own arrival counter)
 enum Site : int {
     kSiteAInit = 0, kSiteAtInit, kSiteACG, kSiteAtCG, kSiteCGUpd, kSiteSmw,
-    kSiteChkA, kSiteChkAt, kSiteMisc, kSiteMisc2, kSiteCount
+    kSiteChkA, kSiteChkAt, kSiteProj, kSiteMisc, kSiteMisc2, kSiteCount
 };
 
 }  // namespace scs

@@ -15,7 +15,7 @@ namespace scs {
 //   Kexp* = closure{(u, v, w): u < 0, -u e^(v/u) <= e w}
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ bool exp_member(double x, double y, double z) {
+__host__ __device__ __forceinline__ bool exp_member(double x, double y, double z) {
     if (y > 0.0) {
         const double q = x / y;
         return q < 700.0 && y * exp(q) <= z;
@@ -23,7 +23,7 @@ __device__ __forceinline__ bool exp_member(double x, double y, double z) {
     return y == 0.0 && x <= 0.0 && z >= 0.0;
 }
 
-__device__ __forceinline__ bool exp_dual_member(double u, double v, double w) {
+__host__ __device__ __forceinline__ bool exp_dual_member(double u, double v, double w) {
     if (u < 0.0) {
         const double q = v / u;
         return q < 700.0 && -u * exp(q) <= M_E * w;
@@ -39,7 +39,7 @@ __device__ __forceinline__ bool exp_dual_member(double u, double v, double w) {
 // and the projection is the rho where y e^rho - mu e^-rho = t0.
 struct ExpCurve {
     double r0, s0, t0;
-    __device__ __forceinline__ void eval(double rho, double &h, double &dh) const {
+    __host__ __device__ __forceinline__ void eval(double rho, double &h, double &dh) const {
         const double den = rho * rho - rho + 1.0;
         const double ep = exp(rho), em = exp(-rho);
         const double a = (rho - 1.0) * r0 + s0;        // y * den
@@ -51,70 +51,109 @@ struct ExpCurve {
     }
 };
 
+// The same curve in FP32 for the first, coarse root search.
+struct ExpCurveF {
+    float r0, s0, t0;
+    __host__ __device__ __forceinline__ void eval(float rho, float &h, float &dh) const {
+        const float den = rho * rho - rho + 1.0f;
+        const float ep = expf(rho), em = expf(-rho);
+        const float a = (rho - 1.0f) * r0 + s0;
+        const float c = r0 - rho * s0;
+        const float num = a * ep - c * em;
+        const float dnum = ep * (rho * r0 + s0) + em * (r0 - rho * s0 + s0);
+        h = num / den - t0;
+        dh = (dnum * den - num * (2.0f * rho - 1.0f)) / (den * den);
+        // inside the bracket y > 0 and mu > 0, so an overflowed h has the sign of rho
+        if (!isfinite(h)) h = rho > 0.0f ? INFINITY : -INFINITY;
+    }
+};
+
 // Euclidean projection of (r0, s0, t0) onto Kexp.
-__device__ inline void proj_exp(double r0, double s0, double t0, double &px, double &py, double &pz) {
+__host__ __device__ inline void proj_exp(double r0, double s0, double t0, double &px, double &py, double &pz) {
     if (exp_member(r0, s0, t0)) { px = r0; py = s0; pz = t0; return; }
     if (exp_dual_member(-r0, -s0, -t0)) { px = 0.0; py = 0.0; pz = 0.0; return; }
     if (r0 <= 0.0 && s0 <= 0.0) { px = r0; py = 0.0; pz = fmax(t0, 0.0); return; }
-    const ExpCurve f{r0, s0, t0};
-    // bracket: h < 0 where y -> 0 (rho = 1 - s0/r0 when r0 > 0, else -inf),
-    //          h > 0 where mu -> 0 (rho = r0/s0 when s0 > 0, else +inf)
-    double lo = 0.0, hi = 0.0, h, dh;
-    const bool lo_open = !(r0 > 0.0), hi_open = !(s0 > 0.0);
-    if (!lo_open) lo = 1.0 - s0 / r0;
-    if (!hi_open) hi = r0 / s0;
+    // the projection is positively homogeneous: solve for v / ||v||_inf
+    const double nrm = fmax(fabs(r0), fmax(fabs(s0), fabs(t0)));
+    const double r = r0 / nrm, s = s0 / nrm, t = t0 / nrm;
+    // bracket: h < 0 where y -> 0 (rho = 1 - s/r when r > 0, else -inf),
+    //          h > 0 where mu -> 0 (rho = r/s when s > 0, else +inf)
+    const bool lo_open = !(r > 0.0), hi_open = !(s > 0.0);
+    double lo = lo_open ? 0.0 : 1.0 - s / r;
+    double hi = hi_open ? 0.0 : r / s;
+    // 1. coarse search in FP32: close the open end by doubling steps, bisect
+    //    while the bracket is wide (h grows like e^|rho|), then Newton
+    const ExpCurveF ff{(float)r, (float)s, (float)t};
+    float h, dh;
     if (lo_open) {
-        double step = 1.0;
-        lo = hi - step;
-        for (int it = 0; it < 80; ++it) {
-            f.eval(lo, h, dh);
-            if (h < 0.0) break;
-            step *= 2.0;
-            lo = hi - step;
+        float step = 1.0f;
+        for (int it = 0; it < 60; ++it) {
+            ff.eval((float)hi - step, h, dh);
+            if (h < 0.0f) break;
+            step *= 2.0f;
         }
+        lo = (double)((float)hi - step);
     }
     if (hi_open) {
-        double step = 1.0;
-        hi = lo + step;
-        for (int it = 0; it < 80; ++it) {
-            f.eval(hi, h, dh);
-            if (h > 0.0) break;
-            step *= 2.0;
-            hi = lo + step;
+        float step = 1.0f;
+        for (int it = 0; it < 60; ++it) {
+            ff.eval((float)lo + step, h, dh);
+            if (h > 0.0f) break;
+            step *= 2.0f;
         }
+        hi = (double)((float)lo + step);
     }
-    // safeguarded Newton: keep the sign bracket, bisect when a Newton step
-    // leaves it
-    double rho = 0.5 * (lo + hi);
-    for (int it = 0; it < 200; ++it) {
-        f.eval(rho, h, dh);
-        if (h == 0.0) break;
-        if (h < 0.0) lo = rho; else hi = rho;
-        double nr = rho - h / dh;
-        if (!(nr > lo && nr < hi)) nr = 0.5 * (lo + hi);
-        const double tol = 1e-15 * fmax(1.0, fabs(nr));
-        if (fabs(nr - rho) <= tol || hi - lo <= tol) { rho = nr; break; }
-        rho = nr;
+    float flo = (float)lo, fhi = (float)hi, frho = 0.5f * (flo + fhi);
+    for (int it = 0; it < 120; ++it) {
+        ff.eval(frho, h, dh);
+        if (h == 0.0f) break;
+        if (h < 0.0f) flo = frho; else fhi = frho;
+        const float tol = 2e-7f * fmaxf(1.0f, fabsf(frho));
+        if (fhi - flo <= 1.0f && isfinite(dh) && dh > 0.0f) {
+            const float step = h / dh;
+            if (fabsf(step) <= tol) { frho -= step; break; }      // converged
+            const float c = frho - step;
+            if (c > flo && c < fhi) { frho = c; continue; }
+        }
+        frho = 0.5f * (flo + fhi);
+        if (fhi - flo <= tol) break;
+    }
+    // 2. FP64 Newton from the FP32 root, kept inside the (FP64) sign bracket
+    const ExpCurve f{r, s, t};
+    double rho = (double)frho, hd, dhd;
+    if (!(rho > lo && rho < hi)) rho = 0.5 * (lo + hi);
+    for (int it = 0; it < 80; ++it) {
+        f.eval(rho, hd, dhd);
+        if (hd == 0.0) break;
+        if (hd < 0.0) lo = rho; else hi = rho;
+        const double tol = 1e-15 * fmax(1.0, fabs(rho));
+        if (isfinite(hd) && isfinite(dhd) && dhd > 0.0) {
+            const double step = hd / dhd;
+            if (fabs(step) <= tol) { rho -= step; break; }        // converged
+            const double c = rho - step;
+            if (c > lo && c < hi) { rho = c; continue; }
+        }
+        rho = 0.5 * (lo + hi);
+        if (hi - lo <= tol) break;
     }
     // return whichever of the two equal expressions rounds better: the
     // primal ray y (rho, 1, e^rho) or v + mu (-1, rho - 1, e^-rho)
     const double den = rho * rho - rho + 1.0;
-    const double y = ((rho - 1.0) * r0 + s0) / den;
-    const double mu = (r0 - rho * s0) / den;
+    const double y = ((rho - 1.0) * r + s) / den;
+    const double mu = (r - rho * s) / den;
     const double ep = exp(rho), em = exp(-rho);
-    const double err_p = (fabs(rho - 1.0) * fabs(r0) + fabs(s0)) / den * sqrt(rho * rho + 1.0 + ep * ep);
-    const double err_d = (fabs(r0) + fabs(rho) * fabs(s0)) / den *
-                             sqrt(1.0 + (rho - 1.0) * (rho - 1.0) + em * em) +
-                         sqrt(r0 * r0 + s0 * s0 + t0 * t0);
+    const double err_p = (fabs(rho - 1.0) * fabs(r) + fabs(s)) / den * sqrt(rho * rho + 1.0 + ep * ep);
+    const double err_d = (fabs(r) + fabs(rho) * fabs(s)) / den * sqrt(1.0 + (rho - 1.0) * (rho - 1.0) + em * em) +
+                         sqrt(r * r + s * s + t * t);
     if (err_p <= err_d) {
-        px = y * rho; py = y; pz = y * ep;
+        px = nrm * (y * rho); py = nrm * y; pz = nrm * (y * ep);
     } else {
-        px = r0 - mu; py = s0 + mu * (rho - 1.0); pz = t0 + mu * em;
+        px = nrm * (r - mu); py = nrm * (s + mu * (rho - 1.0)); pz = nrm * (t + mu * em);
     }
 }
 
 // Pi_{Kexp*}(w) = w + Pi_{Kexp}(-w)
-__device__ inline void proj_exp_dual(double u, double v, double w, double &pu, double &pv, double &pw) {
+__host__ __device__ inline void proj_exp_dual(double u, double v, double w, double &pu, double &pv, double &pw) {
     double a, b, c;
     proj_exp(-u, -v, -w, a, b, c);
     pu = u + a; pv = v + b; pw = w + c;

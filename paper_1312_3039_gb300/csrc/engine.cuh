@@ -82,7 +82,10 @@ class Engine : public EngineBase {
         v[N_ - 1] = 0.0;
         SCS_CUDA(cudaMemcpyAsync(u_, u.data(), sizeof(double) * N_, cudaMemcpyHostToDevice, stream_));
         SCS_CUDA(cudaMemcpyAsync(v_, v.data(), sizeof(double) * N_, cudaMemcpyHostToDevice, stream_));
-        reset_counters();
+        // the warm start is taken to be about as accurate as the tolerances
+        double nrm = 0.0;
+        for (int i = 0; i < N_; ++i) nrm += u[i] * u[i] + v[i] * v[i];
+        reset_counters(std::max(st_.eps_pri, std::max(st_.eps_dual, st_.eps_gap)) * std::sqrt(nrm));
         SCS_CUDA(cudaStreamSynchronize(stream_));
         warm_pending_ = true;
         return 0;
@@ -265,11 +268,6 @@ class Engine : public EngineBase {
         int32_t *at_rowptr = upload(P.at_rowptr), *at_col = upload(P.at_col);
         double *a_val64 = upload(P.a_val), *at_val64 = upload(P.at_val);
         int32_t *a_blk = upload(blkA), *at_blk = upload(blkAt);
-        const int max_blocks = std::max({(int)blkA.size(), (int)blkAt.size(), sms_ * 8, 1});
-        rb_.partials = dalloc<double>(static_cast<size_t>(max_blocks) * kMaxRed);
-        rb_.counter = dalloc<unsigned>(kSiteCount);
-        SCS_CUDA(cudaMemsetAsync(rb_.counter, 0, sizeof(unsigned) * kSiteCount, stream_));
-        S_ = dalloc<Scalars>(1);
 
         // vectors
         u_ = dalloc<double>(N_);
@@ -322,10 +320,19 @@ class Engine : public EngineBase {
         K.nb_elem = (n_ + K.z + K.l + kBlock - 1) / kBlock;
         if (K.nb_elem < 1) K.nb_elem = 1;
         K.nb_soc = (K.nq + kWarps - 1) / kWarps;
-        K.nb_exp = (K.ep + kBlock - 1) / kBlock;
+        K.nb_exp = (K.ep + kExpPerCta - 1) / kExpPerCta;
         cone_ = K;
         const int32_t *d_avg_off = upload(avg_off), *d_avg_len = upload(avg_len);
         const int navg = static_cast<int>(avg_off.size());
+
+        // partial sums of the grid reductions: one slot group per CTA of the
+        // widest reducing launch (SpMV stream blocks, the projection grid, or
+        // the capped grid-stride kernels)
+        rb_cap_ = std::max({(int)blkA.size(), (int)blkAt.size(), sms_ * 8, proj_grid(), 1});
+        rb_.partials = dalloc<double>(static_cast<size_t>(rb_cap_) * kMaxRed);
+        rb_.counter = dalloc<unsigned>(kSiteCount);
+        SCS_CUDA(cudaMemsetAsync(rb_.counter, 0, sizeof(unsigned) * kSiteCount, stream_));
+        S_ = dalloc<Scalars>(1);
 
         // ---- equilibration, Sec. 5 (FP64) ----
         if (st_.normalize) {
@@ -433,6 +440,8 @@ class Engine : public EngineBase {
         // cached p = M^-1 h solved tightly (Sec. 4.1): CG from zero with the
         // right-hand side r = h, i.e. u = (c^, b^, 0), v = 0
         sh.cg_rate = 0.0;
+        sh.cg_adapt = 0.0;
+        sh.dstep = INFINITY;
         sh.cg_tol_rel = std::is_same<T, double>::value ? 1e-14 : 1e-7;
         sh.cg_max = std::max(10 * st_.cg_max_iters, 500);
         SCS_CUDA(cudaMemcpyAsync(S_, &sh, sizeof(Scalars), cudaMemcpyHostToDevice, stream_));
@@ -469,6 +478,7 @@ class Engine : public EngineBase {
         SCS_CUDA(cudaStreamSynchronize(stream_));
         sh.hp1 = 1.0 + hp;
         sh.cg_rate = st_.cg_rate;
+        sh.cg_adapt = st_.cg_adapt;
         sh.cg_tol_rel = st_.cg_tol_rel;
         sh.cg_max = st_.cg_max_iters;
         SCS_CUDA(cudaMemcpy(S_, &sh, sizeof(Scalars), cudaMemcpyHostToDevice));
@@ -483,10 +493,11 @@ class Engine : public EngineBase {
         foreach_kernel<<<grid_for(len), kBlock, 0, stream_>>>([=] __device__(int i) { d[i] = val; }, len);
     }
 
-    void reset_counters() {
-        // k = 0, cg_total = 0, status = 0 (fields of the device scalars)
+    void reset_counters(double dstep = INFINITY) {
+        // k = 0, cg_total = 0, status = 0, last step length (fields of the device scalars)
         const int zero = 0;
         const int64_t zero64 = 0;
+        SCS_CUDA(cudaMemcpyAsync(&S_->dstep, &dstep, sizeof(double), cudaMemcpyHostToDevice, stream_));
         SCS_CUDA(cudaMemcpyAsync(&S_->k, &zero, sizeof(int), cudaMemcpyHostToDevice, stream_));
         SCS_CUDA(cudaMemcpyAsync(&S_->status, &zero, sizeof(int), cudaMemcpyHostToDevice, stream_));
         SCS_CUDA(cudaMemcpyAsync(&S_->cg_total, &zero64, sizeof(int64_t), cudaMemcpyHostToDevice, stream_));
@@ -515,19 +526,29 @@ class Engine : public EngineBase {
     }
 
     // ------------------------------------------------------------ launches
+    int proj_grid() const { return cone_.nb_elem + cone_.nb_soc + cone_.nb_exp; }
+    // every reducing launch must fit the partial-sum buffer
+    void guard(int grid) const {
+        if (grid > rb_cap_ || grid < 1) throw CudaError("reduction grid exceeds its buffer", SCS_DEVICE_ERROR);
+    }
+
     void launch_K1() {
+        guard(A_.nblk);
         EpiAInit<T> e{u_, v_, b_, yacc_, S_, n_, N_, 0.0};
         spmv_stream_kernel<T, T, T, EpiAInit<T>><<<A_.nblk, kBlock, 0, cur_>>>(A_, z_, e, rb_);
     }
     void launch_K2(CondHandle h) {
+        guard(At_.nblk);
         EpiAtInit<T> e{u_, v_, c_, diag_, z_, r_, pv_, S_, h, N_, 0.0};
         spmv_stream_kernel<T, T, T, EpiAtInit<T>><<<At_.nblk, kBlock, 0, cur_>>>(At_, yacc_, e, rb_);
     }
     void launch_K3() {
+        guard(A_.nblk);
         EpiACG<T> e{q_, S_};
         spmv_stream_kernel<T, T, T, EpiACG<T>><<<A_.nblk, kBlock, 0, cur_>>>(A_, pv_, e, rb_);
     }
     void launch_K4() {
+        guard(At_.nblk);
         EpiAtCG<T> e{diag_, z_, r_, pv_, S_, T(0)};
         spmv_stream_kernel<T, T, T, EpiAtCG<T>><<<At_.nblk, kBlock, 0, cur_>>>(At_, q_, e, rb_);
     }
@@ -540,10 +561,13 @@ class Engine : public EngineBase {
     }
     void launch_K7() {
         ProjArgs<T> a{n_, m_, N_, u_, v_, p_, z_, yacc_, S_};
-        const int grid = cone_.nb_elem + cone_.nb_soc + cone_.nb_exp;
-        relax_project_kernel<T><<<grid, kBlock, 0, cur_>>>(a, cone_);
+        const int grid = proj_grid();
+        guard(grid);
+        relax_project_kernel<T><<<grid, kBlock, 0, cur_>>>(a, cone_, rb_);
     }
     void launch_check() {
+        guard(A64_.nblk);
+        guard(At64_.nblk);
         EpiChkA ea{u_, v_, b_, D_, ax_, S_, n_, N_, 0.0};
         spmv_stream_kernel<double, double, double, EpiChkA><<<A64_.nblk, kBlock, 0, stream_>>>(A64_, u_, ea, rb_);
         EpiChkAt eb{u_, v_, c_, E_, S_, N_, 0.0};
@@ -641,6 +665,7 @@ class Engine : public EngineBase {
     Csr<double> A64_{}, At64_{};
     ConeDev cone_{};
     ReduceBuf rb_{};
+    int rb_cap_ = 0;
     Scalars *S_ = nullptr, *Sh_ = nullptr;
     double *u_ = nullptr, *v_ = nullptr, *b_ = nullptr, *c_ = nullptr, *D_ = nullptr, *E_ = nullptr;
     double *p_ = nullptr, *ax_ = nullptr, *out_ = nullptr;

@@ -95,8 +95,12 @@ struct EpiAtInit {
     }
     __device__ void finish(const double (&t)[NV]) {
         const double ww = t[3] + S->ww_y + wtau * wtau;
-        double tol = 0.0;
+        // zeta^k = (1/k)^cg_rate (Sec. 6.1), capped at cg_adapt times the last
+        // ADMM step length, floored at cg_tol_rel ||w||
+        double tol = INFINITY;
         if (S->cg_rate > 0.0) tol = pow(1.0 / (double)(S->k + 1), S->cg_rate);
+        if (S->cg_adapt > 0.0) tol = fmin(tol, S->cg_adapt * S->dstep);
+        if (!isfinite(tol)) tol = 0.0;
         tol = fmax(tol, S->cg_tol_rel * sqrt(ww));
         S->tol = tol;
         S->wtau = wtau;
@@ -217,10 +221,14 @@ __global__ void __launch_bounds__(kBlock) smw_kernel(int n, int m, const double 
 
 // ---------------------------------------------------------------------------
 // K7: relax, project onto C = R^n x K* x R+, update v  (one launch)
-//   block ranges: [0, nb_elem)      x-part, zero rows, nonnegative rows, tau
+//   block ranges: [0, nb_exp)       exponential triples, kExpPerCta per CTA
+//                                   (long FP64 chains: started first, spread
+//                                   over many SMs)
 //                 [.., + nb_soc)    one warp per second-order block
-//                 [.., + nb_exp)    one thread per exponential triple
+//                 [.., + nb_elem)   x-part, zero rows, nonnegative rows, tau
 // ---------------------------------------------------------------------------
+constexpr int kExpPerCta = 64;
+
 struct ConeDev {
     int z, l;              // zero and nonnegative row counts
     int nq;                // second-order blocks
@@ -250,82 +258,99 @@ __device__ __forceinline__ double relaxed(const ProjArgs<T> &a, int idx, double 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBlock) relax_project_kernel(ProjArgs<T> a, ConeDev K) {
+__global__ void __launch_bounds__(kBlock) relax_project_kernel(ProjArgs<T> a, ConeDev K, ReduceBuf rb) {
     const double gamma = a.S->gamma;
     const double alpha = a.S->relax;
     const int bid = blockIdx.x;
-    if (bid < K.nb_elem) {
+    double dd = 0.0;        // squared length of this thread's part of the step
+    if (bid < K.nb_exp) {
+        const int tri = bid * kExpPerCta + threadIdx.x;
+        if (threadIdx.x < kExpPerCta && tri < K.ep) {
+            const int off = a.n + K.exp_off + 3 * tri;
+            double t[3], uo[3], vo[3], up[3];
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                uo[e] = a.u[off + e];
+                vo[e] = a.v[off + e];
+                t[e] = relaxed(a, off + e, gamma, alpha) - vo[e];
+            }
+            proj_exp_dual(t[0], t[1], t[2], up[0], up[1], up[2]);
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                a.u[off + e] = up[e];
+                a.v[off + e] = up[e] - t[e];
+                dd += (up[e] - uo[e]) * (up[e] - uo[e]) + (up[e] - t[e] - vo[e]) * (up[e] - t[e] - vo[e]);
+            }
+        }
+    } else if (bid - K.nb_exp < K.nb_soc) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int blk = (bid - K.nb_exp) * kWarps + warp;
+        if (blk < K.nq) {
+            const int off = a.n + K.q_off[blk];
+            const int len = K.q_len[blk];
+            // t = u_bar - v over the block; projection onto SOC (self-dual)
+            double t0 = 0.0, xx = 0.0;
+            for (int e = lane; e < len; e += 32) {
+                const double t = relaxed(a, off + e, gamma, alpha) - a.v[off + e];
+                if (e == 0) t0 = t; else xx += t * t;
+            }
+            xx = warp_sum(xx);
+            t0 = __shfl_sync(0xffffffffu, t0, 0);
+            const double nx = sqrt(xx);
+            double head, tail;                  // projection = (head, tail * x)
+            if (nx <= t0) { head = t0; tail = 1.0; }
+            else if (nx <= -t0) { head = 0.0; tail = 0.0; }
+            else {
+                head = 0.5 * (t0 + nx);
+                tail = head / nx;
+            }
+            for (int e = lane; e < len; e += 32) {
+                const double uo = a.u[off + e], vo = a.v[off + e];
+                const double t = relaxed(a, off + e, gamma, alpha) - vo;
+                const double up = e == 0 ? head : tail * t;
+                a.u[off + e] = up;
+                a.v[off + e] = up - t;
+                dd += (up - uo) * (up - uo) + (up - t - vo) * (up - t - vo);
+            }
+        }
+    } else {
+        const int ebid = bid - K.nb_exp - K.nb_soc;
         const int nlin = a.n + K.z + K.l;
-        const int idx = bid * kBlock + threadIdx.x;
+        const int idx = ebid * kBlock + threadIdx.x;
         if (idx < nlin) {
             const double ub = relaxed(a, idx, gamma, alpha);
+            const double uo = a.u[idx];
             if (idx < a.n) {
                 a.u[idx] = ub;                       // R^n: identity, v_x stays 0
+                dd += (ub - uo) * (ub - uo);
             } else {
-                const double t = ub - a.v[idx];
+                const double vo = a.v[idx];
+                const double t = ub - vo;
                 const double up = (idx < a.n + K.z) ? t : fmax(t, 0.0);   // K* of {0} is R
                 a.u[idx] = up;
                 a.v[idx] = up - t;
+                dd += (up - uo) * (up - uo) + (up - t - vo) * (up - t - vo);
             }
         }
-        if (bid == 0 && threadIdx.x == 0) {
+        if (ebid == 0 && threadIdx.x == 0) {
             // tau: u~_tau = w_tau + gamma
             const int it = a.N - 1;
             const double ut = a.S->wtau + gamma;
-            const double ub = alpha * ut + (1.0 - alpha) * a.u[it];
-            const double t = ub - a.v[it];
+            const double uo = a.u[it], vo = a.v[it];
+            const double ub = alpha * ut + (1.0 - alpha) * uo;
+            const double t = ub - vo;
             const double up = fmax(t, 0.0);
             a.u[it] = up;
             a.v[it] = up - t;
+            dd += (up - uo) * (up - uo) + (up - t - vo) * (up - t - vo);
+        }
+    }
+    double red[1] = {dd}, tot[1];
+    if (grid_sum<1>(red, rb, kSiteProj, tot)) {
+        if (threadIdx.x == 0) {
+            a.S->dstep = sqrt(tot[0]);
             a.S->k += 1;
         }
-        return;
-    }
-    const int sb = bid - K.nb_elem;
-    if (sb < K.nb_soc) {
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int blk = sb * kWarps + warp;
-        if (blk >= K.nq) return;
-        const int off = a.n + K.q_off[blk];
-        const int len = K.q_len[blk];
-        // t = u_bar - v over the block; project onto SOC (self-dual)
-        double t0 = 0.0, xx = 0.0;
-        for (int e = lane; e < len; e += 32) {
-            const double t = relaxed(a, off + e, gamma, alpha) - a.v[off + e];
-            if (e == 0) t0 = t; else xx += t * t;
-        }
-        xx = warp_sum(xx);
-        t0 = __shfl_sync(0xffffffffu, t0, 0);
-        const double nx = sqrt(xx);
-        double scale_head, scale_tail;     // projection = (scale_head, scale_tail * x)
-        if (nx <= t0) { scale_head = t0; scale_tail = 1.0; }
-        else if (nx <= -t0) { scale_head = 0.0; scale_tail = 0.0; }
-        else {
-            const double h = 0.5 * (t0 + nx);
-            scale_head = h;
-            scale_tail = h / nx;
-        }
-        for (int e = lane; e < len; e += 32) {
-            const double t = relaxed(a, off + e, gamma, alpha) - a.v[off + e];
-            const double up = e == 0 ? scale_head : scale_tail * t;
-            a.u[off + e] = up;
-            a.v[off + e] = up - t;
-        }
-        return;
-    }
-    const int eb = sb - K.nb_soc;
-    if (eb < K.nb_exp) {
-        const int tri = eb * kBlock + threadIdx.x;
-        if (tri >= K.ep) return;
-        const int off = a.n + K.exp_off + 3 * tri;
-        double t[3];
-#pragma unroll
-        for (int e = 0; e < 3; ++e) t[e] = relaxed(a, off + e, gamma, alpha) - a.v[off + e];
-        double pu, pv, pw;
-        proj_exp_dual(t[0], t[1], t[2], pu, pv, pw);
-        a.u[off] = pu; a.v[off] = pu - t[0];
-        a.u[off + 1] = pv; a.v[off + 1] = pv - t[1];
-        a.u[off + 2] = pw; a.v[off + 2] = pw - t[2];
     }
 }
 

@@ -36,6 +36,11 @@ __device__ __forceinline__ Acc fmul(TA a, TX x) {
     return static_cast<Acc>(a) * static_cast<Acc>(x);
 }
 
+// The matrix arrays are read once per product: load them with the streaming
+// (evict-first) policy so that they do not push the gathered vector out of L2.
+template <typename U>
+__device__ __forceinline__ U ld_stream(const U *p) { return __ldcs(p); }
+
 template <typename TA, typename TX, typename Acc, typename Epi>
 __global__ void __launch_bounds__(kBlock) spmv_stream_kernel(Csr<TA> A, const TX *__restrict__ x,
                                                              Epi epi, ReduceBuf rb) {
@@ -60,7 +65,7 @@ __global__ void __launch_bounds__(kBlock) spmv_stream_kernel(Csr<TA> A, const TX
         const int32_t *__restrict__ col = A.col;
         const TA *__restrict__ val = A.val;
 #pragma unroll 4
-        for (int k = k0 + tid; k < k1; k += kBlock) s += fmul<Acc>(__ldg(val + k), __ldg(x + __ldg(col + k)));
+        for (int k = k0 + tid; k < k1; k += kBlock) s += fmul<Acc>(ld_stream(val + k), __ldg(x + ld_stream(col + k)));
         double t[1] = {static_cast<double>(s)};
         // sum in Acc precision order-independent of warps: use block_sum in double
         block_sum<1>(t);
@@ -69,7 +74,7 @@ __global__ void __launch_bounds__(kBlock) spmv_stream_kernel(Csr<TA> A, const TX
         const int32_t *__restrict__ col = A.col + k0;
         const TA *__restrict__ val = A.val + k0;
 #pragma unroll 8
-        for (int k = tid; k < nz; k += kBlock) prod[k] = fmul<Acc>(__ldg(val + k), __ldg(x + __ldg(col + k)));
+        for (int k = tid; k < nz; k += kBlock) prod[k] = fmul<Acc>(ld_stream(val + k), __ldg(x + ld_stream(col + k)));
         __syncthreads();
         const int nr = r1 - r0;
         int L = 1;

@@ -105,6 +105,9 @@ def _svec(M: np.ndarray) -> np.ndarray:
 
 
 def _pair_soc(rng, k):
+    if k == 1:                      # SOC(1) = {t >= 0}: one side takes the mass
+        g = abs(rng.standard_normal()) + 0.1
+        return (np.array([g]), np.zeros(1)) if rng.random() < 0.5 else (np.zeros(1), np.array([g]))
     d = rng.standard_normal(k - 1)
     nd = np.linalg.norm(d)
     d = d / nd if nd > 0 else np.eye(k - 1)[0]

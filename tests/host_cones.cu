@@ -1,0 +1,12 @@
+// Host build of the CUDA path's exponential-cone projection (the same
+// __host__ __device__ functions the kernels call), for CPU tests.
+#include "../paper_1312_3039_gb300/csrc/cones.cuh"
+
+extern "C" void host_proj_exp(const double *in, double *out, int n, int dual) {
+    for (int i = 0; i < n; ++i) {
+        if (dual)
+            scs::proj_exp_dual(in[3 * i], in[3 * i + 1], in[3 * i + 2], out[3 * i], out[3 * i + 1], out[3 * i + 2]);
+        else
+            scs::proj_exp(in[3 * i], in[3 * i + 1], in[3 * i + 2], out[3 * i], out[3 * i + 1], out[3 * i + 2]);
+    }
+}

@@ -1,0 +1,42 @@
+"""The CUDA path's exponential-cone projection (compiled for the host from the
+same header the kernels use) against the oracle, on the CPU."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import cones
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    out = tmp_path_factory.mktemp("hostcones") / "hostcones.so"
+    subprocess.check_call([nvcc, "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+                           os.path.join(HERE, "host_cones.cu"), "-o", str(out)])
+    return ctypes.CDLL(str(out))
+
+
+def points(seed, count):
+    rng = np.random.default_rng(seed)
+    V = rng.standard_normal((count, 3)) * rng.uniform(0.1, 5, size=(count, 1))
+    k = count // 5
+    V[:k] *= 10.0 ** rng.uniform(-6, 3, size=(k, 3))       # mixed magnitudes
+    return V
+
+
+@pytest.mark.parametrize("dual", [0, 1])
+def test_exp_projection_matches_oracle(lib, dual):
+    V = points(10 + dual, 6000)
+    out = np.zeros_like(V)
+    lib.host_proj_exp(V.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p), len(V), dual)
+    ref = np.array([cones.proj_exp_dual(v) if dual else cones.proj_exp(v) for v in V])
+    err = np.linalg.norm(out - ref, axis=1) / np.maximum(1.0, np.linalg.norm(V, axis=1))
+    assert err.max() <= 1e-12, (V[np.argmax(err)], out[np.argmax(err)], ref[np.argmax(err)])

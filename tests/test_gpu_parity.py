@@ -30,7 +30,7 @@ def scs():
     return _scs
 
 
-TIGHT = dict(precision=0, cg_rate=0.0, cg_tol_rel=1e-13, cg_max_iters=500)
+TIGHT = dict(precision=0, cg_rate=0.0, cg_adapt=0.0, cg_tol_rel=1e-13, cg_max_iters=500)
 
 
 def trajectory_parity(scs, P, iters=50, tol=1e-9, **gpu_kw):

@@ -33,7 +33,7 @@ def test_smw_equals_dense_solve():
     P = synth.random_cone(3, n=12)
     for linsys in ("direct", "indirect"):
         S = admm.HSDSolver(P.A, P.b, P.c, P.cone,
-                           exact_settings(linsys=linsys, cg_rate=0.0, cg_tol_rel=1e-14))
+                           exact_settings(linsys=linsys, cg_rate=0.0, cg_adapt=0.0, cg_tol_rel=1e-14))
         Q = naive.hsd_Q(S.A, S.b, S.c)
         rng = np.random.default_rng(0)
         for _ in range(5):
@@ -173,7 +173,7 @@ def test_direct_and_tight_indirect_agree():
     P = synth.lp(2)
     Sd = admm.HSDSolver(P.A, P.b, P.c, P.cone, admm.Settings())
     Si = admm.HSDSolver(P.A, P.b, P.c, P.cone, admm.Settings(linsys="indirect", cg_rate=0.0,
-                                                             cg_tol_rel=1e-13))
+                                                             cg_adapt=0.0, cg_tol_rel=1e-13))
     for _ in range(50):
         Sd.step(); Si.step()
     np.testing.assert_allclose(Si.u, Sd.u, atol=1e-9 * np.linalg.norm(Sd.u))
@@ -213,3 +213,21 @@ def test_warm_start_from_solution():
     r2 = admm.solve(P.A, P.b, P.c, P.cone, st, warm=(r.x, r.y, r.s))
     assert r2.status == admm.SOLVED
     assert r2.iters <= st.check_interval < r.iters
+
+
+@pytest.mark.parametrize("variant", ["infeasible", "unbounded"])
+def test_indirect_certificates(variant):
+    """The indirect method with the capped CG schedule certifies as fast as
+    the exact solve (the absolute schedule alone does not within 3000)."""
+    P = synth.lp(0, variant=variant)
+    r = admm.solve(P.A, P.b, P.c, P.cone, admm.Settings(linsys="indirect", max_iters=2000))
+    assert r.status == (admm.INFEASIBLE if variant == "infeasible" else admm.UNBOUNDED)
+    assert r.iters <= 600
+
+
+def test_indirect_warm_start():
+    P = synth.lp(3)
+    st = admm.Settings(linsys="indirect")
+    r = admm.solve(P.A, P.b, P.c, P.cone, st)
+    r2 = admm.solve(P.A, P.b, P.c, P.cone, st, warm=(r.x, r.y, r.s))
+    assert r2.status == admm.SOLVED and r2.iters <= 40 < r.iters
