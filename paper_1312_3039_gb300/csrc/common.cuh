@@ -12,7 +12,6 @@ namespace scs {
 constexpr int kBlock = 256;          // threads per CTA for every kernel
 constexpr int kWarps = kBlock / 32;
 constexpr int kMaxRed = 6;           // most values one grid sum carries
-constexpr int kStreamCap = 2048;     // nonzeros staged in shared memory per CSR-stream block
 
 // Scalars of one solve.  Written by the "last block" finishers of the grid
 // sums and read by later kernels; the host reads a copy at check time.
@@ -40,12 +39,14 @@ struct Scalars {
     int32_t done;       // CG residual test passed (or cap reached)
     int32_t active;     // CG loop still running
     int32_t status;     // termination status written by the check
+    int32_t dev_error;  // set by a kernel whose bounded wait timed out
     int64_t cg_total;   // CG steps since the last reset
 };
 
 struct ReduceBuf {
-    double *partials;   // [blocks * kMaxRed]
+    double *partials;   // [kMaxRed][cap]: value i of block b at i * cap + b
     unsigned *counter;  // one counter per call site
+    int cap;            // blocks the buffer holds
 };
 
 template <typename T>
@@ -85,7 +86,7 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NV], ReduceBuf rb, int site
     block_sum<NV>(v);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int i = 0; i < NV; ++i) rb.partials[(size_t)blockIdx.x * kMaxRed + i] = v[i];
+        for (int i = 0; i < NV; ++i) rb.partials[(size_t)i * rb.cap + blockIdx.x] = v[i];
         __threadfence();
         unsigned t = atomicAdd(rb.counter + site, 1u);
         last = (t == gridDim.x - 1);
@@ -98,7 +99,7 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NV], ReduceBuf rb, int site
     for (int i = 0; i < NV; ++i) acc[i] = 0.0;
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
 #pragma unroll
-        for (int i = 0; i < NV; ++i) acc[i] += __ldcg(rb.partials + (size_t)b * kMaxRed + i);
+        for (int i = 0; i < NV; ++i) acc[i] += __ldcg(rb.partials + (size_t)i * rb.cap + b);
     }
     block_sum<NV>(acc);
 #pragma unroll

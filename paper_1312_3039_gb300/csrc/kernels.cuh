@@ -478,25 +478,25 @@ static __global__ void __launch_bounds__(kBlock) output_kernel(int n, int m, int
 // ---------------------------------------------------------------------------
 // setup kernels (FP64): equilibration (Sec. 5) and conversions
 // ---------------------------------------------------------------------------
-static __global__ void row_sumsq_kernel(const int32_t *__restrict__ rowptr, const double *__restrict__ val, int rows,
-                                 double *__restrict__ out) {
+static __global__ void row_sumsq_kernel(const int32_t *__restrict__ rowptr, const double *__restrict__ val,
+                                        const int32_t *__restrict__ rowid, int rows, double *__restrict__ out) {
     const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int nw = (gridDim.x * kBlock) >> 5;
     for (int r = warp; r < rows; r += nw) {
         double s = 0.0;
         for (int k = rowptr[r] + lane; k < rowptr[r + 1]; k += 32) s += val[k] * val[k];
         s = warp_sum(s);
-        if (lane == 0) out[r] = s;
+        if (lane == 0) out[rowid[r]] = s;
     }
 }
 
 static __global__ void scale_vals_kernel(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                                  double *__restrict__ val, int rows, const double *__restrict__ drow,
-                                  const double *__restrict__ ecol) {
+                                         double *__restrict__ val, const int32_t *__restrict__ rowid, int rows,
+                                         const double *__restrict__ drow, const double *__restrict__ ecol) {
     const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int nw = (gridDim.x * kBlock) >> 5;
     for (int r = warp; r < rows; r += nw) {
-        const double d = drow[r];
+        const double d = drow[rowid[r]];
         for (int k = rowptr[r] + lane; k < rowptr[r + 1]; k += 32) val[k] *= d * ecol[col[k]];
     }
 }

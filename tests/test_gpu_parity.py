@@ -94,13 +94,23 @@ def test_plain_launch_path_matches_graph(scs):
 
 
 def check_solution(P, x, y, s, eps=1e-4):
+    """Sec. 3.5 tests on the returned point against the original data, and
+    the objective inside the band weak duality gives around the known optimum:
+    with r_p = A x + s - b and r_d = A^T y + c, the generator's x*, y* give
+    p* - c^T x <= ||y*|| ||r_p||  and  c^T x - p* <= |gap| + ||x*|| ||r_d||."""
     nb, nc = np.linalg.norm(P.b), np.linalg.norm(P.c)
-    assert np.linalg.norm(P.A @ x + s - P.b) <= eps * (1 + nb) * 1.0001
-    assert np.linalg.norm(P.A.T @ y + P.c) <= eps * (1 + nc) * 1.0001
+    rp = np.linalg.norm(P.A @ x + s - P.b)
+    rd = np.linalg.norm(P.A.T @ y + P.c)
+    assert rp <= eps * (1 + nb) * 1.0001
+    assert rd <= eps * (1 + nc) * 1.0001
     cx, by = P.c @ x, P.b @ y
     assert abs(cx + by) <= eps * (1 + abs(cx) + abs(by)) * 1.0001
     assert cones.in_K(s, P.cone, 1e-7)
     assert cones.in_Kdual(y, P.cone, 1e-7)
+    if P.p_star is not None:
+        slack = 1e-9 * (1 + abs(P.p_star))
+        assert P.p_star - cx <= np.linalg.norm(P.y_star) * rp + slack
+        assert cx - P.p_star <= abs(cx + by) + np.linalg.norm(P.x_star) * rd + slack
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -111,8 +121,7 @@ def test_lp_solve(scs, precision, seed):
     st, x, y, s, info = scs.solve(P.A, P.b, P.c, P.cone, precision=precision)
     assert st == scs.SOLVED, info
     check_solution(P, x, y, s)
-    assert abs(info["pobj"] - ref.pobj) <= 1e-4 * (1 + abs(ref.pobj)) * 10
-    assert abs(info["pobj"] - P.p_star) <= 1e-3 * (1 + abs(P.p_star))
+    assert abs(info["pobj"] - ref.pobj) <= 1e-3 * (1 + abs(ref.pobj))
     assert info["matvecs"] == 2 * info["iters"] + 2 * info["cg_iters"]
     assert info["iters"] % 20 == 0
 
@@ -123,7 +132,6 @@ def test_mixed_small_solve(scs, precision):
     st, x, y, s, info = scs.solve(P.A, P.b, P.c, P.cone, precision=precision)
     assert st == scs.SOLVED, info
     check_solution(P, x, y, s)
-    assert abs(info["pobj"] - P.p_star) <= 2e-3 * (1 + abs(P.p_star))
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -163,16 +171,20 @@ def test_warm_start_from_solution(scs):
 
 
 def test_long_rows_and_empty_rows(scs):
-    """Rows longer than one shared-memory stream block (2048 nonzeros) take
-    the whole-CTA path; empty rows and columns go through every kernel."""
+    """Every SpMV path: rows longer than 2048 nonzeros (one CTA each), rows of
+    257..2048 (one warp each), short rows of every length class packed into
+    warp tasks; empty rows and columns go through every kernel."""
     rng = np.random.default_rng(5)
     n, m = 3000, 3200
     A = sp.lil_matrix((m, n))
     A[7, :] = rng.standard_normal(n)            # one dense row of 3000 entries
     A[40, :2500] = rng.standard_normal(2500)
+    A[60, 500:1500] = rng.standard_normal(1000)  # one warp
+    A[61, 100:400] = rng.standard_normal(300)
     B = synth.bernoulli_sparse(rng, m, n, 0.002).tolil()
     B[7, :] = 0
     B[40, :] = 0
+    B[60:62, :] = 0
     B[100:120, :] = 0                           # empty rows
     A = sp.csc_matrix(A + B)
     cone = synth.Cone(z=50, l=m - 50 - 12, q=(5, 4), ep=1)

@@ -231,3 +231,18 @@ def test_indirect_warm_start():
     r = admm.solve(P.A, P.b, P.c, P.cone, st)
     r2 = admm.solve(P.A, P.b, P.c, P.cone, st, warm=(r.x, r.y, r.s))
     assert r2.status == admm.SOLVED and r2.iters <= 40 < r.iters
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_weak_duality_band(seed):
+    """At the 1e-4 tolerances the objective need not be within 1e-4 of p*,
+    but weak duality bounds it by the residuals: with the generator's x*, y*,
+    p* - c^T x <= ||y*|| ||A x + s - b|| and c^T x - p* <= |gap| + ||x*|| ||A^T y + c||."""
+    P = synth.mixed_small(seed, scale=500)
+    r = admm.solve(P.A, P.b, P.c, P.cone, admm.Settings())
+    assert r.status == admm.SOLVED
+    rp = np.linalg.norm(P.A @ r.x + r.s - P.b)
+    rd = np.linalg.norm(P.A.T @ r.y + P.c)
+    gap = abs(P.c @ r.x + P.b @ r.y)
+    assert P.p_star - P.c @ r.x <= np.linalg.norm(P.y_star) * rp + 1e-9
+    assert P.c @ r.x - P.p_star <= gap + np.linalg.norm(P.x_star) * rd + 1e-9
