@@ -264,30 +264,20 @@ class Engine : public EngineBase {
     // ------------------------------------------------------------------ setup
     void setup(const HostProblem &P) {
         // sparse layouts
-        // stored layouts and work items of A and A^T: persistent grids of as
-        // many CTAs as fit on the GPU at once (shared memory bounds it)
-        SCS_CUDA(cudaFuncSetAttribute(spmv_kernel<T, T, T, EpiACG<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)SpmvSmem<T, T>::kBytes));
-        int per_sm = 1;
-        SCS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spmv_kernel<T, T, T, EpiACG<T>>, kBlock,
-                                                               SpmvSmem<T, T>::kBytes));
-        const int spmv_grid = sms_ * std::max(per_sm, 1);
-        SpmvLayout<double> LA = spmv_layout(P.a_rowptr, P.a_col, P.a_val, spmv_grid);
-        SpmvLayout<double> LAt = spmv_layout(P.at_rowptr, P.at_col, P.at_val, spmv_grid);
+        // stored layouts of A and A^T; region grids for 8 CTAs per SM
+        const int spmv_ctas = sms_ * 8;
+        SpmvLayout<double> LA = spmv_layout(P.a_rowptr, P.a_col, P.a_val, spmv_ctas);
+        SpmvLayout<double> LAt = spmv_layout(P.at_rowptr, P.at_col, P.at_val, spmv_ctas);
         int32_t *a_rowptr = upload(LA.rowptr), *a_col = upload(LA.col), *a_rowid = upload(LA.rowid);
-        int32_t *a_chunk = upload(LA.chunk), *a_kind = upload(LA.kind), *a_cta = upload(LA.cta_item);
         double *a_val64 = upload(LA.val);
         int32_t *at_rowptr = upload(LAt.rowptr), *at_col = upload(LAt.col), *at_rowid = upload(LAt.rowid);
-        int32_t *at_chunk = upload(LAt.chunk), *at_kind = upload(LAt.kind), *at_cta = upload(LAt.cta_item);
         double *at_val64 = upload(LAt.val);
         S_ = dalloc<Scalars>(1);
         SCS_CUDA(cudaMemsetAsync(S_, 0, sizeof(Scalars), stream_));
-        int32_t *derr = &S_->dev_error;
-        auto mkcsr = [&](auto *vals, const int32_t *rp, const int32_t *cl, const int32_t *rid, const int32_t *ch,
-                         const int32_t *kd, const int32_t *ct, const SpmvLayout<double> &lay, int rows) {
+        auto mkcsr = [&](auto *vals, const int32_t *rp, const int32_t *cl, const int32_t *rid,
+                         const SpmvLayout<double> &lay, int rows) {
             using V = std::remove_cv_t<std::remove_pointer_t<decltype(vals)>>;
-            return Csr<V>{rp, cl, vals, rid, reinterpret_cast<const int4 *>(ch), kd, ct, derr, lay.nchunk, rows,
-                          lay.grid};
+            return Csr<V>{rp, cl, vals, rid, rows, lay.reg};
         };
         SCS_CUDA(cudaStreamSynchronize(stream_));     // host layouts are released below
 
@@ -350,28 +340,13 @@ class Engine : public EngineBase {
         // partial sums of the grid reductions: one slot group per CTA of the
         // widest reducing launch (SpMV stream blocks, the projection grid, or
         // the capped grid-stride kernels)
-        rb_cap_ = std::max({LA.grid, LAt.grid, sms_ * 8, proj_grid(), 1});
+        rb_cap_ = std::max({mkcsr(a_val64, a_rowptr, a_col, a_rowid, LA, m_).grid(),
+                            mkcsr(at_val64, at_rowptr, at_col, at_rowid, LAt, n_).grid(), sms_ * 8, proj_grid(), 1});
         rb_.partials = dalloc<double>(static_cast<size_t>(rb_cap_) * kMaxRed);
         rb_.cap = rb_cap_;
         rb_.counter = dalloc<unsigned>(kSiteCount);
         SCS_CUDA(cudaMemsetAsync(rb_.counter, 0, sizeof(unsigned) * kSiteCount, stream_));
         S_ = dalloc<Scalars>(1);
-
-        // the SpMV kernels use more than 48 KB of dynamic shared memory
-        SCS_CUDA(cudaFuncSetAttribute(spmv_kernel<T, T, T, EpiAInit<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)SpmvSmem<T, T>::kBytes));
-        SCS_CUDA(cudaFuncSetAttribute(spmv_kernel<T, T, T, EpiAtInit<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)SpmvSmem<T, T>::kBytes));
-        SCS_CUDA(cudaFuncSetAttribute(spmv_kernel<T, T, T, EpiACG<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)SpmvSmem<T, T>::kBytes));
-        SCS_CUDA(cudaFuncSetAttribute(spmv_kernel<T, T, T, EpiAtCG<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)SpmvSmem<T, T>::kBytes));
-        SCS_CUDA(cudaFuncSetAttribute(spmv_kernel<double, double, double, EpiChkA>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)SpmvSmem<double, double>::kBytes));
-        SCS_CUDA(cudaFuncSetAttribute(spmv_kernel<double, double, double, EpiChkAt>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)SpmvSmem<double, double>::kBytes));
 
         // ---- equilibration, Sec. 5 (FP64) ----
         if (st_.normalize) {
@@ -433,21 +408,21 @@ class Engine : public EngineBase {
             a_val = reinterpret_cast<const T *>(a_val64);
             at_val = reinterpret_cast<const T *>(at_val64);
         } else {
-            T *av = dalloc<T>(nnz_ + kPad), *atv = dalloc<T>(nnz_ + kPad);
+            T *av = dalloc<T>(nnz_), *atv = dalloc<T>(nnz_);
             const double *a64 = a_val64, *at64 = at_val64;
             foreach_kernel<<<grid_for(nnz_), kBlock, 0, stream_>>>(
                 [=] __device__(int k) { av[k] = static_cast<T>(a64[k]); atv[k] = static_cast<T>(at64[k]); },
-                (int)nnz_ + kPad);
+                (int)nnz_);
             a_val = av;
             at_val = atv;
         }
-        A_ = mkcsr(a_val, a_rowptr, a_col, a_rowid, a_chunk, a_kind, a_cta, LA, m_);
-        At_ = mkcsr(at_val, at_rowptr, at_col, at_rowid, at_chunk, at_kind, at_cta, LAt, n_);
+        A_ = mkcsr(a_val, a_rowptr, a_col, a_rowid, LA, m_);
+        At_ = mkcsr(at_val, at_rowptr, at_col, at_rowid, LAt, n_);
         SCS_CUDA(cudaGetLastError());
         SCS_CUDA(cudaStreamSynchronize(stream_));
         // FP64 values (the same arrays in the FP64 engine) for the termination tests
-        A64_ = mkcsr(a_val64, a_rowptr, a_col, a_rowid, a_chunk, a_kind, a_cta, LA, m_);
-        At64_ = mkcsr(at_val64, at_rowptr, at_col, at_rowid, at_chunk, at_kind, at_cta, LAt, n_);
+        A64_ = mkcsr(a_val64, a_rowptr, a_col, a_rowid, LA, m_);
+        At64_ = mkcsr(at_val64, at_rowptr, at_col, at_rowid, LAt, n_);
 
         // host copies of the scaling (warm start, scs_get_scaling)
         Dh_.resize(m_);
@@ -567,24 +542,24 @@ class Engine : public EngineBase {
     }
 
     void launch_K1() {
-        guard(A_.grid);
+        guard(A_.grid());
         EpiAInit<T> e{u_, v_, b_, yacc_, S_, n_, N_, 0.0};
-        spmv_kernel<T, T, T, EpiAInit<T>><<<A_.grid, kBlock, SpmvSmem<T, T>::kBytes, cur_>>>(A_, z_, e, rb_);
+        spmv_kernel<T, T, T, EpiAInit<T>><<<A_.grid(), kBlock, 0, cur_>>>(A_, z_, e, rb_);
     }
     void launch_K2(CondHandle h) {
-        guard(At_.grid);
+        guard(At_.grid());
         EpiAtInit<T> e{u_, v_, c_, diag_, z_, r_, pv_, S_, h, N_, 0.0};
-        spmv_kernel<T, T, T, EpiAtInit<T>><<<At_.grid, kBlock, SpmvSmem<T, T>::kBytes, cur_>>>(At_, yacc_, e, rb_);
+        spmv_kernel<T, T, T, EpiAtInit<T>><<<At_.grid(), kBlock, 0, cur_>>>(At_, yacc_, e, rb_);
     }
     void launch_K3() {
-        guard(A_.grid);
+        guard(A_.grid());
         EpiACG<T> e{q_, S_};
-        spmv_kernel<T, T, T, EpiACG<T>><<<A_.grid, kBlock, SpmvSmem<T, T>::kBytes, cur_>>>(A_, pv_, e, rb_);
+        spmv_kernel<T, T, T, EpiACG<T>><<<A_.grid(), kBlock, 0, cur_>>>(A_, pv_, e, rb_);
     }
     void launch_K4() {
-        guard(At_.grid);
+        guard(At_.grid());
         EpiAtCG<T> e{diag_, z_, r_, pv_, S_, T(0)};
-        spmv_kernel<T, T, T, EpiAtCG<T>><<<At_.grid, kBlock, SpmvSmem<T, T>::kBytes, cur_>>>(At_, q_, e, rb_);
+        spmv_kernel<T, T, T, EpiAtCG<T>><<<At_.grid(), kBlock, 0, cur_>>>(At_, q_, e, rb_);
     }
     void launch_K5(CondHandle h) {
         cg_update_kernel<T><<<grid_for(std::max(n_, m_)), kBlock, 0, cur_>>>(n_, m_, q_, yacc_, r_, diag_, pv_, S_,
@@ -600,12 +575,12 @@ class Engine : public EngineBase {
         relax_project_kernel<T><<<grid, kBlock, 0, cur_>>>(a, cone_, rb_);
     }
     void launch_check() {
-        guard(A64_.grid);
-        guard(At64_.grid);
+        guard(A64_.grid());
+        guard(At64_.grid());
         EpiChkA ea{u_, v_, b_, D_, ax_, S_, n_, N_, 0.0};
-        spmv_kernel<double, double, double, EpiChkA><<<A64_.grid, kBlock, SpmvSmem<double, double>::kBytes, stream_>>>(A64_, u_, ea, rb_);
+        spmv_kernel<double, double, double, EpiChkA><<<A64_.grid(), kBlock, 0, stream_>>>(A64_, u_, ea, rb_);
         EpiChkAt eb{u_, v_, c_, E_, S_, N_, 0.0};
-        spmv_kernel<double, double, double, EpiChkAt><<<At64_.grid, kBlock, SpmvSmem<double, double>::kBytes, stream_>>>(At64_, u_ + n_, eb,
+        spmv_kernel<double, double, double, EpiChkAt><<<At64_.grid(), kBlock, 0, stream_>>>(At64_, u_ + n_, eb,
                                                                                                   rb_);
         SCS_CUDA(cudaGetLastError());
     }

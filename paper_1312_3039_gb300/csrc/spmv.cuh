@@ -1,268 +1,135 @@
 // CSR sparse matrix-vector product with a fused per-row epilogue and a fused
 // deterministic grid reduction, built for rows of power-law lengths.
 //
+// With uniformly random columns every product gathers one 4- or 8-byte
+// entry of x from its own 32-byte L2 sector; on GB300 those gathers (not the
+// HBM stream of the matrix) bound the product.  The kernel is therefore a
+// flat, barrier-free launch that keeps as many independent gathers in
+// flight as possible:
+//
 // Layout (setup, host): rows are stored grouped by length class (1, 2, 3-4,
 // 5-8, ...; original order kept inside a class; `rowid` maps a stored row
-// back to its matrix row, which is where the epilogue writes).  The stored
-// rows are cut into chunks of at most kChunkNnz nonzeros:
-//   * runs of same-class rows (at most kChunkRows rows), so the rows summed
-//     together have similar lengths;
-//   * pieces of a row longer than kChunkNnz, in order; the pieces of one
-//     row carry a running sum and the last one completes the row.
-// The chunk list is cut into one contiguous, nnz-balanced range per CTA of a
-// persistent grid (never inside the pieces of one row).
-//
-// Kernel: each CTA keeps kStages shared-memory stages.  One thread fills a
-// stage with TMA bulk copies (cp.async.bulk, completion on an mbarrier) of
-// the chunk's column indices and values (and, for a run of rows, its row
-// pointers and row ids), and puts the chunk descriptor in the stage header.
-// For each chunk the threads wait on the stage's barrier (bounded: on
-// timeout an error flag is set), form the products val * x[col] (the only
-// global loads left on the threads' path are the gathers of x, served from
-// L2), stage them in shared memory, and either sum each row with a group of
-// L lanes sized to the chunk's row count, or (a piece) sum the whole chunk
-// into the row's running sum; completed row sums go to the epilogue.  Every thread accumulates the epilogue's
-// reduction values over all its rows; each CTA joins one grid_sum at the end,
-// whose last CTA runs the epilogue's finisher.
+// back to its matrix row, which is where the epilogue writes).  Each run of
+// classes forms a region whose rows get groups of L lanes: L = 1 up to 4
+// nonzeros, 2 up to 8, 4 up to 16, 8 up to 32, a warp up to kWarpRow and a
+// whole CTA beyond, so every lane holds a few nonzeros of one row and the
+// group's loads of a row are contiguous.  One launch covers all regions
+// (grid-stride loops whose trip counts are uniform per warp; region grids
+// sized by their nonzeros).  Every thread accumulates the epilogue's
+// reduction values over all its rows; each CTA joins one grid_sum at the
+// end, whose last CTA runs the epilogue's finisher.
 #pragma once
 
 #include <stdint.h>
 
 #include <algorithm>
-#include <numeric>
 #include <vector>
 
 #include "common.cuh"
 
 namespace scs {
 
-constexpr int kChunkNnz = 1024;      // nonzeros of one chunk (and the long-row threshold)
-constexpr int kChunkRows = 512;      // rows of one chunk
-constexpr int kStages = 2;           // TMA stages per CTA
-constexpr int kPad = 4;              // elements of zero padding after every array a copy may touch
+constexpr int kWarpRow = 4096;       // rows up to this length: at most a warp (longer: one CTA)
+constexpr int kMaxRegions = 8;
+constexpr int kCtaLanes = kBlock;    // lanes per row in the CTA region
 
-// chunk kinds
-constexpr int kRun = 0;          // whole rows [r0, r1)
-constexpr int kPiece = 1;        // nonzeros [k0, k1) of the single row r0
-constexpr int kLastPiece = 3;    // ... and the row ends here
+// lanes per row for a row length
+inline int lanes_for(int32_t len) {
+    if (len <= 4) return 1;
+    if (len <= 8) return 2;
+    if (len <= 16) return 4;
+    if (len <= 32) return 8;
+    if (len <= kWarpRow) return 32;
+    return kCtaLanes;
+}
+
+struct SpmvRegions {
+    int32_t n;                        // regions in use
+    int32_t row0[kMaxRegions];        // stored rows [row0, row1)
+    int32_t row1[kMaxRegions];
+    int32_t lanes[kMaxRegions];       // 1, 2, 4, 8, 32 or kCtaLanes
+    int32_t cta0[kMaxRegions + 1];    // CTAs [cta0[i], cta0[i+1]) serve region i
+};
 
 template <typename TA>
 struct Csr {
-    const int32_t *rowptr;   // rows + 1 (+kPad) (stored order)
-    const int32_t *col;      // nnz (+kPad)
-    const TA *val;           // nnz (+kPad)
-    const int32_t *rowid;    // rows (+kPad): matrix row of each stored row
-    const int4 *chunk;       // nchunk: (r0, r1, k0, k1)
-    const int32_t *kind;     // nchunk: kRun, kPiece or kLastPiece
-    const int32_t *cta_item; // grid + 1: chunk range of each CTA
-    int32_t *err;            // set to 1 by a CTA whose copy wait timed out
-    int32_t nchunk, rows, grid;
+    const int32_t *rowptr;   // rows + 1 (stored order)
+    const int32_t *col;      // nnz
+    const TA *val;           // nnz
+    const int32_t *rowid;    // rows: matrix row of each stored row
+    int32_t rows;
+    SpmvRegions reg;
+    int32_t grid() const { return reg.cta0[reg.n]; }
 };
-
-template <typename TA, typename Acc>
-struct SpmvSmem {
-    // one stage; each array starts on a 16-byte boundary
-    static constexpr int kColWords = kChunkNnz + 2 * kPad;
-    static constexpr int kValElems = kChunkNnz + 2 * kPad;
-    static constexpr int kRowWords = kChunkRows + 2 * kPad;
-    static constexpr size_t kColOff = 0;
-    static constexpr size_t kValOff = kColOff + sizeof(int32_t) * kColWords;
-    static constexpr size_t kRpOff = kValOff + ((sizeof(TA) * kValElems + 15) / 16) * 16;
-    static constexpr size_t kRidOff = kRpOff + sizeof(int32_t) * kRowWords;
-    static constexpr size_t kStageBytes = kRidOff + sizeof(int32_t) * kRowWords;
-    static constexpr size_t kProdOff = kStages * kStageBytes;
-    static constexpr size_t kBarOff = kProdOff + ((sizeof(Acc) * kChunkNnz + 15) / 16) * 16;
-    static constexpr size_t kHdrOff = kBarOff + 8 * kStages;          // int4 descriptor + kind per stage
-    static constexpr size_t kBytes = kHdrOff + 32 * kStages;
-};
-
-// ---------------------------------------------------------------------------
-// TMA / mbarrier helpers (inline PTX)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_init_fence() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// bounded wait: false if the phase did not complete within the limit
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (int i = 0; i < (1 << 20); ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
 
 template <typename Acc, typename TA, typename TX>
 __device__ __forceinline__ Acc fmul(TA a, TX x) {
     return static_cast<Acc>(a) * static_cast<Acc>(x);
 }
 
-// first element of the 16-byte block holding element k of an array of U,
-// and the end of the 16-byte block holding element k - 1
-template <typename U>
-__device__ __host__ __forceinline__ int64_t align_down16(int64_t k) {
-    constexpr int per = 16 / (int)sizeof(U);
-    return k & ~(int64_t)(per - 1);
-}
-template <typename U>
-__device__ __host__ __forceinline__ int64_t align_up16(int64_t k) {
-    constexpr int per = 16 / (int)sizeof(U);
-    return (k + per - 1) & ~(int64_t)(per - 1);
-}
-
-// Issue the copies of chunk c into stage s (one thread); the descriptor goes
-// to the stage header (written before the arrive, which releases it).
-template <typename TA, typename Acc>
-__device__ __forceinline__ void issue_chunk(const Csr<TA> &A, int c, unsigned char *smem, int s) {
-    using L = SpmvSmem<TA, Acc>;
-    unsigned char *st = smem + s * L::kStageBytes;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L::kBarOff) + s;
-    int4 *hdr = reinterpret_cast<int4 *>(smem + L::kHdrOff);
-    int *hkind = reinterpret_cast<int *>(smem + L::kHdrOff + 16 * kStages);
-    const int4 d = A.chunk[c];
-    const int kind = A.kind[c];
-    hdr[s] = d;
-    hkind[s] = kind;
-    const int r0 = d.x, r1 = d.y, k0 = d.z, k1 = d.w;
-    const int64_t ca = align_down16<int32_t>(k0), cb = align_up16<int32_t>(k1);
-    const int64_t va = align_down16<TA>(k0), vb = align_up16<TA>(k1);
-    const uint32_t bc = (uint32_t)(4 * (cb - ca)), bv = (uint32_t)(sizeof(TA) * (vb - va));
-    uint32_t bp = 0, bi = 0;
-    int64_t pa = 0, ia = 0;
-    if (kind == kRun) {
-        pa = align_down16<int32_t>(r0);
-        ia = pa;
-        bp = (uint32_t)(4 * (align_up16<int32_t>(r1 + 1) - pa));
-        bi = (uint32_t)(4 * (align_up16<int32_t>(r1) - ia));
+template <int L, typename TA, typename TX, typename Acc, typename Epi>
+__device__ __forceinline__ void spmv_groups(const Csr<TA> &A, const TX *__restrict__ x, Epi &epi, double (&red)[Epi::NV],
+                                            int r0, int r1, int cta, int nctas) {
+    // groups of L lanes, 32 / L groups per warp; the loop runs while any
+    // group of the warp has a row, so shuffles see the whole warp
+    constexpr int G = 32 / L;
+    const int lane = threadIdx.x & 31, g = lane / L, gl = lane % L;
+    const int warp = cta * kWarps + (threadIdx.x >> 5), nwarps = nctas * kWarps;
+    const int32_t *__restrict__ rowptr = A.rowptr;
+    const int32_t *__restrict__ col = A.col;
+    const TA *__restrict__ val = A.val;
+    for (int base = r0 + warp * G; base < r1; base += nwarps * G) {
+        const int r = base + g;
+        Acc sacc = 0;
+        if (r < r1) {
+            const int k0 = rowptr[r], k1 = rowptr[r + 1];
+#pragma unroll 4
+            for (int k = k0 + gl; k < k1; k += L) sacc += fmul<Acc>(__ldcs(val + k), __ldg(x + __ldcs(col + k)));
+        }
+#pragma unroll
+        for (int o = L >> 1; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+        if (r < r1 && gl == 0) epi.row(A.rowid[r], sacc, red);
     }
-    mbar_expect_tx(bar, bc + bv + bp + bi);
-    if (bc) bulk_g2s(st + L::kColOff, A.col + ca, bc, bar);
-    if (bv) bulk_g2s(st + L::kValOff, A.val + va, bv, bar);
-    if (bp) bulk_g2s(st + L::kRpOff, A.rowptr + pa, bp, bar);
-    if (bi) bulk_g2s(st + L::kRidOff, A.rowid + ia, bi, bar);
 }
 
 template <typename TA, typename TX, typename Acc, typename Epi>
 __global__ void __launch_bounds__(kBlock) spmv_kernel(Csr<TA> A, const TX *__restrict__ x, Epi epi, ReduceBuf rb) {
-    using L = SpmvSmem<TA, Acc>;
     constexpr int NV = Epi::NV;
     static_assert(NV >= 1 && NV <= kMaxRed, "epilogue reduction width");
     if (epi.skip()) return;
-    extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L::kBarOff);
-    const int4 *hdr = reinterpret_cast<const int4 *>(smem + L::kHdrOff);
-    const int *hkind = reinterpret_cast<const int *>(smem + L::kHdrOff + 16 * kStages);
-    Acc *prod = reinterpret_cast<Acc *>(smem + L::kProdOff);
     epi.begin();
     double red[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) red[i] = 0.0;
-    const int tid = threadIdx.x;
-    const int c0 = A.cta_item[blockIdx.x], c1 = A.cta_item[blockIdx.x + 1];
-    const int nch = c1 - c0;
-
-    if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
-        mbar_init_fence();
-        for (int j = 0; j < nch && j < kStages; ++j) issue_chunk<TA, Acc>(A, c0 + j, smem, j);
-    }
-    __syncthreads();
-
-    double piece_sum = 0.0;          // running sum of a row split into pieces (thread 0)
-    bool ok = true;
-    for (int j = 0; j < nch; ++j) {
-        const int s = j % kStages;
-        const uint32_t parity = (uint32_t)((j / kStages) & 1);
-        unsigned char *st = smem + s * L::kStageBytes;
-        // every thread observes the stage's phase; the CTA leaves together if
-        // any wait timed out
-        const bool got = mbar_wait(&bar[s], parity);
-        if (!__syncthreads_and(got)) { ok = false; break; }
-        const int32_t *col_s = reinterpret_cast<const int32_t *>(st + L::kColOff);
-        const TA *val_s = reinterpret_cast<const TA *>(st + L::kValOff);
-        const int4 d = hdr[s];
-        const int kind = hkind[s];
-        const int r0 = d.x, r1 = d.y, k0 = d.z, k1 = d.w;
-        const int cofs = k0 - (int)align_down16<int32_t>(k0), vofs = k0 - (int)align_down16<TA>(k0);
-        const int nz = k1 - k0;
-#pragma unroll 8
-        for (int e = tid; e < nz; e += kBlock) prod[e] = fmul<Acc>(val_s[vofs + e], __ldg(x + col_s[cofs + e]));
-        __syncthreads();
-        if (kind == kRun) {
-            const int32_t *rp_s = reinterpret_cast<const int32_t *>(st + L::kRpOff);
-            const int32_t *rid_s = reinterpret_cast<const int32_t *>(st + L::kRidOff);
-            const int pa = (int)align_down16<int32_t>(r0);
-            const int nr = r1 - r0;
-            int Ln = 1;
-            while (Ln < 32 && 2 * Ln * nr <= kBlock) Ln *= 2;
-            const int groups = kBlock / Ln, g = tid / Ln, gl = tid % Ln;
-            for (int base = 0; base < nr; base += groups) {
-                const int rr = base + g;
+    const int b = blockIdx.x;
+    int ri = 0;
+    while (ri + 1 < A.reg.n && b >= A.reg.cta0[ri + 1]) ++ri;
+    const int r0 = A.reg.row0[ri], r1 = A.reg.row1[ri];
+    const int cta = b - A.reg.cta0[ri], nctas = A.reg.cta0[ri + 1] - A.reg.cta0[ri];
+    switch (A.reg.lanes[ri]) {
+        case 1: spmv_groups<1, TA, TX, Acc>(A, x, epi, red, r0, r1, cta, nctas); break;
+        case 2: spmv_groups<2, TA, TX, Acc>(A, x, epi, red, r0, r1, cta, nctas); break;
+        case 4: spmv_groups<4, TA, TX, Acc>(A, x, epi, red, r0, r1, cta, nctas); break;
+        case 8: spmv_groups<8, TA, TX, Acc>(A, x, epi, red, r0, r1, cta, nctas); break;
+        case 32: spmv_groups<32, TA, TX, Acc>(A, x, epi, red, r0, r1, cta, nctas); break;
+        default: {
+            // one CTA per row
+            const int tid = threadIdx.x;
+            for (int r = r0 + cta; r < r1; r += nctas) {
+                const int k0 = A.rowptr[r], k1 = A.rowptr[r + 1];
                 Acc sacc = 0;
-                if (rr < nr) {
-                    const int rs = rp_s[r0 + rr - pa] - k0, re = rp_s[r0 + rr + 1 - pa] - k0;
-                    for (int e = rs + gl; e < re; e += Ln) sacc += prod[e];
-                }
-                for (int o = Ln >> 1; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-                if (rr < nr && gl == 0) epi.row(rid_s[r0 + rr - pa], sacc, red);
-            }
-        } else {
-            Acc sacc = 0;
-            for (int e = tid; e < nz; e += kBlock) sacc += prod[e];
-            double t[1] = {static_cast<double>(sacc)};
-            block_sum<1>(t);
-            if (tid == 0) {
-                piece_sum += t[0];
-                if (kind == kLastPiece) {
-                    epi.row(A.rowid[r0], static_cast<Acc>(piece_sum), red);
-                    piece_sum = 0.0;
-                }
+#pragma unroll 4
+                for (int k = k0 + tid; k < k1; k += kBlock)
+                    sacc += fmul<Acc>(__ldcs(A.val + k), __ldg(x + __ldcs(A.col + k)));
+                double t[1] = {static_cast<double>(sacc)};
+                block_sum<1>(t);
+                if (tid == 0) epi.row(A.rowid[r], static_cast<Acc>(t[0]), red);
             }
         }
-        __syncthreads();      // stage s and prod are free again
-        if (tid == 0 && j + kStages < nch) {
-            fence_proxy_async_smem();
-            issue_chunk<TA, Acc>(A, c0 + j + kStages, smem, s);
-        }
-    }
-    if (!ok) {
-        // a copy did not complete: flag it, let the outstanding copies land
-        // (bounded) and leave without joining the grid sum
-        if (tid == 0) {
-            atomicExch(A.err, 1);
-            for (int s = 0; s < kStages; ++s) mbar_wait(&bar[s], 0);
-        }
-        return;
     }
     double tot[NV];
     if (grid_sum<NV>(red, rb, Epi::kSite, tot)) {
-        if (tid == 0) epi.finish(tot);
+        if (threadIdx.x == 0) epi.finish(tot);
     }
 }
 
@@ -277,18 +144,17 @@ inline int length_class(int32_t len) {
     return c;
 }
 
-// Stored layout and chunks of one CSR matrix for a grid of `grid` CTAs.
+// Stored layout of one CSR matrix and its regions for a grid of about `ctas` CTAs.
 template <typename V>
 struct SpmvLayout {
-    std::vector<int32_t> rowptr, col, rowid, kind, cta_item;
-    std::vector<int32_t> chunk;       // 4 ints per chunk: r0, r1, k0, k1
+    std::vector<int32_t> rowptr, col, rowid;
     std::vector<V> val;
-    int32_t nchunk = 0, grid = 1;
+    SpmvRegions reg{};
 };
 
 template <typename V>
 inline SpmvLayout<V> spmv_layout(const std::vector<int32_t> &rp, const std::vector<int32_t> &cl,
-                                 const std::vector<V> &vl, int grid) {
+                                 const std::vector<V> &vl, int ctas) {
     SpmvLayout<V> L;
     const int32_t rows = (int32_t)rp.size() - 1;
     std::vector<int> cls(rows);
@@ -300,65 +166,55 @@ inline SpmvLayout<V> spmv_layout(const std::vector<int32_t> &rp, const std::vect
     std::vector<int32_t> start(maxc + 2, 0);
     for (int32_t r = 0; r < rows; ++r) start[cls[r] + 1]++;
     for (int c = 0; c <= maxc; ++c) start[c + 1] += start[c];
-    L.rowid.assign(rows + kPad, 0);
+    L.rowid.assign(rows, 0);
     std::vector<int32_t> pos(start.begin(), start.end() - 1);
     for (int32_t r = 0; r < rows; ++r) L.rowid[pos[cls[r]]++] = r;
     const size_t nnz = cl.size();
-    L.rowptr.assign(rows + 1 + kPad, 0);
-    L.col.assign(nnz + kPad, 0);
-    L.val.assign(nnz + kPad, V(0));
+    L.rowptr.assign(rows + 1, 0);
+    L.col.resize(nnz);
+    L.val.resize(nnz);
     for (int32_t i = 0; i < rows; ++i) {
         const int32_t r = L.rowid[i], len = rp[r + 1] - rp[r];
         L.rowptr[i + 1] = L.rowptr[i] + len;
         std::copy(cl.begin() + rp[r], cl.begin() + rp[r + 1], L.col.begin() + L.rowptr[i]);
         std::copy(vl.begin() + rp[r], vl.begin() + rp[r + 1], L.val.begin() + L.rowptr[i]);
     }
-    for (int k = 0; k < kPad; ++k) L.rowptr[rows + 1 + k] = L.rowptr[rows];
-    // chunks; `cut_ok[c]`: a CTA range may start at chunk c
-    std::vector<char> cut_ok;
-    auto add = [&](int32_t r0, int32_t r1, int32_t k0, int32_t k1, int32_t kind, bool ok) {
-        L.chunk.insert(L.chunk.end(), {r0, r1, k0, k1});
-        L.kind.push_back(kind);
-        cut_ok.push_back(ok ? 1 : 0);
-    };
+    // regions: maximal runs of stored rows with the same lanes per row
+    SpmvRegions &R = L.reg;
+    R.n = 0;
+    std::vector<int64_t> work;
     int32_t i = 0;
-    while (i < rows) {
-        const int32_t k0 = L.rowptr[i], len = L.rowptr[i + 1] - k0;
-        if (len > kChunkNnz) {
-            for (int32_t k = k0; k < k0 + len; k += kChunkNnz) {
-                const int32_t ke = std::min(k + kChunkNnz, k0 + len);
-                add(i, i + 1, k, ke, ke == k0 + len ? kLastPiece : kPiece, k == k0);
-            }
-            ++i;
-            continue;
-        }
-        const int c = cls[L.rowid[i]];
+    while (i < rows && R.n < kMaxRegions) {
+        const int lanes = lanes_for(L.rowptr[i + 1] - L.rowptr[i]);
         int32_t e = i + 1;
-        while (e < rows && cls[L.rowid[e]] == c && L.rowptr[e + 1] - k0 <= kChunkNnz && e - i < kChunkRows) ++e;
-        add(i, e, k0, L.rowptr[e], kRun, true);
+        while (e < rows && lanes_for(L.rowptr[e + 1] - L.rowptr[e]) == lanes) ++e;
+        R.row0[R.n] = i;
+        R.row1[R.n] = e;
+        R.lanes[R.n] = lanes;
+        work.push_back((int64_t)(L.rowptr[e] - L.rowptr[i]) + (e - i));   // nonzeros + one per row
+        ++R.n;
         i = e;
     }
-    L.nchunk = (int32_t)L.kind.size();
-    // contiguous chunk ranges per CTA, balanced by nonzeros (+ a per-chunk
-    // cost), cut only where a row starts
-    std::vector<int64_t> work(L.nchunk);
-    for (int32_t c = 0; c < L.nchunk; ++c) work[c] = L.chunk[4 * c + 3] - L.chunk[4 * c + 2] + 64;
-    const int64_t total = std::accumulate(work.begin(), work.end(), (int64_t)0);
-    grid = std::max(1, std::min(grid, std::max(L.nchunk, 1)));
-    L.cta_item.assign(grid + 1, L.nchunk);
-    L.cta_item[0] = 0;
-    int64_t acc = 0;
-    int b = 1;
-    for (int32_t c = 0; c < L.nchunk && b < grid; ++c) {
-        acc += work[c];
-        while (b < grid && acc * grid >= total * b) {
-            int32_t cut = c + 1;
-            while (cut < L.nchunk && !cut_ok[cut]) ++cut;
-            L.cta_item[b++] = cut;
-        }
+    if (R.n == 0) {                   // no rows: one empty region
+        R.n = 1;
+        R.row0[0] = R.row1[0] = 0;
+        R.lanes[0] = 1;
+        work.push_back(0);
     }
-    for (int k = 1; k <= grid; ++k) L.cta_item[k] = std::max(L.cta_item[k], L.cta_item[k - 1]);
-    L.grid = grid;
+    // CTAs in proportion to the work, at least one per region and no more
+    // than the region can use
+    ctas = std::max(ctas, R.n);
+    int64_t total = 0;
+    for (int64_t wv : work) total += wv;
+    R.cta0[0] = 0;
+    for (int k = 0; k < R.n; ++k) {
+        const int64_t nrows = R.row1[k] - R.row0[k];
+        const int64_t rows_per_cta = R.lanes[k] == kCtaLanes ? 1 : kBlock / R.lanes[k];
+        const int64_t useful = std::max<int64_t>(1, (nrows + rows_per_cta - 1) / rows_per_cta);
+        int64_t g = total > 0 ? (int64_t)((double)ctas * work[k] / total) : 1;
+        g = std::max<int64_t>(1, std::min(g, useful));
+        R.cta0[k + 1] = R.cta0[k] + (int32_t)g;
+    }
     return L;
 }
 
