@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-1e-4 solve")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--solve-seconds", type=float, default=30.0, help="time limit of the time-to-1e-4 leg")
     return ap.parse_args()
 
 
@@ -143,25 +144,48 @@ def spmv_bytes(P, it, cg, elt=4):
     return {0: it * k1 + cg * k3, 1: it * k2 + cg * k4, "per_launch": {"A_cg": k3, "At_cg": k4}}
 
 
-def cpu_oracle_rate(P, seconds, steps=None):
-    """Time the FP64 oracle's indirect method on this problem (single thread).
-    Returns (iterations, elapsed seconds, setup seconds)."""
-    from oracle import admm
-    t0 = time.perf_counter()
-    S = admm.HSDSolver(P.A, P.b, P.c, P.cone, admm.Settings(linsys="indirect"))
-    setup = time.perf_counter() - t0
-    t1 = time.perf_counter()
-    it = 0
-    while True:
-        S.step()
-        it += 1
-        el = time.perf_counter() - t1
-        if steps is not None:
-            if it >= steps:
+def cpu_oracle_job(workload, seed, seconds, queue):
+    """CPU baseline (runs in a spawned process, in parallel with the GPU
+    legs): the FP64 oracle's indirect method on the same problem, one
+    thread; ADMM iterations are timed after its setup for about `seconds`."""
+    try:
+        P, _ = make_problem(workload, seed)
+        from oracle import admm
+        t0 = time.perf_counter()
+        S = admm.HSDSolver(P.A, P.b, P.c, P.cone, admm.Settings(linsys="indirect"))
+        setup = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        it = 0
+        while True:
+            S.step()
+            it += 1
+            if time.perf_counter() - t1 >= seconds:
                 break
-        elif el >= seconds:
-            break
-    return it, time.perf_counter() - t1, setup, S
+        queue.put({"iters": it, "seconds": time.perf_counter() - t1, "setup": setup})
+    except Exception as e:  # report, never hang the benchmark
+        queue.put({"error": repr(e)})
+
+
+def traffic_record(kind):
+    """DRAM bytes per launch of SpMV kind 0 (A) / 1 (A^T) from the committed
+    ncu summary, if the kernel sources are unchanged since that capture."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_1312_3039_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("spmv.cuh", "kernels.cuh", "common.cuh"):
+        with open(os.path.join(src, f), "rb") as fh:
+            h.update(fh.read())
+    digest = h.hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "spmv_traffic.txt")
+    try:
+        with open(path) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) == 4 and parts[0] == "traffic" and int(parts[1]) == kind and parts[3] == digest:
+                    return float(parts[2]), digest
+    except OSError:
+        pass
+    return None, digest
 
 
 def run_reference(args):
@@ -196,9 +220,18 @@ def run_reference(args):
 
 
 def run_gb300(args):
+    world, rank, local = dist_env()
+    cpu_proc = cpu_q = None
+    if rank == 0 and not args.no_cpu_baseline:
+        # spawned before any CUDA call, so the child never inherits a context
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        cpu_q = ctx.Queue()
+        cpu_proc = ctx.Process(target=cpu_oracle_job, args=(args.workload, args.seed, args.cpu_seconds, cpu_q),
+                               daemon=True)
+        cpu_proc.start()
     import numpy as np
     import torch
-    world, rank, local = dist_env()
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", init_method="env://")
@@ -230,7 +263,7 @@ def run_gb300(args):
         torch.distributed.all_reduce(t)
         return float(t.item())
 
-    S = scs.Solver(P.A, P.b, P.c, P.cone, time_limit_s=120.0, **common)
+    S = scs.Solver(P.A, P.b, P.c, P.cone, time_limit_s=args.solve_seconds, **common)
     # warm-up iterations, then exactly `steps` timed iterations
     S.iterate(args.warmup)
     torch.cuda.synchronize()
@@ -266,8 +299,10 @@ def run_gb300(args):
     achieved = byt[kind] / (prof[kind][0] / 1e3) / 1e9
     peak, peak_src = measured_hbm_peak()
     names = {0: "spmv_A (q = A p, y_acc init)", 1: "spmv_At (A^T q + CG update)"}
+    traffic, src_digest = traffic_record(kind)
     roofline = {"bound": "hbm", "kernel": names[kind], "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
+                "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
+                "kernel_src_digest": src_digest,
                 "algorithmic_bytes_per_cg_launch": byt["per_launch"]["A_cg" if kind == 0 else "At_cg"],
                 "avg_launch_us": 1e3 * prof[kind][0] / prof[kind][1],
                 "other_kernel_avg_us": 1e3 * prof[1 - kind][0] / max(prof[1 - kind][1], 1),
@@ -305,11 +340,19 @@ def run_gb300(args):
                                           f"({args.steps} iterations) + D2H of x, y, s"}
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        it, el, setup, _ = cpu_oracle_rate(P, args.cpu_seconds)
-        cpu = {"value": it / el, "unit": "iter/s", "cores": 1, "kind": "oracle",
-               "sample": f"{it} ADMM iterations of the FP64 oracle (indirect CG, scipy sparse, one thread) on "
-                         f"the same problem after its setup ({setup:.1f} s, not timed)"}
+    if cpu_proc is not None:
+        try:
+            r = cpu_q.get(timeout=600)
+        except Exception as e:
+            r = {"error": "no result: " + repr(e)}
+        cpu_proc.join(timeout=10)
+        if "error" in r:
+            cpu = {"value": None, "unit": "iter/s", "cores": 1, "kind": "oracle", "sample": r["error"]}
+        else:
+            cpu = {"value": r["iters"] / r["seconds"], "unit": "iter/s", "cores": 1, "kind": "oracle",
+                   "sample": f"{r['iters']} ADMM iterations ({r['seconds']:.1f} s) of the FP64 oracle (indirect "
+                             f"CG, scipy sparse, one thread) on the same problem after its setup "
+                             f"({r['setup']:.1f} s, not timed); run in a separate process alongside the GPU legs"}
 
     if rank == 0:
         line = {

@@ -177,6 +177,21 @@ int32_t scs_counters(scs_work *w, int32_t *iters, int64_t *cg_iters);
 /* Sizes of the work object's problem and the device bytes it holds. */
 int32_t scs_dims(scs_work *w, int32_t *m, int32_t *n, int64_t *nnz, int64_t *device_bytes);
 
+/* Euclidean projection, on the device, of `count` vectors stacked back to
+ * back (each of the cone's length m, rows ordered as in scs_cone) onto K
+ * (dual = 0) or onto K* (dual = 1): block by block, the zero cone (its dual
+ * is all of R), the nonnegative and second-order cones (self-dual) and the
+ * exponential cone and its dual (Sec. 6.1; the dual through Moreau,
+ * Eq. "e-moreau").  This puts a predicted warm start back into the cones.
+ * v and out are device pointers to count * m doubles (out may equal v);
+ * *dist2 (host, may be NULL) receives the sum over all vectors of
+ * ||out - v||^2.  Runs on `stream` (a cudaStream_t, or NULL for the legacy
+ * default stream) of the current device and returns when it is done.  It
+ * allocates a small device scratch buffer for the call.  PSD blocks give
+ * SCS_UNSUPPORTED. */
+int32_t scs_project(const scs_cone *k, int32_t dual, const double *v, double *out, int64_t count,
+                    double *dist2, void *stream);
+
 /* Human-readable description of the most recent error on this thread. */
 const char *scs_last_error(void);
 

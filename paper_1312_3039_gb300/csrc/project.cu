@@ -1,0 +1,194 @@
+// Stand-alone cone projection of a batch of vectors on the device
+// (scs_project): Euclidean projection onto K or K* block by block, with the
+// squared distance moved summed by a deterministic grid reduction.  The
+// same projections as the iteration's fused kernel (zero/free, nonnegative,
+// second-order, exponential via Moreau); used to put predicted warm starts
+// back into the cones.
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/scs_gpu.h"
+#include "common.cuh"
+#include "cones.cuh"
+#include "engine_base.h"
+
+namespace scs {
+
+struct ProjCone {
+    int m;                 // rows of one vector
+    int z, l;
+    int nq;
+    const int32_t *q_off;  // row offset of each SOC block
+    const int32_t *q_len;
+    int ep;
+    int exp_off;
+    int64_t count;         // vectors
+    int g_elem, g_soc, g_exp;   // CTAs of each region (grid-stride inside)
+};
+
+// Regions: [0, g_exp) exponential triples (64 per CTA pass), then
+// [.., + g_soc) one warp per SOC block, then the elementwise rows.
+__global__ void __launch_bounds__(kBlock) cone_project_kernel(ProjCone P, int dual, const double *__restrict__ v,
+                                                              double *__restrict__ out, ReduceBuf rb,
+                                                              double *dist2) {
+    double dd = 0.0;
+    const int b = blockIdx.x;
+    if (b < P.g_exp) {
+        const int64_t ntri = P.count * P.ep;
+        for (int64_t t = (int64_t)b * 64 + threadIdx.x; threadIdx.x < 64 && t < ntri; t += (int64_t)P.g_exp * 64) {
+            const int64_t vec = t / P.ep, tri = t % P.ep;
+            const int64_t off = vec * P.m + P.exp_off + 3 * tri;
+            const double a0 = v[off], a1 = v[off + 1], a2 = v[off + 2];
+            double p0, p1, p2;
+            if (dual) proj_exp_dual(a0, a1, a2, p0, p1, p2);
+            else proj_exp(a0, a1, a2, p0, p1, p2);
+            out[off] = p0; out[off + 1] = p1; out[off + 2] = p2;
+            dd += (p0 - a0) * (p0 - a0) + (p1 - a1) * (p1 - a1) + (p2 - a2) * (p2 - a2);
+        }
+    } else if (b < P.g_exp + P.g_soc) {
+        const int lane = threadIdx.x & 31;
+        const int64_t nblk = P.count * P.nq;
+        const int64_t w0 = (int64_t)(b - P.g_exp) * kWarps + (threadIdx.x >> 5);
+        for (int64_t w = w0; w < nblk; w += (int64_t)P.g_soc * kWarps) {
+            const int64_t vec = w / P.nq, blk = w % P.nq;
+            const int64_t off = vec * P.m + P.q_off[blk];
+            const int len = P.q_len[blk];
+            double t0 = 0.0, xx = 0.0;
+            for (int e = lane; e < len; e += 32) {
+                const double t = v[off + e];
+                if (e == 0) t0 = t; else xx += t * t;
+            }
+            xx = warp_sum(xx);
+            t0 = __shfl_sync(0xffffffffu, t0, 0);
+            const double nx = sqrt(xx);
+            double head, tail;
+            if (nx <= t0) { head = t0; tail = 1.0; }
+            else if (nx <= -t0) { head = 0.0; tail = 0.0; }
+            else { head = 0.5 * (t0 + nx); tail = head / nx; }
+            for (int e = lane; e < len; e += 32) {
+                const double t = v[off + e];
+                const double p = e == 0 ? head : tail * t;
+                out[off + e] = p;
+                dd += (p - t) * (p - t);
+            }
+        }
+    } else {
+        const int64_t lin = (int64_t)P.z + P.l;
+        const int64_t total = P.count * lin;
+        for (int64_t i = (int64_t)(b - P.g_exp - P.g_soc) * kBlock + threadIdx.x; i < total;
+             i += (int64_t)P.g_elem * kBlock) {
+            const int64_t vec = i / lin, row = i % lin;
+            const int64_t off = vec * P.m + row;
+            const double t = v[off];
+            double p;
+            if (row < P.z) p = dual ? t : 0.0;       // K* of {0} is R
+            else p = fmax(t, 0.0);
+            out[off] = p;
+            dd += (p - t) * (p - t);
+        }
+    }
+    double red[1] = {dd}, tot[1];
+    if (grid_sum<1>(red, rb, kSiteMisc, tot)) {
+        if (threadIdx.x == 0) *dist2 = tot[0];
+    }
+}
+
+// Region grids for a batch (each region gets CTAs only if it has work).
+inline void project_grid(ProjCone &P, int max_ctas) {
+    const int64_t lin = P.count * ((int64_t)P.z + P.l);
+    const int64_t soc = P.count * P.nq, exp_ = P.count * P.ep;
+    P.g_exp = exp_ ? (int)std::min<int64_t>((exp_ + 63) / 64, max_ctas / 4) : 0;
+    P.g_soc = soc ? (int)std::min<int64_t>((soc + kWarps - 1) / kWarps, max_ctas / 4) : 0;
+    P.g_elem = lin ? (int)std::min<int64_t>((lin + kBlock - 1) / kBlock, max_ctas / 2) : 0;
+    if (P.g_exp + P.g_soc + P.g_elem == 0) P.g_elem = 1;
+    if (P.g_exp == 0 && exp_) P.g_exp = 1;
+    if (P.g_soc == 0 && soc) P.g_soc = 1;
+}
+
+// Validate the cone, fill the SOC tables (host) and the row offsets.
+inline int project_setup(const scs_cone *k, int64_t count, ProjCone &P, std::vector<int32_t> &qoff,
+                         std::vector<int32_t> &qlen, std::string &err) {
+    if (!k || count < 0) { err = "bad argument"; return SCS_INVALID_INPUT; }
+    if (k->z < 0 || k->l < 0 || k->nq < 0 || k->ns < 0 || k->ep < 0 || (k->nq > 0 && !k->q)) {
+        err = "bad cone";
+        return SCS_INVALID_INPUT;
+    }
+    if (k->ns > 0) { err = "PSD cones are not handled by this build"; return SCS_UNSUPPORTED; }
+    int64_t off = (int64_t)k->z + k->l;
+    qoff.clear();
+    qlen.clear();
+    for (int i = 0; i < k->nq; ++i) {
+        if (k->q[i] < 1) { err = "SOC size must be >= 1"; return SCS_INVALID_INPUT; }
+        qoff.push_back((int32_t)off);
+        qlen.push_back(k->q[i]);
+        off += k->q[i];
+    }
+    P.exp_off = (int)off;
+    off += 3 * (int64_t)k->ep;
+    if (off > (int64_t)1 << 30) { err = "cone too large"; return SCS_UNSUPPORTED; }
+    P.m = (int)off;
+    P.z = k->z;
+    P.l = k->l;
+    P.nq = k->nq;
+    P.ep = k->ep;
+    P.count = count;
+    return 0;
+}
+
+thread_local std::string g_project_error;
+
+}  // namespace scs
+
+extern "C" int32_t scs_project(const scs_cone *k, int32_t dual, const double *v, double *out, int64_t count,
+                               double *dist2, void *stream) {
+    using namespace scs;
+    ProjCone P{};
+    std::vector<int32_t> qoff, qlen;
+    std::string err;
+    int rc = project_setup(k, count, P, qoff, qlen, err);
+    if (rc) return rc;
+    if (count == 0 || P.m == 0) {
+        if (dist2) *dist2 = 0.0;
+        return 0;
+    }
+    if (!v || !out) return SCS_INVALID_INPUT;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))
+        return SCS_DEVICE_ERROR;
+    project_grid(P, sms * 8);
+    const int grid = P.g_exp + P.g_soc + P.g_elem;
+    // scratch for this call: partial sums, arrival counters, SOC tables, result
+    double *partials = nullptr, *res = nullptr;
+    unsigned *counter = nullptr;
+    int32_t *tables = nullptr;
+    rc = 0;
+    if (cudaMalloc(&partials, sizeof(double) * kMaxRed * grid) || cudaMalloc(&counter, sizeof(unsigned) * kSiteCount) ||
+        cudaMalloc(&res, sizeof(double)) || cudaMalloc(&tables, sizeof(int32_t) * (2 * qoff.size() + 2)))
+        rc = SCS_DEVICE_ERROR;
+    if (!rc) {
+        if (!qoff.empty() && (cudaMemcpyAsync(tables, qoff.data(), 4 * qoff.size(), cudaMemcpyHostToDevice, s) ||
+                              cudaMemcpyAsync(tables + qoff.size(), qlen.data(), 4 * qlen.size(),
+                                              cudaMemcpyHostToDevice, s)))
+            rc = SCS_DEVICE_ERROR;
+        if (cudaMemsetAsync(counter, 0, sizeof(unsigned) * kSiteCount, s)) rc = SCS_DEVICE_ERROR;
+    }
+    if (!rc) {
+        P.q_off = tables;
+        P.q_len = tables + qoff.size();
+        ReduceBuf rb{partials, counter, grid};
+        cone_project_kernel<<<grid, kBlock, 0, s>>>(P, dual ? 1 : 0, v, out, rb, res);
+        double h = 0.0;
+        if (cudaGetLastError() || cudaMemcpyAsync(&h, res, sizeof(double), cudaMemcpyDeviceToHost, s) ||
+            cudaStreamSynchronize(s))
+            rc = SCS_DEVICE_ERROR;
+        if (!rc && dist2) *dist2 = h;
+    }
+    cudaFree(partials);
+    cudaFree(counter);
+    cudaFree(res);
+    cudaFree(tables);
+    return rc;
+}

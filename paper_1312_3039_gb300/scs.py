@@ -96,6 +96,8 @@ def lib():
         L.scs_dims.restype = I32
         L.scs_counters.argtypes = [P, C.POINTER(I32), I64]
         L.scs_counters.restype = I32
+        L.scs_project.argtypes = [C.POINTER(ConeC), I32, C.c_void_p, C.c_void_p, C.c_int64, D, C.c_void_p]
+        L.scs_project.restype = I32
         L.scs_last_error.argtypes = []
         L.scs_last_error.restype = C.c_char_p
         _lib_handle = L
@@ -118,6 +120,26 @@ def default_settings(**kw) -> Settings:
 
 def _dptr(a):
     return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+def cone_struct(cone):
+    """ctypes scs_cone for a cone description (keeps its arrays alive)."""
+    q = np.ascontiguousarray(list(getattr(cone, "q", ())) or [0], dtype=np.int32)
+    s = np.ascontiguousarray(list(getattr(cone, "s", ())) or [0], dtype=np.int32)
+    kc = ConeC(int(cone.z), int(cone.l), q.ctypes.data_as(C.POINTER(C.c_int32)), len(getattr(cone, "q", ())),
+               s.ctypes.data_as(C.POINTER(C.c_int32)), len(getattr(cone, "s", ())), int(cone.ep))
+    return kc, (q, s)
+
+
+def project(cone, dual, v_ptr, out_ptr, count, stream=None):
+    """scs_project on device pointers (ints); returns the summed ||out - v||^2."""
+    kc, keep = cone_struct(cone)
+    d2 = C.c_double(0.0)
+    rc = lib().scs_project(C.byref(kc), int(dual), C.c_void_p(v_ptr), C.c_void_p(out_ptr), int(count),
+                           C.byref(d2), C.c_void_p(stream) if stream else None)
+    if rc != 0:
+        raise ScsError(rc, last_error())
+    return d2.value
 
 
 class ScsError(RuntimeError):
