@@ -192,6 +192,24 @@ int32_t scs_dims(scs_work *w, int32_t *m, int32_t *n, int64_t *nnz, int64_t *dev
 int32_t scs_project(const scs_cone *k, int32_t dual, const double *v, double *out, int64_t count,
                     double *dist2, void *stream);
 
+/* scs_project for callers that cannot allocate device memory -- for
+ * example an application whose memory pool already owns the whole GPU, or
+ * a runtime that forbids cudaMalloc while it captures or serves requests.
+ * The paper has no counterpart: this is a property of the library.
+ * Same arguments, result and stream semantics as scs_project, but the call
+ * allocates nothing: its scratch (the reduction's counters and partial sums,
+ * the SOC block tables and the result) lives in one fixed-size device array
+ * inside the library, which every GPU that loads the library holds
+ * (about 41 KB) until the process exits.
+ *   - The first call on a device looks up that array's device address, with
+ *     the device current; make that first call before any stream capture.
+ *   - Limits: at most 4096 SOC blocks per cone (SCS_UNSUPPORTED otherwise).
+ *   - Every call shares the one array, and each call resets the part that
+ *     must start at zero; calls that overlap on the GPU (different streams or
+ *     threads at the same time) race on it and must not be issued. */
+int32_t scs_project_noalloc(const scs_cone *k, int32_t dual, const double *v, double *out, int64_t count,
+                            double *dist2, void *stream);
+
 /* Human-readable description of the most recent error on this thread. */
 const char *scs_last_error(void);
 

@@ -6,6 +6,8 @@
 // back into the cones.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -191,4 +193,91 @@ extern "C" int32_t scs_project(const scs_cone *k, int32_t dual, const double *v,
     cudaFree(res);
     cudaFree(tables);
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// scs_project_noalloc: the same projection for callers that cannot allocate
+// device memory (for example code running inside a memory pool that owns
+// the whole device, or a runtime that forbids cudaMalloc while it is
+// capturing or serving).  Its scratch -- the reduction's arrival counters and
+// partial sums, the SOC block tables and the result -- lives in one
+// file-scope device array of fixed size, held by every GPU that loads the
+// library until the process exits.
+// ---------------------------------------------------------------------------
+namespace scs {
+
+constexpr int kNoAllocMaxCtas = 1024;      // CTAs of one projection launch
+constexpr int kNoAllocMaxSoc = 4096;       // SOC blocks per cone
+constexpr size_t kNoAllocCounterOff = 0;                                   // kSiteCount unsigned
+constexpr size_t kNoAllocResultOff = 128;                                  // one double
+constexpr size_t kNoAllocPartialOff = 256;                                 // kNoAllocMaxCtas doubles
+constexpr size_t kNoAllocTableOff = kNoAllocPartialOff + 8 * kNoAllocMaxCtas;   // 2 * kNoAllocMaxSoc int32
+constexpr size_t kNoAllocBytes = kNoAllocTableOff + 8 * kNoAllocMaxSoc;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// device address of the scratch array on each device (set up once per device)
+static void *g_noalloc_addr[64];
+static std::mutex g_noalloc_mutex;
+
+}  // namespace scs
+
+extern "C" int32_t scs_project_noalloc(const scs_cone *k, int32_t dual, const double *v, double *out,
+                                       int64_t count, double *dist2, void *stream) {
+    using namespace scs;
+    ProjCone P{};
+    std::vector<int32_t> qoff, qlen;
+    std::string err;
+    int rc = project_setup(k, count, P, qoff, qlen, err);
+    if (rc) return rc;
+    if ((int64_t)qoff.size() > kNoAllocMaxSoc) return SCS_UNSUPPORTED;   // more SOC blocks than the scratch holds
+    if (count == 0 || P.m == 0) {
+        if (dist2) *dist2 = 0.0;
+        return 0;
+    }
+    if (!v || !out) return SCS_INVALID_INPUT;
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return SCS_DEVICE_ERROR;
+    void *base = nullptr;
+    {
+        // first call on this device: look up the array's device address
+        // (host code cannot use the symbol's host-side name as a pointer)
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_addr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SCS_DEVICE_ERROR;
+            g_noalloc_addr[dev] = p;
+        }
+        base = g_noalloc_addr[dev];
+    }
+    unsigned char *sc = static_cast<unsigned char *>(base);
+    unsigned *counter = reinterpret_cast<unsigned *>(sc + kNoAllocCounterOff);
+    double *res = reinterpret_cast<double *>(sc + kNoAllocResultOff);
+    double *partials = reinterpret_cast<double *>(sc + kNoAllocPartialOff);
+    int32_t *tables = reinterpret_cast<int32_t *>(sc + kNoAllocTableOff);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    project_grid(P, std::min(sms * 8, kNoAllocMaxCtas));
+    const int grid = P.g_exp + P.g_soc + P.g_elem;
+    if (grid > kNoAllocMaxCtas) return SCS_UNSUPPORTED;
+    // the counters must start at zero (the array keeps the last call's contents)
+    if (cudaMemsetAsync(counter, 0, sizeof(unsigned) * kSiteCount, s) != cudaSuccess) return SCS_DEVICE_ERROR;
+    if (!qoff.empty()) {
+        if (cudaMemcpyAsync(tables, qoff.data(), 4 * qoff.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(tables + kNoAllocMaxSoc, qlen.data(), 4 * qlen.size(), cudaMemcpyHostToDevice, s) !=
+                cudaSuccess)
+            return SCS_DEVICE_ERROR;
+    }
+    P.q_off = tables;
+    P.q_len = tables + kNoAllocMaxSoc;
+    ReduceBuf rb{partials, counter, grid};
+    cone_project_kernel<<<grid, kBlock, 0, s>>>(P, dual ? 1 : 0, v, out, rb, res);
+    double h = 0.0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&h, res, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return SCS_DEVICE_ERROR;
+    if (dist2) *dist2 = h;
+    return 0;
 }

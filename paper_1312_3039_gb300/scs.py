@@ -98,6 +98,10 @@ def lib():
         L.scs_counters.restype = I32
         L.scs_project.argtypes = [C.POINTER(ConeC), I32, C.c_void_p, C.c_void_p, C.c_int64, D, C.c_void_p]
         L.scs_project.restype = I32
+        if hasattr(L, "scs_project_noalloc"):
+            L.scs_project_noalloc.argtypes = [C.POINTER(ConeC), I32, C.c_void_p, C.c_void_p, C.c_int64, D,
+                                              C.c_void_p]
+            L.scs_project_noalloc.restype = I32
         L.scs_last_error.argtypes = []
         L.scs_last_error.restype = C.c_char_p
         _lib_handle = L
@@ -137,6 +141,18 @@ def project(cone, dual, v_ptr, out_ptr, count, stream=None):
     d2 = C.c_double(0.0)
     rc = lib().scs_project(C.byref(kc), int(dual), C.c_void_p(v_ptr), C.c_void_p(out_ptr), int(count),
                            C.byref(d2), C.c_void_p(stream) if stream else None)
+    if rc != 0:
+        raise ScsError(rc, last_error())
+    return d2.value
+
+
+def project_noalloc(cone, dual, v_ptr, out_ptr, count, stream=None):
+    """scs_project_noalloc (no device allocation; scratch in the library's
+    static device array); returns the summed ||out - v||^2."""
+    kc, keep = cone_struct(cone)
+    d2 = C.c_double(0.0)
+    rc = lib().scs_project_noalloc(C.byref(kc), int(dual), C.c_void_p(v_ptr), C.c_void_p(out_ptr), int(count),
+                                   C.byref(d2), C.c_void_p(stream) if stream else None)
     if rc != 0:
         raise ScsError(rc, last_error())
     return d2.value
