@@ -56,12 +56,13 @@ struct EpiAInit {
     Scalars *S;
     int n, N;
     double wtau;
+    struct In { double w, b; };
     __device__ bool skip() const { return false; }
     __device__ void begin() { wtau = u[N - 1] + v[N - 1]; }
-    __device__ void row(int i, T s, double (&red)[NV]) {
-        const double w = u[n + i] + v[n + i];
-        yacc[i] = static_cast<T>(w - wtau * b[i] + static_cast<double>(s));
-        red[0] += w * w;
+    __device__ In load(int i) const { return In{u[n + i] + v[n + i], b[i]}; }
+    __device__ void row(int i, T s, const In &in, double (&red)[NV]) {
+        yacc[i] = static_cast<T>(in.w - wtau * in.b + static_cast<double>(s));
+        red[0] += in.w * in.w;
     }
     __device__ void finish(const double (&t)[NV]) { S->ww_y = t[0]; }
 };
@@ -80,12 +81,14 @@ struct EpiAtInit {
     CondHandle cond;
     int N;
     double wtau;
+    struct In { double ux, c; T z, d; };
     __device__ bool skip() const { return false; }
     __device__ void begin() { wtau = u[N - 1] + v[N - 1]; }
-    __device__ void row(int j, T s, double (&red)[NV]) {
-        const double ux = u[j];
-        const T rj = static_cast<T>(ux - wtau * c[j] - static_cast<double>(z[j]) - static_cast<double>(s));
-        const T sj = rj / diag[j];
+    __device__ In load(int j) const { return In{u[j], c[j], z[j], diag[j]}; }
+    __device__ void row(int j, T s, const In &in, double (&red)[NV]) {
+        const double ux = in.ux;
+        const T rj = static_cast<T>(ux - wtau * in.c - static_cast<double>(in.z) - static_cast<double>(s));
+        const T sj = rj / in.d;
         r[j] = rj;
         p[j] = sj;
         red[0] += static_cast<double>(rj) * sj;
@@ -124,9 +127,11 @@ struct EpiACG {
     static constexpr int kSite = kSiteACG;
     T *q;
     Scalars *S;
+    struct In {};
     __device__ bool skip() const { return !S->active; }
     __device__ void begin() {}
-    __device__ void row(int i, T s, double (&red)[NV]) {
+    __device__ In load(int) const { return In{}; }
+    __device__ void row(int i, T s, const In &, double (&red)[NV]) {
         q[i] = s;
         red[0] += static_cast<double>(s) * s;
     }
@@ -147,15 +152,17 @@ struct EpiAtCG {
     T *z, *r, *p;
     Scalars *S;
     T alpha;
+    struct In { T p, z, r, d; };
     __device__ bool skip() const { return !S->active; }
     __device__ void begin() { alpha = static_cast<T>(S->alpha); }
-    __device__ void row(int j, T s, double (&red)[NV]) {
-        const T pj = p[j];
+    __device__ In load(int j) const { return In{p[j], z[j], r[j], diag[j]}; }
+    __device__ void row(int j, T s, const In &in, double (&red)[NV]) {
+        const T pj = in.p;
         const T gp = pj + s;
-        z[j] = z[j] + alpha * pj;
-        const T rj = r[j] - alpha * gp;
+        z[j] = in.z + alpha * pj;
+        const T rj = in.r - alpha * gp;
         r[j] = rj;
-        const T sj = rj / diag[j];
+        const T sj = rj / in.d;
         red[0] += static_cast<double>(rj) * sj;
         red[1] += static_cast<double>(rj) * rj;
     }
@@ -369,16 +376,18 @@ struct EpiChkA {
     Scalars *S;
     int n, N;
     double tau;
+    struct In { double vs, b, d, uy; };
     __device__ bool skip() const { return false; }
     __device__ void begin() { tau = u[N - 1]; }
-    __device__ void row(int i, double s, double (&red)[NV]) {
+    __device__ In load(int i) const { return In{v[n + i], b[i], D[i], u[n + i]}; }
+    __device__ void row(int i, double s, const In &in, double (&red)[NV]) {
         ax[i] = s;
-        const double a = s + v[n + i];
-        const double pr = (a - tau * b[i]) / D[i];
-        const double ub = a / D[i];
+        const double a = s + in.vs;
+        const double pr = (a - tau * in.b) / in.d;
+        const double ub = a / in.d;
         red[0] += pr * pr;
         red[1] += ub * ub;
-        red[2] += b[i] * u[n + i];
+        red[2] += in.b * in.uy;
     }
     __device__ void finish(const double (&t)[NV]) {
         S->pri2 = t[0];
@@ -394,14 +403,16 @@ struct EpiChkAt {
     Scalars *S;
     int N;
     double tau;
+    struct In { double c, e, ux; };
     __device__ bool skip() const { return false; }
     __device__ void begin() { tau = u[N - 1]; }
-    __device__ void row(int j, double s, double (&red)[NV]) {
-        const double du = (s + tau * c[j]) / E[j];
-        const double in = s / E[j];
+    __device__ In load(int j) const { return In{c[j], E[j], u[j]}; }
+    __device__ void row(int j, double s, const In &in, double (&red)[NV]) {
+        const double du = (s + tau * in.c) / in.e;
+        const double inf = s / in.e;
         red[0] += du * du;
-        red[1] += in * in;
-        red[2] += c[j] * u[j];
+        red[1] += inf * inf;
+        red[2] += in.c * in.ux;
     }
     __device__ void finish(const double (&t)[NV]) {
         S->dual2 = t[0];

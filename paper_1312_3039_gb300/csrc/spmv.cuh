@@ -29,17 +29,22 @@
 
 namespace scs {
 
-constexpr int kWarpRow = 4096;       // rows up to this length: at most a warp (longer: one CTA)
-constexpr int kMaxRegions = 8;
-constexpr int kCtaLanes = kBlock;    // lanes per row in the CTA region
+constexpr int kWarpRow = 4096;       // rows up to this length: one warp (longer: one CTA)
+constexpr int kMaxRegions = 10;
+constexpr int kWarpLoop = 33;        // region tag: one warp per row, looping over the row
+constexpr int kCtaLanes = kBlock;    // region tag: one CTA per row
+constexpr int kRowsPerLane = 2;      // rows a lane of a small group serves per step
 
-// lanes per row for a row length
+// lanes per row for a row length: groups of 1..32 lanes give every lane at
+// most 4 nonzeros; longer rows loop with a warp, the longest with a CTA
 inline int lanes_for(int32_t len) {
     if (len <= 4) return 1;
     if (len <= 8) return 2;
     if (len <= 16) return 4;
     if (len <= 32) return 8;
-    if (len <= kWarpRow) return 32;
+    if (len <= 64) return 16;
+    if (len <= 128) return 32;
+    if (len <= kWarpRow) return kWarpLoop;
     return kCtaLanes;
 }
 
@@ -47,7 +52,7 @@ struct SpmvRegions {
     int32_t n;                        // regions in use
     int32_t row0[kMaxRegions];        // stored rows [row0, row1)
     int32_t row1[kMaxRegions];
-    int32_t lanes[kMaxRegions];       // 1, 2, 4, 8, 32 or kCtaLanes
+    int32_t lanes[kMaxRegions];       // 1, 2, 4, 8, 16, 32, kWarpLoop or kCtaLanes
     int32_t cta0[kMaxRegions + 1];    // CTAs [cta0[i], cta0[i+1]) serve region i
 };
 
@@ -67,28 +72,86 @@ __device__ __forceinline__ Acc fmul(TA a, TX x) {
     return static_cast<Acc>(a) * static_cast<Acc>(x);
 }
 
+// Groups of L <= 32 lanes: a row of such a group has at most 4 L nonzeros,
+// so each lane holds at most 4 of them and the loop is unrolled and
+// predicated.  Each lane serves kRowsPerLane rows per step, and the
+// epilogue's inputs are loaded (Epi::load) as soon as the row id is known, so
+// the row pointers, matrix entries, epilogue inputs and gathers of several
+// rows are in flight together.
 template <int L, typename TA, typename TX, typename Acc, typename Epi>
-__device__ __forceinline__ void spmv_groups(const Csr<TA> &A, const TX *__restrict__ x, Epi &epi, double (&red)[Epi::NV],
-                                            int r0, int r1, int cta, int nctas) {
-    // groups of L lanes, 32 / L groups per warp; the loop runs while any
-    // group of the warp has a row, so shuffles see the whole warp
-    constexpr int G = 32 / L;
+__device__ __forceinline__ void spmv_small_groups(const Csr<TA> &A, const TX *__restrict__ x, Epi &epi,
+                                                  double (&red)[Epi::NV], int r0, int r1, int cta, int nctas) {
+    constexpr int G = 32 / L;                 // groups per warp
+    constexpr int R = kRowsPerLane;
     const int lane = threadIdx.x & 31, g = lane / L, gl = lane % L;
     const int warp = cta * kWarps + (threadIdx.x >> 5), nwarps = nctas * kWarps;
     const int32_t *__restrict__ rowptr = A.rowptr;
     const int32_t *__restrict__ col = A.col;
     const TA *__restrict__ val = A.val;
-    for (int base = r0 + warp * G; base < r1; base += nwarps * G) {
-        const int r = base + g;
-        Acc sacc = 0;
-        if (r < r1) {
-            const int k0 = rowptr[r], k1 = rowptr[r + 1];
-#pragma unroll 4
-            for (int k = k0 + gl; k < k1; k += L) sacc += fmul<Acc>(__ldcs(val + k), __ldg(x + __ldcs(col + k)));
+    // the loop runs while any row of the warp's step exists, so the shuffles
+    // below always see the whole warp
+    for (int base = r0 + warp * G * R; base < r1; base += nwarps * G * R) {
+        int k0[R], k1[R], rid[R];
+        bool ok[R];
+        typename Epi::In in[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int r = base + q * G + g;
+            ok[q] = r < r1;
+            k0[q] = ok[q] ? rowptr[r] : 0;
+            k1[q] = ok[q] ? rowptr[r + 1] : 0;
+            rid[q] = ok[q] ? A.rowid[r] : 0;
         }
 #pragma unroll
-        for (int o = L >> 1; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-        if (r < r1 && gl == 0) epi.row(A.rowid[r], sacc, red);
+        for (int q = 0; q < R; ++q)
+            if (ok[q] && gl == 0) in[q] = epi.load(rid[q]);
+        int c[R][4];
+        TA v[R][4];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int k = k0[q] + gl + j * L;
+                const bool has = k < k1[q];
+                c[q][j] = has ? __ldcs(col + k) : 0;
+                v[q][j] = has ? __ldcs(val + k) : TA(0);
+            }
+        }
+        Acc acc[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            acc[q] = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (k0[q] + gl + j * L < k1[q]) acc[q] += fmul<Acc>(v[q][j], __ldg(x + c[q][j]));
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+#pragma unroll
+            for (int o = L >> 1; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+            if (ok[q] && gl == 0) epi.row(rid[q], acc[q], in[q], red);
+        }
+    }
+}
+
+// a warp per row (rows of up to kWarpRow nonzeros)
+template <typename TA, typename TX, typename Acc, typename Epi>
+__device__ __forceinline__ void spmv_warp_rows(const Csr<TA> &A, const TX *__restrict__ x, Epi &epi,
+                                               double (&red)[Epi::NV], int r0, int r1, int cta, int nctas) {
+    const int lane = threadIdx.x & 31;
+    const int warp = cta * kWarps + (threadIdx.x >> 5), nwarps = nctas * kWarps;
+    const int32_t *__restrict__ col = A.col;
+    const TA *__restrict__ val = A.val;
+    for (int r = r0 + warp; r < r1; r += nwarps) {
+        const int k0 = A.rowptr[r], k1 = A.rowptr[r + 1];
+        const int rid = A.rowid[r];
+        typename Epi::In in;
+        if (lane == 0) in = epi.load(rid);
+        Acc sacc = 0;
+#pragma unroll 4
+        for (int k = k0 + lane; k < k1; k += 32) sacc += fmul<Acc>(__ldcs(val + k), __ldg(x + __ldcs(col + k)));
+        sacc = warp_sum(sacc);
+        if (lane == 0) epi.row(rid, sacc, in, red);
     }
 }
 
@@ -107,23 +170,28 @@ __global__ void __launch_bounds__(kBlock) spmv_kernel(Csr<TA> A, const TX *__res
     const int r0 = A.reg.row0[ri], r1 = A.reg.row1[ri];
     const int cta = b - A.reg.cta0[ri], nctas = A.reg.cta0[ri + 1] - A.reg.cta0[ri];
     switch (A.reg.lanes[ri]) {
-        case 1: spmv_groups<1, TA, TX, Acc>(A, x, epi, red, r0, r1, cta, nctas); break;
-        case 2: spmv_groups<2, TA, TX, Acc>(A, x, epi, red, r0, r1, cta, nctas); break;
-        case 4: spmv_groups<4, TA, TX, Acc>(A, x, epi, red, r0, r1, cta, nctas); break;
-        case 8: spmv_groups<8, TA, TX, Acc>(A, x, epi, red, r0, r1, cta, nctas); break;
-        case 32: spmv_groups<32, TA, TX, Acc>(A, x, epi, red, r0, r1, cta, nctas); break;
+        case 1: spmv_small_groups<1, TA, TX, Acc>(A, x, epi, red, r0, r1, cta, nctas); break;
+        case 2: spmv_small_groups<2, TA, TX, Acc>(A, x, epi, red, r0, r1, cta, nctas); break;
+        case 4: spmv_small_groups<4, TA, TX, Acc>(A, x, epi, red, r0, r1, cta, nctas); break;
+        case 8: spmv_small_groups<8, TA, TX, Acc>(A, x, epi, red, r0, r1, cta, nctas); break;
+        case 16: spmv_small_groups<16, TA, TX, Acc>(A, x, epi, red, r0, r1, cta, nctas); break;
+        case 32: spmv_small_groups<32, TA, TX, Acc>(A, x, epi, red, r0, r1, cta, nctas); break;
+        case kWarpLoop: spmv_warp_rows<TA, TX, Acc>(A, x, epi, red, r0, r1, cta, nctas); break;
         default: {
             // one CTA per row
             const int tid = threadIdx.x;
             for (int r = r0 + cta; r < r1; r += nctas) {
                 const int k0 = A.rowptr[r], k1 = A.rowptr[r + 1];
+                const int rid = A.rowid[r];
+                typename Epi::In in;
+                if (tid == 0) in = epi.load(rid);
                 Acc sacc = 0;
 #pragma unroll 4
                 for (int k = k0 + tid; k < k1; k += kBlock)
                     sacc += fmul<Acc>(__ldcs(A.val + k), __ldg(x + __ldcs(A.col + k)));
                 double t[1] = {static_cast<double>(sacc)};
                 block_sum<1>(t);
-                if (tid == 0) epi.row(A.rowid[r], static_cast<Acc>(t[0]), red);
+                if (tid == 0) epi.row(rid, static_cast<Acc>(t[0]), in, red);
             }
         }
     }
@@ -191,7 +259,18 @@ inline SpmvLayout<V> spmv_layout(const std::vector<int32_t> &rp, const std::vect
         R.row0[R.n] = i;
         R.row1[R.n] = e;
         R.lanes[R.n] = lanes;
-        work.push_back((int64_t)(L.rowptr[e] - L.rowptr[i]) + (e - i));   // nonzeros + one per row
+        // cost in warp steps (each step is one chain of dependent loads):
+        // small groups serve 32 / lanes * kRowsPerLane rows per step, a
+        // looping warp 128 nonzeros per step, a CTA 1024 per step of 8 warps
+        int64_t steps = 0;
+        if (lanes <= 32) {
+            steps = (e - i + (32 / lanes) * kRowsPerLane - 1) / ((32 / lanes) * kRowsPerLane);
+        } else if (lanes == kWarpLoop) {
+            for (int32_t r = i; r < e; ++r) steps += (L.rowptr[r + 1] - L.rowptr[r] + 127) / 128;
+        } else {
+            for (int32_t r = i; r < e; ++r) steps += kWarps * ((L.rowptr[r + 1] - L.rowptr[r] + 1023) / 1024);
+        }
+        work.push_back(steps);
         ++R.n;
         i = e;
     }
@@ -209,7 +288,7 @@ inline SpmvLayout<V> spmv_layout(const std::vector<int32_t> &rp, const std::vect
     R.cta0[0] = 0;
     for (int k = 0; k < R.n; ++k) {
         const int64_t nrows = R.row1[k] - R.row0[k];
-        const int64_t rows_per_cta = R.lanes[k] == kCtaLanes ? 1 : kBlock / R.lanes[k];
+        const int64_t rows_per_cta = R.lanes[k] == kCtaLanes ? 1 : R.lanes[k] == kWarpLoop ? kWarps : (int64_t)kBlock / R.lanes[k] * kRowsPerLane;
         const int64_t useful = std::max<int64_t>(1, (nrows + rows_per_cta - 1) / rows_per_cta);
         int64_t g = total > 0 ? (int64_t)((double)ctas * work[k] / total) : 1;
         g = std::max<int64_t>(1, std::min(g, useful));

@@ -2,8 +2,9 @@
 satisfies what the kernel relies on: the stored rows are a permutation of the
 matrix rows carrying the same columns; the regions tile the stored rows in
 order, every row of a region gets the lane count its length calls for (1 up
-to 4 nonzeros, 2 up to 8, 4 up to 16, 8 up to 32, 32 up to 4096, a CTA
-beyond), and every region gets at least one CTA."""
+to 4 nonzeros, 2 up to 8, 4 up to 16, 8 up to 32, 16 up to 64, 32 up to 128,
+a looping warp up to 4096, a CTA beyond), and every region gets at least one
+CTA."""
 import ctypes
 import os
 import shutil
@@ -37,7 +38,7 @@ def layout(lib, A, ctas):
     o_rp = np.zeros(rows + 1, np.int32)
     o_cl = np.zeros(max(nnz, 1), np.int32)
     o_id = np.zeros(max(rows, 1), np.int32)
-    info = np.zeros(1 + 4 * 8, np.int32)
+    info = np.zeros(1 + 4 * 10, np.int32)
     P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     assert lib.host_spmv_layout(rows, P(rp), P(cl), ctas, P(o_rp), P(o_cl), P(o_id), P(info)) == 0
     n = int(info[0])
@@ -46,7 +47,8 @@ def layout(lib, A, ctas):
 
 
 def lanes_for(n):
-    return 1 if n <= 4 else 2 if n <= 8 else 4 if n <= 16 else 8 if n <= 32 else 32 if n <= 4096 else 256
+    return (1 if n <= 4 else 2 if n <= 8 else 4 if n <= 16 else 8 if n <= 32 else 16 if n <= 64 else 32 if n <= 128
+            else 33 if n <= 4096 else 256)
 
 
 def check(A, L):
