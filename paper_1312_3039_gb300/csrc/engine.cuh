@@ -81,8 +81,10 @@ class Engine : public EngineBase {
         }
         u[N_ - 1] = 1.0;
         v[N_ - 1] = 0.0;
-        SCS_CUDA(cudaMemcpyAsync(u_, u.data(), sizeof(double) * N_, cudaMemcpyHostToDevice, stream_));
-        SCS_CUDA(cudaMemcpyAsync(v_, v.data(), sizeof(double) * N_, cudaMemcpyHostToDevice, stream_));
+        std::vector<T> ut(u.begin(), u.end()), vt(v.begin(), v.end());
+        SCS_CUDA(cudaMemcpyAsync(u_, ut.data(), sizeof(T) * N_, cudaMemcpyHostToDevice, stream_));
+        SCS_CUDA(cudaMemcpyAsync(v_, vt.data(), sizeof(T) * N_, cudaMemcpyHostToDevice, stream_));
+        SCS_CUDA(cudaStreamSynchronize(stream_));
         // the warm start is taken to be about as accurate as the tolerances
         double nrm = 0.0;
         for (int i = 0; i < N_; ++i) nrm += u[i] * u[i] + v[i] * v[i];
@@ -135,8 +137,15 @@ class Engine : public EngineBase {
     int get_iterates(double *u, double *v) override {
         SCS_CUDA(cudaSetDevice(device_));
         SCS_CUDA(cudaStreamSynchronize(stream_));
-        if (u) SCS_CUDA(cudaMemcpy(u, u_, sizeof(double) * N_, cudaMemcpyDeviceToHost));
-        if (v) SCS_CUDA(cudaMemcpy(v, v_, sizeof(double) * N_, cudaMemcpyDeviceToHost));
+        std::vector<T> h(N_);
+        if (u) {
+            SCS_CUDA(cudaMemcpy(h.data(), u_, sizeof(T) * N_, cudaMemcpyDeviceToHost));
+            for (int i = 0; i < N_; ++i) u[i] = static_cast<double>(h[i]);
+        }
+        if (v) {
+            SCS_CUDA(cudaMemcpy(h.data(), v_, sizeof(T) * N_, cudaMemcpyDeviceToHost));
+            for (int i = 0; i < N_; ++i) v[i] = static_cast<double>(h[i]);
+        }
         return 0;
     }
 
@@ -192,7 +201,7 @@ class Engine : public EngineBase {
         if (status == 0) status = inaccurate_status();
         (void)timed_out;
         // outputs
-        output_kernel<<<grid_for(n_ + 2 * m_), kBlock, 0, stream_>>>(n_, m_, status, u_, v_, D_, E_, ax_, S_,
+        output_kernel<T><<<grid_for(n_ + 2 * m_), kBlock, 0, stream_>>>(n_, m_, status, u_, v_, D_, E_, ax_, S_,
                                                                     out_, out_ + n_, out_ + n_ + m_);
         SCS_CUDA(cudaGetLastError());
         if (x) SCS_CUDA(cudaMemcpyAsync(x, out_, sizeof(double) * n_, cudaMemcpyDeviceToHost, stream_));
@@ -282,8 +291,8 @@ class Engine : public EngineBase {
         SCS_CUDA(cudaStreamSynchronize(stream_));     // host layouts are released below
 
         // vectors
-        u_ = dalloc<double>(N_);
-        v_ = dalloc<double>(N_);
+        u_ = dalloc<T>(N_);
+        v_ = dalloc<T>(N_);
         b_ = upload(P.b);
         c_ = upload(P.c);
         D_ = dalloc<double>(m_);
@@ -394,6 +403,18 @@ class Engine : public EngineBase {
             foreach_kernel<<<grid_for(m_), kBlock, 0, stream_>>>([=] __device__(int i) { bd[i] *= sg * Dd[i]; }, m_);
             foreach_kernel<<<grid_for(n_), kBlock, 0, stream_>>>([=] __device__(int j) { cd[j] *= rh * Ed[j]; }, n_);
         }
+        // working copies of b^, c^ in the iteration's precision
+        if (std::is_same<T, double>::value) {
+            bT_ = reinterpret_cast<T *>(b_);
+            cT_ = reinterpret_cast<T *>(c_);
+        } else {
+            bT_ = dalloc<T>(m_);
+            cT_ = dalloc<T>(n_);
+            T *bt = bT_, *ct = cT_;
+            const double *bd = b_, *cd = c_;
+            foreach_kernel<<<grid_for(m_), kBlock, 0, stream_>>>([=] __device__(int i) { bt[i] = static_cast<T>(bd[i]); }, m_);
+            foreach_kernel<<<grid_for(n_), kBlock, 0, stream_>>>([=] __device__(int j) { ct[j] = static_cast<T>(cd[j]); }, n_);
+        }
         // Jacobi preconditioner diag(I + A^T A) = 1 + ||col_j(A^)||^2
         row_sumsq_kernel<<<grid_for((int64_t)n_ * 32), kBlock, 0, stream_>>>(at_rowptr, at_val64, at_rowid, n_, tmp_n);
         {
@@ -454,10 +475,10 @@ class Engine : public EngineBase {
         sh.cg_tol_rel = std::is_same<T, double>::value ? 1e-14 : 1e-7;
         sh.cg_max = std::max(10 * st_.cg_max_iters, 500);
         SCS_CUDA(cudaMemcpyAsync(S_, &sh, sizeof(Scalars), cudaMemcpyHostToDevice, stream_));
-        SCS_CUDA(cudaMemsetAsync(u_, 0, sizeof(double) * N_, stream_));
-        SCS_CUDA(cudaMemsetAsync(v_, 0, sizeof(double) * N_, stream_));
-        SCS_CUDA(cudaMemcpyAsync(u_, c_, sizeof(double) * n_, cudaMemcpyDeviceToDevice, stream_));
-        SCS_CUDA(cudaMemcpyAsync(u_ + n_, b_, sizeof(double) * m_, cudaMemcpyDeviceToDevice, stream_));
+        SCS_CUDA(cudaMemsetAsync(u_, 0, sizeof(T) * N_, stream_));
+        SCS_CUDA(cudaMemsetAsync(v_, 0, sizeof(T) * N_, stream_));
+        SCS_CUDA(cudaMemcpyAsync(u_, cT_, sizeof(T) * n_, cudaMemcpyDeviceToDevice, stream_));
+        SCS_CUDA(cudaMemcpyAsync(u_ + n_, bT_, sizeof(T) * m_, cudaMemcpyDeviceToDevice, stream_));
         SCS_CUDA(cudaMemsetAsync(z_, 0, sizeof(T) * n_, stream_));
         launch_K1();
         launch_K2(CondHandle{0, 0});
@@ -481,6 +502,14 @@ class Engine : public EngineBase {
             const double *cc = c_, *bb = b_;
             reduce_kernel<<<grid_for(n_ + m_), kBlock, 0, stream_>>>(
                 [=] __device__(int i) { return (i < n ? cc[i] : bb[i - n]) * pd[i]; }, n_ + m_, rb_, red_out + 3);
+            if (std::is_same<T, double>::value) {
+                pT_ = reinterpret_cast<T *>(p_);
+            } else {
+                pT_ = dalloc<T>(n_ + m_);
+                T *pt = pT_;
+                foreach_kernel<<<grid_for(n_ + m_), kBlock, 0, stream_>>>(
+                    [=] __device__(int i) { pt[i] = static_cast<T>(pd[i]); }, n_ + m_);
+            }
         }
         double hp;
         SCS_CUDA(cudaMemcpyAsync(&hp, red_out + 3, sizeof(double), cudaMemcpyDeviceToHost, stream_));
@@ -515,12 +544,12 @@ class Engine : public EngineBase {
 
     // Sec. 3.4: u0 = (0, 0, 1), v0 = (0, 0, 1); CG warm start from zero
     void set_initial_point() {
-        SCS_CUDA(cudaMemsetAsync(u_, 0, sizeof(double) * N_, stream_));
-        SCS_CUDA(cudaMemsetAsync(v_, 0, sizeof(double) * N_, stream_));
+        SCS_CUDA(cudaMemsetAsync(u_, 0, sizeof(T) * N_, stream_));
+        SCS_CUDA(cudaMemsetAsync(v_, 0, sizeof(T) * N_, stream_));
         SCS_CUDA(cudaMemsetAsync(z_, 0, sizeof(T) * n_, stream_));
-        double *uu = u_, *vv = v_;
+        T *uu = u_, *vv = v_;
         const int N = N_;
-        foreach_kernel<<<1, 32, 0, stream_>>>([=] __device__(int) { uu[N - 1] = 1.0; vv[N - 1] = 1.0; }, 1);
+        foreach_kernel<<<1, 32, 0, stream_>>>([=] __device__(int) { uu[N - 1] = T(1); vv[N - 1] = T(1); }, 1);
         SCS_CUDA(cudaGetLastError());
         reset_counters();
     }
@@ -543,12 +572,12 @@ class Engine : public EngineBase {
 
     void launch_K1() {
         guard(A_.grid());
-        EpiAInit<T> e{u_, v_, b_, yacc_, S_, n_, N_, 0.0};
+        EpiAInit<T> e{u_, v_, bT_, yacc_, S_, n_, N_, 0.0};
         spmv_kernel<T, T, T, EpiAInit<T>><<<A_.grid(), kBlock, 0, cur_>>>(A_, z_, e, rb_);
     }
     void launch_K2(CondHandle h) {
         guard(At_.grid());
-        EpiAtInit<T> e{u_, v_, c_, diag_, z_, r_, pv_, S_, h, N_, 0.0};
+        EpiAtInit<T> e{u_, v_, cT_, diag_, z_, r_, pv_, S_, h, N_, 0.0};
         spmv_kernel<T, T, T, EpiAtInit<T>><<<At_.grid(), kBlock, 0, cur_>>>(At_, yacc_, e, rb_);
     }
     void launch_K3() {
@@ -566,10 +595,10 @@ class Engine : public EngineBase {
                                                                               h, rb_);
     }
     void launch_K6() {
-        smw_kernel<T><<<grid_for(n_ + m_), kBlock, 0, cur_>>>(n_, m_, c_, b_, z_, yacc_, S_, rb_);
+        smw_kernel<T><<<grid_for(n_ + m_), kBlock, 0, cur_>>>(n_, m_, cT_, bT_, z_, yacc_, S_, rb_);
     }
     void launch_K7() {
-        ProjArgs<T> a{n_, m_, N_, u_, v_, p_, z_, yacc_, S_};
+        ProjArgs<T> a{n_, m_, N_, u_, v_, pT_, z_, yacc_, S_};
         const int grid = proj_grid();
         guard(grid);
         relax_project_kernel<T><<<grid, kBlock, 0, cur_>>>(a, cone_, rb_);
@@ -577,10 +606,10 @@ class Engine : public EngineBase {
     void launch_check() {
         guard(A64_.grid());
         guard(At64_.grid());
-        EpiChkA ea{u_, v_, b_, D_, ax_, S_, n_, N_, 0.0};
-        spmv_kernel<double, double, double, EpiChkA><<<A64_.grid(), kBlock, 0, stream_>>>(A64_, u_, ea, rb_);
-        EpiChkAt eb{u_, v_, c_, E_, S_, N_, 0.0};
-        spmv_kernel<double, double, double, EpiChkAt><<<At64_.grid(), kBlock, 0, stream_>>>(At64_, u_ + n_, eb,
+        EpiChkA<T> ea{u_, v_, b_, D_, ax_, S_, n_, N_, 0.0};
+        spmv_kernel<double, T, double, EpiChkA<T>><<<A64_.grid(), kBlock, 0, stream_>>>(A64_, u_, ea, rb_);
+        EpiChkAt<T> eb{u_, v_, c_, E_, S_, N_, 0.0};
+        spmv_kernel<double, T, double, EpiChkAt<T>><<<At64_.grid(), kBlock, 0, stream_>>>(At64_, u_ + n_, eb,
                                                                                                   rb_);
         SCS_CUDA(cudaGetLastError());
     }
@@ -676,7 +705,8 @@ class Engine : public EngineBase {
     ReduceBuf rb_{};
     int rb_cap_ = 0;
     Scalars *S_ = nullptr, *Sh_ = nullptr;
-    double *u_ = nullptr, *v_ = nullptr, *b_ = nullptr, *c_ = nullptr, *D_ = nullptr, *E_ = nullptr;
+    T *u_ = nullptr, *v_ = nullptr, *bT_ = nullptr, *cT_ = nullptr, *pT_ = nullptr;
+    double *b_ = nullptr, *c_ = nullptr, *D_ = nullptr, *E_ = nullptr;
     double *p_ = nullptr, *ax_ = nullptr, *out_ = nullptr;
     T *z_ = nullptr, *r_ = nullptr, *pv_ = nullptr, *diag_ = nullptr, *q_ = nullptr, *yacc_ = nullptr;
     std::vector<double> Dh_, Eh_;

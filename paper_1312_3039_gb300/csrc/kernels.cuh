@@ -26,6 +26,14 @@
 //   K7  relax + project onto C + dual update (fused, per cone type)
 // Each reduction is a deterministic grid sum whose last CTA updates the
 // scalars (and, inside a CUDA graph, the CG loop's conditional handle).
+//
+// Precision: T is the type of A, the CG vectors and the working copies of the
+// iterates u, v and of p = M^-1 h (float in the mixed-precision engine,
+// double in the FP64 engine).  Threads accumulate their reduction values in
+// T and the grid sums add them in FP64; the scaling, the termination tests,
+// tau / kappa and the exponential-cone root polish are FP64 (GB300's FP64
+// rate is a small fraction of its FP32 rate, so FP64 stays off the
+// per-element paths of the mixed-precision engine).
 #pragma once
 
 #include <math.h>
@@ -51,17 +59,17 @@ template <typename T>
 struct EpiAInit {
     static constexpr int NV = 1;
     static constexpr int kSite = kSiteAInit;
-    const double *u, *v, *b;
+    const T *u, *v, *b;
     T *yacc;
     Scalars *S;
     int n, N;
     double wtau;
-    struct In { double w, b; };
+    struct In { T w, b; };
     __device__ bool skip() const { return false; }
-    __device__ void begin() { wtau = u[N - 1] + v[N - 1]; }
+    __device__ void begin() { wtau = static_cast<double>(u[N - 1]) + static_cast<double>(v[N - 1]); }
     __device__ In load(int i) const { return In{u[n + i] + v[n + i], b[i]}; }
-    __device__ void row(int i, T s, const In &in, double (&red)[NV]) {
-        yacc[i] = static_cast<T>(in.w - wtau * in.b + static_cast<double>(s));
+    __device__ void row(int i, T s, const In &in, T (&red)[NV]) {
+        yacc[i] = in.w - static_cast<T>(wtau) * in.b + s;
         red[0] += in.w * in.w;
     }
     __device__ void finish(const double (&t)[NV]) { S->ww_y = t[0]; }
@@ -74,27 +82,26 @@ template <typename T>
 struct EpiAtInit {
     static constexpr int NV = 4;
     static constexpr int kSite = kSiteAtInit;
-    const double *u, *v, *c;
+    const T *u, *v, *c;
     const T *diag;
     T *z, *r, *p;
     Scalars *S;
     CondHandle cond;
     int N;
     double wtau;
-    struct In { double ux, c; T z, d; };
+    struct In { T ux, c, z, d; };
     __device__ bool skip() const { return false; }
-    __device__ void begin() { wtau = u[N - 1] + v[N - 1]; }
+    __device__ void begin() { wtau = static_cast<double>(u[N - 1]) + static_cast<double>(v[N - 1]); }
     __device__ In load(int j) const { return In{u[j], c[j], z[j], diag[j]}; }
-    __device__ void row(int j, T s, const In &in, double (&red)[NV]) {
-        const double ux = in.ux;
-        const T rj = static_cast<T>(ux - wtau * in.c - static_cast<double>(in.z) - static_cast<double>(s));
+    __device__ void row(int j, T s, const In &in, T (&red)[NV]) {
+        const T rj = in.ux - static_cast<T>(wtau) * in.c - in.z - s;
         const T sj = rj / in.d;
         r[j] = rj;
         p[j] = sj;
-        red[0] += static_cast<double>(rj) * sj;
-        red[1] += static_cast<double>(rj) * rj;
-        red[2] += static_cast<double>(sj) * sj;
-        red[3] += ux * ux;
+        red[0] += rj * sj;
+        red[1] += rj * rj;
+        red[2] += sj * sj;
+        red[3] += in.ux * in.ux;
     }
     __device__ void finish(const double (&t)[NV]) {
         const double ww = t[3] + S->ww_y + wtau * wtau;
@@ -131,9 +138,9 @@ struct EpiACG {
     __device__ bool skip() const { return !S->active; }
     __device__ void begin() {}
     __device__ In load(int) const { return In{}; }
-    __device__ void row(int i, T s, const In &, double (&red)[NV]) {
+    __device__ void row(int i, T s, const In &, T (&red)[NV]) {
         q[i] = s;
-        red[0] += static_cast<double>(s) * s;
+        red[0] += s * s;
     }
     __device__ void finish(const double (&t)[NV]) {
         S->qq = t[0];
@@ -156,15 +163,15 @@ struct EpiAtCG {
     __device__ bool skip() const { return !S->active; }
     __device__ void begin() { alpha = static_cast<T>(S->alpha); }
     __device__ In load(int j) const { return In{p[j], z[j], r[j], diag[j]}; }
-    __device__ void row(int j, T s, const In &in, double (&red)[NV]) {
+    __device__ void row(int j, T s, const In &in, T (&red)[NV]) {
         const T pj = in.p;
         const T gp = pj + s;
         z[j] = in.z + alpha * pj;
         const T rj = in.r - alpha * gp;
         r[j] = rj;
         const T sj = rj / in.d;
-        red[0] += static_cast<double>(rj) * sj;
-        red[1] += static_cast<double>(rj) * rj;
+        red[0] += rj * sj;
+        red[1] += rj * rj;
     }
     __device__ void finish(const double (&t)[NV]) {
         S->cg_it += 1;
@@ -189,17 +196,17 @@ __global__ void __launch_bounds__(kBlock) cg_update_kernel(int n, int m, const T
     const T alpha = static_cast<T>(S->alpha);
     const T beta = static_cast<T>(S->beta);
     const int done = S->done;
-    double red[1] = {0.0};
+    T acc = 0;
     const int total = n > m ? n : m;
     for (int i = blockIdx.x * kBlock + threadIdx.x; i < total; i += gridDim.x * kBlock) {
         if (i < m) yacc[i] = yacc[i] + alpha * q[i];
         if (i < n && !done) {
             const T pj = r[i] / diag[i] + beta * p[i];
             p[i] = pj;
-            red[0] += static_cast<double>(pj) * pj;
+            acc += pj * pj;
         }
     }
-    double tot[1];
+    double red[1] = {static_cast<double>(acc)}, tot[1];
     if (grid_sum<1>(red, rb, kSiteCGUpd, tot)) {
         if (threadIdx.x == 0) {
             if (!done) S->pp = tot[0];
@@ -213,14 +220,14 @@ __global__ void __launch_bounds__(kBlock) cg_update_kernel(int n, int m, const T
 // K6: gamma = h^T z / (1 + h^T p)
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kBlock) smw_kernel(int n, int m, const double *__restrict__ c,
-                                                     const double *__restrict__ b, const T *__restrict__ z,
+__global__ void __launch_bounds__(kBlock) smw_kernel(int n, int m, const T *__restrict__ c,
+                                                     const T *__restrict__ b, const T *__restrict__ z,
                                                      const T *__restrict__ yacc, Scalars *S, ReduceBuf rb) {
-    double red[1] = {0.0};
+    T acc = 0;
     for (int i = blockIdx.x * kBlock + threadIdx.x; i < n + m; i += gridDim.x * kBlock) {
-        red[0] += i < n ? c[i] * static_cast<double>(z[i]) : b[i - n] * static_cast<double>(yacc[i - n]);
+        acc += i < n ? c[i] * z[i] : b[i - n] * yacc[i - n];
     }
-    double tot[1];
+    double red[1] = {static_cast<double>(acc)}, tot[1];
     if (grid_sum<1>(red, rb, kSiteSmw, tot)) {
         if (threadIdx.x == 0) S->gamma = tot[0] / S->hp1;
     }
@@ -249,44 +256,47 @@ struct ConeDev {
 template <typename T>
 struct ProjArgs {
     int n, m, N;
-    double *u, *v;
-    const double *p;       // cached M^-1 h (n + m)
+    T *u, *v;
+    const T *p;            // cached M^-1 h (n + m)
     const T *z;            // z_x
     const T *yacc;         // z_y
     Scalars *S;
 };
 
 template <typename T>
-__device__ __forceinline__ double relaxed(const ProjArgs<T> &a, int idx, double gamma, double alpha) {
+__device__ __forceinline__ T relaxed(const ProjArgs<T> &a, int idx, T gamma, T alpha) {
     // u~ = z - p gamma; u_bar = alpha u~ + (1 - alpha) u
-    const double zi = idx < a.n ? static_cast<double>(a.z[idx]) : static_cast<double>(a.yacc[idx - a.n]);
-    const double ut = zi - a.p[idx] * gamma;
-    return alpha * ut + (1.0 - alpha) * a.u[idx];
+    const T zi = idx < a.n ? a.z[idx] : a.yacc[idx - a.n];
+    const T ut = zi - a.p[idx] * gamma;
+    return alpha * ut + (T(1) - alpha) * a.u[idx];
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) relax_project_kernel(ProjArgs<T> a, ConeDev K, ReduceBuf rb) {
-    const double gamma = a.S->gamma;
-    const double alpha = a.S->relax;
+    const double gamma_d = a.S->gamma;
+    const T gamma = static_cast<T>(gamma_d);
+    const T alpha = static_cast<T>(a.S->relax);
     const int bid = blockIdx.x;
-    double dd = 0.0;        // squared length of this thread's part of the step
+    T dd = 0;               // squared length of this thread's part of the step
     if (bid < K.nb_exp) {
         const int tri = bid * kExpPerCta + threadIdx.x;
         if (threadIdx.x < kExpPerCta && tri < K.ep) {
             const int off = a.n + K.exp_off + 3 * tri;
-            double t[3], uo[3], vo[3], up[3];
+            double t[3], up[3];
+            T uo[3], vo[3];
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
                 uo[e] = a.u[off + e];
                 vo[e] = a.v[off + e];
-                t[e] = relaxed(a, off + e, gamma, alpha) - vo[e];
+                t[e] = static_cast<double>(relaxed(a, off + e, gamma, alpha)) - static_cast<double>(vo[e]);
             }
             proj_exp_dual(t[0], t[1], t[2], up[0], up[1], up[2]);
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
-                a.u[off + e] = up[e];
-                a.v[off + e] = up[e] - t[e];
-                dd += (up[e] - uo[e]) * (up[e] - uo[e]) + (up[e] - t[e] - vo[e]) * (up[e] - t[e] - vo[e]);
+                const T un = static_cast<T>(up[e]), vn = static_cast<T>(up[e] - t[e]);
+                a.u[off + e] = un;
+                a.v[off + e] = vn;
+                dd += (un - uo[e]) * (un - uo[e]) + (vn - vo[e]) * (vn - vo[e]);
             }
         }
     } else if (bid - K.nb_exp < K.nb_soc) {
@@ -296,25 +306,25 @@ __global__ void __launch_bounds__(kBlock) relax_project_kernel(ProjArgs<T> a, Co
             const int off = a.n + K.q_off[blk];
             const int len = K.q_len[blk];
             // t = u_bar - v over the block; projection onto SOC (self-dual)
-            double t0 = 0.0, xx = 0.0;
+            T t0 = 0, xx = 0;
             for (int e = lane; e < len; e += 32) {
-                const double t = relaxed(a, off + e, gamma, alpha) - a.v[off + e];
+                const T t = relaxed(a, off + e, gamma, alpha) - a.v[off + e];
                 if (e == 0) t0 = t; else xx += t * t;
             }
             xx = warp_sum(xx);
             t0 = __shfl_sync(0xffffffffu, t0, 0);
-            const double nx = sqrt(xx);
-            double head, tail;                  // projection = (head, tail * x)
-            if (nx <= t0) { head = t0; tail = 1.0; }
-            else if (nx <= -t0) { head = 0.0; tail = 0.0; }
+            const T nx = sqrt(xx);
+            T head, tail;                       // projection = (head, tail * x)
+            if (nx <= t0) { head = t0; tail = T(1); }
+            else if (nx <= -t0) { head = T(0); tail = T(0); }
             else {
-                head = 0.5 * (t0 + nx);
+                head = T(0.5) * (t0 + nx);
                 tail = head / nx;
             }
             for (int e = lane; e < len; e += 32) {
-                const double uo = a.u[off + e], vo = a.v[off + e];
-                const double t = relaxed(a, off + e, gamma, alpha) - vo;
-                const double up = e == 0 ? head : tail * t;
+                const T uo = a.u[off + e], vo = a.v[off + e];
+                const T t = relaxed(a, off + e, gamma, alpha) - vo;
+                const T up = e == 0 ? head : tail * t;
                 a.u[off + e] = up;
                 a.v[off + e] = up - t;
                 dd += (up - uo) * (up - uo) + (up - t - vo) * (up - t - vo);
@@ -325,34 +335,34 @@ __global__ void __launch_bounds__(kBlock) relax_project_kernel(ProjArgs<T> a, Co
         const int nlin = a.n + K.z + K.l;
         const int idx = ebid * kBlock + threadIdx.x;
         if (idx < nlin) {
-            const double ub = relaxed(a, idx, gamma, alpha);
-            const double uo = a.u[idx];
+            const T ub = relaxed(a, idx, gamma, alpha);
+            const T uo = a.u[idx];
             if (idx < a.n) {
                 a.u[idx] = ub;                       // R^n: identity, v_x stays 0
                 dd += (ub - uo) * (ub - uo);
             } else {
-                const double vo = a.v[idx];
-                const double t = ub - vo;
-                const double up = (idx < a.n + K.z) ? t : fmax(t, 0.0);   // K* of {0} is R
+                const T vo = a.v[idx];
+                const T t = ub - vo;
+                const T up = (idx < a.n + K.z) ? t : (t > T(0) ? t : T(0));   // K* of {0} is R
                 a.u[idx] = up;
                 a.v[idx] = up - t;
                 dd += (up - uo) * (up - uo) + (up - t - vo) * (up - t - vo);
             }
         }
         if (ebid == 0 && threadIdx.x == 0) {
-            // tau: u~_tau = w_tau + gamma
+            // tau (FP64): u~_tau = w_tau + gamma
             const int it = a.N - 1;
-            const double ut = a.S->wtau + gamma;
-            const double uo = a.u[it], vo = a.v[it];
-            const double ub = alpha * ut + (1.0 - alpha) * uo;
+            const double ut = a.S->wtau + gamma_d;
+            const double uo = static_cast<double>(a.u[it]), vo = static_cast<double>(a.v[it]);
+            const double ub = a.S->relax * ut + (1.0 - a.S->relax) * uo;
             const double t = ub - vo;
             const double up = fmax(t, 0.0);
-            a.u[it] = up;
-            a.v[it] = up - t;
-            dd += (up - uo) * (up - uo) + (up - t - vo) * (up - t - vo);
+            a.u[it] = static_cast<T>(up);
+            a.v[it] = static_cast<T>(up - t);
+            dd += static_cast<T>((up - uo) * (up - uo) + (up - t - vo) * (up - t - vo));
         }
     }
-    double red[1] = {dd}, tot[1];
+    double red[1] = {static_cast<double>(dd)}, tot[1];
     if (grid_sum<1>(red, rb, kSiteProj, tot)) {
         if (threadIdx.x == 0) {
             a.S->dstep = sqrt(tot[0]);
@@ -368,18 +378,22 @@ __global__ void __launch_bounds__(kBlock) relax_project_kernel(ProjArgs<T> a, Co
 // The last CTA of KC2 evaluates the tests in the order optimality, primal
 // infeasibility, dual infeasibility and writes S->status.
 // ---------------------------------------------------------------------------
+template <typename T>
 struct EpiChkA {
     static constexpr int NV = 3;
     static constexpr int kSite = kSiteChkA;
-    const double *u, *v, *b, *D;
+    const T *u, *v;
+    const double *b, *D;
     double *ax;
     Scalars *S;
     int n, N;
     double tau;
     struct In { double vs, b, d, uy; };
     __device__ bool skip() const { return false; }
-    __device__ void begin() { tau = u[N - 1]; }
-    __device__ In load(int i) const { return In{v[n + i], b[i], D[i], u[n + i]}; }
+    __device__ void begin() { tau = static_cast<double>(u[N - 1]); }
+    __device__ In load(int i) const {
+        return In{static_cast<double>(v[n + i]), b[i], D[i], static_cast<double>(u[n + i])};
+    }
     __device__ void row(int i, double s, const In &in, double (&red)[NV]) {
         ax[i] = s;
         const double a = s + in.vs;
@@ -396,17 +410,19 @@ struct EpiChkA {
     }
 };
 
+template <typename T>
 struct EpiChkAt {
     static constexpr int NV = 3;
     static constexpr int kSite = kSiteChkAt;
-    const double *u, *v, *c, *E;
+    const T *u, *v;
+    const double *c, *E;
     Scalars *S;
     int N;
     double tau;
     struct In { double c, e, ux; };
     __device__ bool skip() const { return false; }
-    __device__ void begin() { tau = u[N - 1]; }
-    __device__ In load(int j) const { return In{c[j], E[j], u[j]}; }
+    __device__ void begin() { tau = static_cast<double>(u[N - 1]); }
+    __device__ In load(int j) const { return In{c[j], E[j], static_cast<double>(u[j])}; }
     __device__ void row(int j, double s, const In &in, double (&red)[NV]) {
         const double du = (s + tau * in.c) / in.e;
         const double inf = s / in.e;
@@ -418,7 +434,7 @@ struct EpiChkAt {
         S->dual2 = t[0];
         S->inf2 = t[1];
         S->ctx = t[2];
-        const double tau_ = u[N - 1], kappa = v[N - 1];
+        const double tau_ = static_cast<double>(u[N - 1]), kappa = static_cast<double>(v[N - 1]);
         const double sg = S->sigma, rh = S->rho;
         S->tau = tau_;
         S->kappa = kappa;
@@ -455,13 +471,14 @@ struct EpiChkAt {
 };
 
 // Solution or certificate in the caller's units (Sec. 5 unscaling, Sec. 2.3 cases).
-static __global__ void __launch_bounds__(kBlock) output_kernel(int n, int m, int status, const double *__restrict__ u,
-                                                        const double *__restrict__ v, const double *__restrict__ D,
+template <typename T>
+__global__ void __launch_bounds__(kBlock) output_kernel(int n, int m, int status, const T *__restrict__ u,
+                                                        const T *__restrict__ v, const double *__restrict__ D,
                                                         const double *__restrict__ E, const double *__restrict__ ax,
                                                         const Scalars *S, double *__restrict__ x,
                                                         double *__restrict__ y, double *__restrict__ s) {
     const int N = n + m + 1;
-    const double tau = u[N - 1];
+    const double tau = static_cast<double>(u[N - 1]);
     const double sg = S->sigma, rh = S->rho;
     for (int i = blockIdx.x * kBlock + threadIdx.x; i < n + 2 * m; i += gridDim.x * kBlock) {
         if (status == 1 || status == 2) {

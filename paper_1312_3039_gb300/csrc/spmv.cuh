@@ -80,7 +80,7 @@ __device__ __forceinline__ Acc fmul(TA a, TX x) {
 // rows are in flight together.
 template <int L, typename TA, typename TX, typename Acc, typename Epi>
 __device__ __forceinline__ void spmv_small_groups(const Csr<TA> &A, const TX *__restrict__ x, Epi &epi,
-                                                  double (&red)[Epi::NV], int r0, int r1, int cta, int nctas) {
+                                                  Acc (&red)[Epi::NV], int r0, int r1, int cta, int nctas) {
     constexpr int G = 32 / L;                 // groups per warp
     constexpr int R = kRowsPerLane;
     const int lane = threadIdx.x & 31, g = lane / L, gl = lane % L;
@@ -137,7 +137,7 @@ __device__ __forceinline__ void spmv_small_groups(const Csr<TA> &A, const TX *__
 // a warp per row (rows of up to kWarpRow nonzeros)
 template <typename TA, typename TX, typename Acc, typename Epi>
 __device__ __forceinline__ void spmv_warp_rows(const Csr<TA> &A, const TX *__restrict__ x, Epi &epi,
-                                               double (&red)[Epi::NV], int r0, int r1, int cta, int nctas) {
+                                               Acc (&red)[Epi::NV], int r0, int r1, int cta, int nctas) {
     const int lane = threadIdx.x & 31;
     const int warp = cta * kWarps + (threadIdx.x >> 5), nwarps = nctas * kWarps;
     const int32_t *__restrict__ col = A.col;
@@ -161,9 +161,9 @@ __global__ void __launch_bounds__(kBlock) spmv_kernel(Csr<TA> A, const TX *__res
     static_assert(NV >= 1 && NV <= kMaxRed, "epilogue reduction width");
     if (epi.skip()) return;
     epi.begin();
-    double red[NV];
+    Acc red[NV];                  // per-thread reduction values, in the product's precision
 #pragma unroll
-    for (int i = 0; i < NV; ++i) red[i] = 0.0;
+    for (int i = 0; i < NV; ++i) red[i] = Acc(0);
     const int b = blockIdx.x;
     int ri = 0;
     while (ri + 1 < A.reg.n && b >= A.reg.cta0[ri + 1]) ++ri;
@@ -195,8 +195,10 @@ __global__ void __launch_bounds__(kBlock) spmv_kernel(Csr<TA> A, const TX *__res
             }
         }
     }
-    double tot[NV];
-    if (grid_sum<NV>(red, rb, Epi::kSite, tot)) {
+    double redd[NV], tot[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) redd[i] = static_cast<double>(red[i]);
+    if (grid_sum<NV>(redd, rb, Epi::kSite, tot)) {
         if (threadIdx.x == 0) epi.finish(tot);
     }
 }

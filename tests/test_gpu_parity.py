@@ -93,9 +93,10 @@ def test_plain_launch_path_matches_graph(scs):
         np.testing.assert_allclose(u1, u2, rtol=0, atol=1e-12 * np.linalg.norm(u1))
 
 
-def check_solution(P, x, y, s, eps=1e-4):
+def check_solution(P, x, y, s, eps=1e-4, cone_tol=1e-7):
     """Sec. 3.5 tests on the returned point against the original data, and
-    the objective inside the band weak duality gives around the known optimum:
+    the objective inside the band weak duality gives around the known optimum
+    (cone membership to cone_tol: FP32 iterates round at ~1e-7 relative):
     with r_p = A x + s - b and r_d = A^T y + c, the generator's x*, y* give
     p* - c^T x <= ||y*|| ||r_p||  and  c^T x - p* <= |gap| + ||x*|| ||r_d||."""
     nb, nc = np.linalg.norm(P.b), np.linalg.norm(P.c)
@@ -105,8 +106,8 @@ def check_solution(P, x, y, s, eps=1e-4):
     assert rd <= eps * (1 + nc) * 1.0001
     cx, by = P.c @ x, P.b @ y
     assert abs(cx + by) <= eps * (1 + abs(cx) + abs(by)) * 1.0001
-    assert cones.in_K(s, P.cone, 1e-7)
-    assert cones.in_Kdual(y, P.cone, 1e-7)
+    assert cones.in_K(s, P.cone, cone_tol)
+    assert cones.in_Kdual(y, P.cone, cone_tol)
     if P.p_star is not None:
         slack = 1e-9 * (1 + abs(P.p_star))
         assert P.p_star - cx <= np.linalg.norm(P.y_star) * rp + slack
@@ -120,7 +121,7 @@ def test_lp_solve(scs, precision, seed):
     ref = admm.solve(P.A, P.b, P.c, P.cone, admm.Settings())
     st, x, y, s, info = scs.solve(P.A, P.b, P.c, P.cone, precision=precision)
     assert st == scs.SOLVED, info
-    check_solution(P, x, y, s)
+    check_solution(P, x, y, s, cone_tol=1e-5 if precision else 1e-7)
     assert abs(info["pobj"] - ref.pobj) <= 1e-3 * (1 + abs(ref.pobj))
     assert info["matvecs"] == 2 * info["iters"] + 2 * info["cg_iters"]
     assert info["iters"] % 20 == 0
@@ -131,7 +132,7 @@ def test_mixed_small_solve(scs, precision):
     P = synth.mixed_small(1, scale=500)
     st, x, y, s, info = scs.solve(P.A, P.b, P.c, P.cone, precision=precision)
     assert st == scs.SOLVED, info
-    check_solution(P, x, y, s)
+    check_solution(P, x, y, s, cone_tol=1e-5 if precision else 1e-7)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -141,7 +142,7 @@ def test_infeasible_certificate(scs, precision):
     assert st == scs.INFEASIBLE, info
     assert abs(P.b @ y + 1.0) < 1e-9
     assert np.linalg.norm(P.A.T @ y) <= 1e-3
-    assert cones.in_Kdual(y, P.cone, 1e-6)
+    assert cones.in_Kdual(y, P.cone, 1e-5 if precision else 1e-6)
     assert np.all(np.isnan(x)) and np.all(np.isnan(s))
 
 
