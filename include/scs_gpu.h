@@ -91,6 +91,9 @@ typedef struct {
     int32_t cg_max_iters;                 /* cap on CG steps per ADMM iteration          */
     int32_t normalize;                    /* 1: equilibrate (Sec. 5); 0: use data as is   */
     int32_t scale_passes;                 /* equilibration passes                       */
+    int32_t block_scale;                  /* one D value per SOC / PSD / exp block: the
+                                             0 mean, 1 root mean square (default) or 2
+                                             maximum of the block's row norms (Sec. 5)  */
     int32_t precision;                    /* 0: FP64 throughout; 1: FP32 A and CG, FP64
                                              iterates, residuals, gap and certificates */
     int32_t use_graph;                    /* 1: one CUDA graph per iteration with the CG
@@ -118,7 +121,7 @@ typedef struct scs_work scs_work;
 /* Fill *s with defaults: eps 1e-4, alpha 1.5, cg_rate 1.5, cg_adapt 0.3,
  * cg_tol_rel 0,
  * max_iters 10000, check_interval 20, cg_max_iters 50, normalize 1,
- * scale_passes 10, precision 1, use_graph 1, device 0. */
+ * scale_passes 10, block_scale 1, precision 1, use_graph 1, device 0. */
 void scs_default_settings(scs_settings *s);
 
 /* Validate and copy A, b (m), c (n) and the cone to the device, equilibrate

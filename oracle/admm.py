@@ -70,6 +70,7 @@ class Settings:
     check_interval: int = 20
     normalize: bool = True
     scale_passes: int = 10
+    block_scale: str = "rms"        # one D value per cone block: "mean", "rms" or "max" of its row norms
     linsys: str = "direct"          # "direct" | "indirect"
     cg_rate: float = 1.5            # zeta^k = (1/k)^cg_rate; <= 0 disables it
     cg_adapt: float = 0.3           # also at most cg_adapt * (last ADMM step length); 0 disables
@@ -108,7 +109,8 @@ class HSDSolver:
         self.b_orig = np.asarray(b, float)
         self.c_orig = np.asarray(c, float)
         if self.st.normalize:
-            Ah, bh, ch, D, E, sigma, rho = equilibrate(A, b, c, cone, self.st.scale_passes)
+            Ah, bh, ch, D, E, sigma, rho = equilibrate(A, b, c, cone, self.st.scale_passes,
+                                                       block=self.st.block_scale)
         else:
             Ah, bh, ch, D, E, sigma, rho = identity_scaling(A, b, c)
         self.A = sp.csr_matrix(Ah)

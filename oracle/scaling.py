@@ -9,7 +9,10 @@ The reading implemented here (identically, but independently, on the GPU):
 
   repeat ``passes`` times:
     r_i = ||row_i(A^)||_2 and c_j = ||col_j(A^)||_2, both from the current A^;
-    over every SOC, PSD and exponential block, replace r_i by the block mean;
+    over every SOC, PSD and exponential block, replace r_i by one value for
+    the block (``block``: the root mean square of the block's norms -- the
+    Frobenius norm of the block over the square root of its row count, the
+    block form of a 2-norm row equilibration -- or their mean, or maximum);
     a norm below ``lo`` is replaced by 1 (nothing to scale), a norm above
     ``hi`` is clamped to ``hi``;
     d_i = 1/sqrt(r_i), e_j = 1/sqrt(c_j);  A^ <- diag(d) A^ diag(e);
@@ -29,7 +32,15 @@ def _clamp(nrm, lo, hi):
     return np.minimum(nrm, hi)
 
 
-def equilibrate(A, b, c, cone, passes=10, lo=1e-4, hi=1e4):
+def _block_value(seg, block):
+    if block == "rms":
+        return float(np.sqrt(np.mean(seg * seg)))
+    if block == "max":
+        return float(seg.max())
+    return float(seg.mean())
+
+
+def equilibrate(A, b, c, cone, passes=10, lo=1e-4, hi=1e4, block="rms"):
     """Return ``(A_hat (csr), b_hat, c_hat, D, E, sigma, rho)``."""
     A = sp.csr_matrix(A, dtype=np.float64, copy=True)
     m, n = A.shape
@@ -41,7 +52,7 @@ def equilibrate(A, b, c, cone, passes=10, lo=1e-4, hi=1e4):
         cn = np.sqrt(np.asarray(sq.sum(axis=0)).ravel())
         for kind, off, size, _order in cone.blocks():
             if kind in ("soc", "psd", "exp"):
-                rn[off:off + size] = rn[off:off + size].mean()
+                rn[off:off + size] = _block_value(rn[off:off + size], block)
         d = 1.0 / np.sqrt(_clamp(rn, lo, hi))
         e = 1.0 / np.sqrt(_clamp(cn, lo, hi))
         A = sp.csr_matrix(sp.diags(d) @ A @ sp.diags(e))

@@ -141,6 +141,7 @@ int validate_settings(const scs_settings &s) {
     }
     if (!(s.cg_adapt >= 0.0) || !(s.cg_tol_rel >= 0.0)) { set_error("negative CG tolerance setting"); return SCS_INVALID_INPUT; }
     if (s.precision != 0 && s.precision != 1) { set_error("precision must be 0 or 1"); return SCS_INVALID_INPUT; }
+    if (s.block_scale < 0 || s.block_scale > 2) { set_error("block_scale must be 0, 1 or 2"); return SCS_INVALID_INPUT; }
     return 0;
 }
 
@@ -182,6 +183,7 @@ void scs_default_settings(scs_settings *s) {
     s->cg_max_iters = 50;
     s->normalize = 1;
     s->scale_passes = 10;
+    s->block_scale = 1;
     s->precision = 1;
     s->use_graph = 1;
     s->verbose = 0;

@@ -366,7 +366,8 @@ class Engine : public EngineBase {
                 sqrt_kernel<<<grid_for(n_), kBlock, 0, stream_>>>(tmp_n, n_);
                 if (navg)
                     block_mean_kernel<<<grid_for((int64_t)navg * 32), kBlock, 0, stream_>>>(tmp_m, d_avg_off,
-                                                                                            d_avg_len, navg);
+                                                                                            d_avg_len, navg,
+                                                                                            st_.block_scale);
                 inv_sqrt_clamp_kernel<<<grid_for(m_), kBlock, 0, stream_>>>(tmp_m, m_, 1e-4, 1e4, tmp_m, D_);
                 inv_sqrt_clamp_kernel<<<grid_for(n_), kBlock, 0, stream_>>>(tmp_n, n_, 1e-4, 1e4, tmp_n, E_);
                 scale_vals_kernel<<<grid_for((int64_t)m_ * 32), kBlock, 0, stream_>>>(a_rowptr, a_col, a_val64, a_rowid,

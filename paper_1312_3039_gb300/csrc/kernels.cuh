@@ -533,18 +533,23 @@ static __global__ void sqrt_kernel(double *__restrict__ nrm, int len) {
     for (int i = blockIdx.x * kBlock + threadIdx.x; i < len; i += gridDim.x * kBlock) nrm[i] = sqrt(nrm[i]);
 }
 
-// over each cone block that D must keep scalar: replace the norms by their mean
-
+// over each cone block that D must keep scalar: replace the norms by one
+// value for the block (mode 0: mean, 1: root mean square, 2: maximum)
 static __global__ void block_mean_kernel(double *__restrict__ nrm, const int32_t *__restrict__ bo,
-                                  const int32_t *__restrict__ bl, int nblocks) {
+                                         const int32_t *__restrict__ bl, int nblocks, int mode) {
     const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int nw = (gridDim.x * kBlock) >> 5;
     for (int b = warp; b < nblocks; b += nw) {
-        double s = 0.0;
-        for (int i = lane; i < bl[b]; i += 32) s += nrm[bo[b] + i];
+        double s = 0.0, mx = 0.0;
+        for (int i = lane; i < bl[b]; i += 32) {
+            const double t = nrm[bo[b] + i];
+            s += mode == 1 ? t * t : t;
+            mx = fmax(mx, t);
+        }
         s = warp_sum(s);
-        const double mean = s / bl[b];
-        for (int i = lane; i < bl[b]; i += 32) nrm[bo[b] + i] = mean;
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const double val = mode == 2 ? mx : mode == 1 ? sqrt(s / bl[b]) : s / bl[b];
+        for (int i = lane; i < bl[b]; i += 32) nrm[bo[b] + i] = val;
     }
 }
 

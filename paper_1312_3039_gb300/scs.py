@@ -43,7 +43,8 @@ class Settings(C.Structure):
                 ("eps_infeas", C.c_double), ("eps_unbdd", C.c_double), ("alpha", C.c_double),
                 ("cg_rate", C.c_double), ("cg_adapt", C.c_double), ("cg_tol_rel", C.c_double), ("time_limit_s", C.c_double),
                 ("max_iters", C.c_int32), ("check_interval", C.c_int32), ("cg_max_iters", C.c_int32),
-                ("normalize", C.c_int32), ("scale_passes", C.c_int32), ("precision", C.c_int32),
+                ("normalize", C.c_int32), ("scale_passes", C.c_int32), ("block_scale", C.c_int32),
+                ("precision", C.c_int32),
                 ("use_graph", C.c_int32), ("verbose", C.c_int32), ("device", C.c_int32),
                 ("cuda_stream", C.c_void_p)]
 

@@ -81,6 +81,25 @@ def test_mixed_small_trajectory_fp64(scs):
     trajectory_parity(scs, synth.mixed_small(0, scale=500))
 
 
+@pytest.mark.parametrize("mode,name", [(0, "mean"), (1, "rms"), (2, "max")])
+def test_block_scale_variants(scs, mode, name):
+    """The three per-block values of the Sec. 5 equilibration give the
+    oracle's D, E, sigma, rho, and the first iterations follow it."""
+    P = synth.mixed_small(3, scale=500)
+    orc = admm.HSDSolver(P.A, P.b, P.c, P.cone, admm.Settings(block_scale=name))
+    with scs.Solver(P.A, P.b, P.c, P.cone, block_scale=mode, **TIGHT) as g:
+        D, E, sigma, rho = g.scaling()
+        np.testing.assert_allclose(D, orc.D, rtol=1e-12)
+        np.testing.assert_allclose(E, orc.E, rtol=1e-12)
+        assert abs(sigma - orc.sigma) <= 1e-12 * orc.sigma
+        assert abs(rho - orc.rho) <= 1e-12 * orc.rho
+        g.iterate(20)
+        for _ in range(20):
+            orc.step()
+        u, _ = g.iterates()
+        assert np.linalg.norm(u - orc.u) <= 1e-9 * np.linalg.norm(orc.u)
+
+
 def test_plain_launch_path_matches_graph(scs):
     """The un-graphed launch sequence gives the same iterates as the graph."""
     P = synth.random_cone(12, n=30, cone=synth.Cone(z=3, l=15, q=(4, 5), ep=3))

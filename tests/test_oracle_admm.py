@@ -204,6 +204,30 @@ def test_equilibration_targets():
     np.testing.assert_allclose((sp.diags(D) @ P.A @ sp.diags(E) - Ah).toarray(), 0, atol=1e-12)
 
 
+@pytest.mark.parametrize("block", ["rms", "mean", "max"])
+def test_equilibration_one_pass_by_hand(block):
+    """One Ruiz pass (Sec. 5 reading) on a 4x2 matrix with known norms: the
+    SOC block's rows (norms 4, 12, 5) share one value -- their RMS, mean or
+    maximum -- the free row keeps its norm 3, and the columns have norms 13
+    and 5."""
+    from oracle.scaling import equilibrate
+    A = np.array([[0.0, 3.0],        # free row, norm 3
+                  [4.0, 0.0],        # SOC rows: norms 4, 12, 5
+                  [12.0, 0.0],
+                  [3.0, 4.0]])
+    cone = synth.Cone(z=1, q=(3,))
+    Ah, bh, ch, D, E, sigma, rho = equilibrate(sp.csr_matrix(A), np.zeros(4), np.zeros(2),
+                                               cone, passes=1, block=block)
+    seg = np.array([4.0, 12.0, 5.0])
+    want_r = {"rms": np.sqrt(np.mean(seg ** 2)), "mean": seg.mean(), "max": seg.max()}[block]
+    np.testing.assert_allclose(D, [1 / np.sqrt(3.0)] + [1 / np.sqrt(want_r)] * 3, rtol=1e-15)
+    np.testing.assert_allclose(E, [1 / np.sqrt(13.0), 1 / np.sqrt(5.0)], rtol=1e-15)
+    np.testing.assert_allclose(Ah.toarray(), np.diag(D) @ A @ np.diag(E), rtol=1e-15)
+    # b = 0 and c = 0: sigma and rho fall back to the 1e-4 floor
+    assert sigma == 1e4
+    assert bh.tolist() == [0.0] * 4 and ch.tolist() == [0.0] * 2
+
+
 def test_warm_start_from_solution():
     """Sec. 4.2: restarting from the solution (u0 = (x, y, 1), v0 = (0, s, 0))
     stops at the first check."""
