@@ -39,7 +39,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["mixed", "mixed_small", "lp"], default="mixed")
+    ap.add_argument("--workload", choices=["mixed", "mixed_small", "sdp", "sdp_small", "sdp_blocks", "lp"],
+                    default="mixed")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-1e-4 solve")
@@ -61,6 +62,17 @@ def make_problem(workload, seed):
                                    "SOC 2e4 blocks of 3-50, exp 1e4, nonneg rest)")
     if workload == "mixed_small":
         return synth.mixed_small(seed, scale=50), "mixed-cone program n=2e4 m=4e4 nnz=4e5 (same recipe)"
+    if workload == "sdp":
+        return synth.sdp(seed), ("SDP-heavy program n=2e5 m=578384 nnz=1.16e8 (64 PSD blocks of order 128 in svec "
+                                 "form, 5e4 nonneg; uniform A at density 1e-3; 8 blocks with eigenvalues over "
+                                 "1e-7..1)")
+    if workload == "sdp_blocks":
+        return (synth.sdp(seed, n=20000, density=1e-4),
+                "PSD blocks of the SDP-heavy program with a small A: 64 PSD blocks of order 128 + 5e4 nonneg, "
+                "n=2e4, density 1e-4 (nnz 1.16e6)")
+    if workload == "sdp_small":
+        return (synth.sdp(seed, n=4000, n_psd=16, order=64, n_nonneg=2000, density=2e-3, n_ill=2),
+                "SDP program n=4e3 m=35280 (16 PSD blocks of order 64, 2e3 nonneg; density 2e-3; 2 ill blocks)")
     return synth.lp(seed), "sparse LP n=200 m=400 (zero 100, nonneg 300), 5% density"
 
 
@@ -142,6 +154,26 @@ def spmv_bytes(P, it, cg, elt=4):
     k2 = mat_at + elt * m + (8 + 8 + elt + elt) * n + 2 * elt * n  # y_acc gathered; u_x, c, z, diag read; r, p written
     k4 = mat_at + elt * m + 4 * elt * n + 2 * elt * n             # q gathered; p, z, r, diag read; z, r written
     return {0: it * k1 + cg * k3, 1: it * k2 + cg * k4, "per_launch": {"A_cg": k3, "At_cg": k4}}
+
+
+def psd_flops(orders, sweeps_per_block):
+    """Flop model of one PSD launch (every block once), FP32 arithmetic:
+    re-orthonormalisation of V and the similarity V^T X V (4 products of
+    order ne: 8 ne^3), the Jacobi sweeps ((ne - 1) rounds of 12 h^2 + 6 n h
+    flops, h = ne / 2: both sides of the lower 2 x 2 blocks and the rows of V)
+    and the reconstruction over half of the eigenvalues (ne^3)."""
+    tot = 0.0
+    for n in orders:
+        ne = max(4, (n + 3) // 4 * 4)
+        h = ne // 2
+        tot += 8.0 * ne ** 3 + sweeps_per_block * (ne - 1) * (12.0 * h * h + 6.0 * n * h) + 1.0 * ne ** 3
+    return tot
+
+
+def fp32_alu_peak_tflops(sm_mhz):
+    """FP32 FMA peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flops
+    per clock at the sampled SM clock (max 2070 MHz)."""
+    return 152 * 128 * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
 
 
 def cpu_oracle_job(workload, seed, seconds, queue):
@@ -286,11 +318,14 @@ def run_gb300(args):
     iters_done = sum_over_ranks(it1 - it0)
     value = iters_done / (ms / 1e3)
     cg_steps = cg1 - cg0
-    launches = 4 * (it1 - it0) + 3 * cg_steps
+    # K1, K2, K6, K7 (+ the PSD kernel) per iteration and K3, K4, K5 per CG step
+    launches = (5 if getattr(P.cone, "s", ()) else 4) * (it1 - it0) + 3 * cg_steps
 
     # roofline of the dominant kernel (CUDA events around each SpMV launch)
+    has_psd = bool(getattr(P.cone, "s", ()))
+    psd0 = S.psd_counters() if has_psd else None
     S.iterate_profiled(5)
-    prof = {k: S.kernel_time(k) for k in (0, 1, 2)}
+    prof = {k: S.kernel_time(k) for k in (0, 1, 2, 3)}
     it_p, cg_p = S.counters()
     # counters include the profiled iterations: take CG steps of those 5 from the launch counts
     cg_prof = prof[0][1] - 5
@@ -306,12 +341,32 @@ def run_gb300(args):
                 "algorithmic_bytes_per_cg_launch": byt["per_launch"]["A_cg" if kind == 0 else "At_cg"],
                 "avg_launch_us": 1e3 * prof[kind][0] / prof[kind][1],
                 "other_kernel_avg_us": 1e3 * prof[1 - kind][0] / max(prof[1 - kind][1], 1),
-                "projection_avg_us": 1e3 * prof[2][0] / max(prof[2][1], 1)}
+                "projection_avg_us": 1e3 * prof[2][0] / max(prof[2][1], 1),
+                "psd_projection_avg_us": 1e3 * prof[3][0] / prof[3][1] if prof[3][1] else None}
+
+    psd = None
+    if has_psd and prof[3][1]:
+        calls, sweeps, fp64 = (b - a for a, b in zip(psd0, S.psd_counters()))
+        per_block = sweeps / max(calls, 1)
+        avg_us = 1e3 * prof[3][0] / prof[3][1]
+        flops = psd_flops(P.cone.s, per_block)
+        peak_t = fp32_alu_peak_tflops(clk.get("sm_mhz"))
+        achieved_t = flops / (avg_us * 1e-6) / 1e12
+        psd = {"bound": "alu", "kernel": "psd_project_kernel (Jacobi per block, one CTA per block)",
+               "achieved": achieved_t, "peak": peak_t, "unit": "TFLOP/s", "frac": achieved_t / peak_t,
+               "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x sampled SM clock",
+               "avg_launch_us": avg_us, "blocks": len(P.cone.s), "sweeps_per_block": per_block,
+               "fp64_reconstructed_frac": fp64 / max(calls, 1), "flops_per_launch": flops}
 
     # time to the 1e-4 tolerances from a cold start, data resident
     solve = None
     if not args.no_solve:
+        psd_s0 = S.psd_counters() if has_psd else None
         st, x, y, s, info = S.solve()
+        if psd is not None:
+            c_, sw_, f_ = (b - a for a, b in zip(psd_s0, S.psd_counters()))
+            psd["solve_sweeps_per_block"] = sw_ / max(c_, 1)
+            psd["solve_fp64_reconstructed_frac"] = f_ / max(c_, 1)
         solve = {"status": int(st), "iters": info["iters"], "seconds": info["solve_s"],
                  "avg_cg_per_iter": info["cg_iters"] / max(info["iters"], 1),
                  "pobj": info["pobj"], "p_star": P.p_star,
@@ -367,6 +422,8 @@ def run_gb300(args):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "time_to_1e4": solve,
         }
+        if psd is not None:
+            line["psd_roofline"] = psd
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

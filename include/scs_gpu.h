@@ -86,6 +86,10 @@ typedef struct {
                                              (0 disables; see scs_default_settings)     */
     double cg_tol_rel;                    /* CG also stops at cg_tol_rel * ||u^k + v^k|| */
     double time_limit_s;                  /* <= 0: none                                 */
+    double psd_fp64_cond;                 /* FP32 engine: a PSD block whose positive
+                                             eigenvalues spread wider than this (max /
+                                             min >= psd_fp64_cond) sums V max(L,0) V^T in
+                                             FP64 (Sec. 6.1 projection); INFINITY: never */
     int32_t max_iters;
     int32_t check_interval;               /* termination test every this many iterations */
     int32_t cg_max_iters;                 /* cap on CG steps per ADMM iteration          */
@@ -119,7 +123,7 @@ typedef struct {
 typedef struct scs_work scs_work;
 
 /* Fill *s with defaults: eps 1e-4, alpha 1.5, cg_rate 1.5, cg_adapt 0.3,
- * cg_tol_rel 0,
+ * cg_tol_rel 0, psd_fp64_cond 1e6,
  * max_iters 10000, check_interval 20, cg_max_iters 50, normalize 1,
  * scale_passes 10, block_scale 1, precision 1, use_graph 1, device 0. */
 void scs_default_settings(scs_settings *s);
@@ -168,7 +172,8 @@ int32_t scs_get_scaling(scs_work *w, double *D, double *E, double *sigma, double
 
 /* Per-kernel device time since the last call (CUDA events on the work's
  * stream, collected only by scs_iterate_profiled).  kind: 0 = SpMV with A in
- * the CG loop, 1 = SpMV with A^T in the CG loop, 2 = cone projection.
+ * the CG loop, 1 = SpMV with A^T in the CG loop, 2 = cone projection of the
+ * non-PSD rows, 3 = projection of the PSD blocks.
  * Writes the summed milliseconds and the launch count. */
 int32_t scs_iterate_profiled(scs_work *w, int32_t iters);
 int32_t scs_kernel_time(scs_work *w, int32_t kind, double *ms, int64_t *launches);
@@ -176,6 +181,13 @@ int32_t scs_kernel_time(scs_work *w, int32_t kind, double *ms, int64_t *launches
 /* Iteration counters since the last reset / warm start / solve start: ADMM
  * iterations and CG steps (synchronises the work's stream). */
 int32_t scs_counters(scs_work *w, int32_t *iters, int64_t *cg_iters);
+
+/* PSD projection statistics since scs_init (Sec. 6.1 eigendecomposition per
+ * block): block projections done, the Jacobi sweeps they took, and how many
+ * of them summed the reconstruction V max(Lambda, 0) V^T in FP64 (blocks whose
+ * eigenvalue magnitudes spread over more than 1e6, FP32 engine only).  Any
+ * pointer may be NULL; synchronises the work's stream. */
+int32_t scs_psd_counters(scs_work *w, int64_t *calls, int64_t *sweeps, int64_t *fp64_blocks);
 
 /* Sizes of the work object's problem and the device bytes it holds. */
 int32_t scs_dims(scs_work *w, int32_t *m, int32_t *n, int64_t *nnz, int64_t *device_bytes);
@@ -190,8 +202,10 @@ int32_t scs_dims(scs_work *w, int32_t *m, int32_t *n, int64_t *nnz, int64_t *dev
  * *dist2 (host, may be NULL) receives the sum over all vectors of
  * ||out - v||^2.  Runs on `stream` (a cudaStream_t, or NULL for the legacy
  * default stream) of the current device and returns when it is done.  It
- * allocates a small device scratch buffer for the call.  PSD blocks give
- * SCS_UNSUPPORTED. */
+ * allocates a device scratch buffer for the call (PSD blocks of order above
+ * 96 add three order x order FP64 matrices per CTA).  PSD blocks (order at
+ * most 1024) are projected by eigendecomposition, Sec. 6.1, with a
+ * cold-started FP64 Jacobi eigensolver. */
 int32_t scs_project(const scs_cone *k, int32_t dual, const double *v, double *out, int64_t count,
                     double *dist2, void *stream);
 
@@ -206,7 +220,8 @@ int32_t scs_project(const scs_cone *k, int32_t dual, const double *v, double *ou
  * (about 41 KB) until the process exits.
  *   - The first call on a device looks up that array's device address, with
  *     the device current; make that first call before any stream capture.
- *   - Limits: at most 4096 SOC blocks per cone (SCS_UNSUPPORTED otherwise).
+ *   - Limits: at most 4096 SOC blocks per cone and no PSD blocks (their
+ *     eigensolver needs matrix scratch); SCS_UNSUPPORTED otherwise.
  *   - Every call shares the one array, and each call resets the part that
  *     must start at zero; calls that overlap on the GPU (different streams or
  *     threads at the same time) race on it and must not be issued. */

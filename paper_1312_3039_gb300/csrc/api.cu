@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include "engine_base.h"
+#include "psd.cuh"
 
 struct scs_work {
     scs::EngineBase *eng = nullptr;
@@ -57,10 +58,10 @@ int validate_and_build(const scs_csc *A, const double *b, const double *c, const
     }
     for (int32_t i = 0; i < k->ns; ++i) {
         if (k->s[i] < 1) { set_error("PSD order must be >= 1"); return SCS_INVALID_INPUT; }
+        if (k->s[i] > scs::kPsdMaxOrder) { set_error("PSD order above 1024"); return SCS_UNSUPPORTED; }
         rows += (int64_t)k->s[i] * (k->s[i] + 1) / 2;
     }
     if (rows != m) { set_error("cone sizes do not add up to m"); return SCS_INVALID_INPUT; }
-    if (k->ns > 0) { set_error("PSD cones are not handled by this build"); return SCS_UNSUPPORTED; }
 
     // CSR of A (counting sort by row; columns visited in order keep each row
     // sorted by column, so duplicates are adjacent and are summed)
@@ -140,6 +141,7 @@ int validate_settings(const scs_settings &s) {
         return SCS_INVALID_INPUT;
     }
     if (!(s.cg_adapt >= 0.0) || !(s.cg_tol_rel >= 0.0)) { set_error("negative CG tolerance setting"); return SCS_INVALID_INPUT; }
+    if (!(s.psd_fp64_cond >= 1.0)) { set_error("psd_fp64_cond must be >= 1"); return SCS_INVALID_INPUT; }
     if (s.precision != 0 && s.precision != 1) { set_error("precision must be 0 or 1"); return SCS_INVALID_INPUT; }
     if (s.block_scale < 0 || s.block_scale > 2) { set_error("block_scale must be 0, 1 or 2"); return SCS_INVALID_INPUT; }
     return 0;
@@ -178,6 +180,7 @@ void scs_default_settings(scs_settings *s) {
     s->cg_adapt = 0.3;
     s->cg_tol_rel = 0.0;
     s->time_limit_s = 0.0;
+    s->psd_fp64_cond = 1e6;
     s->max_iters = 10000;
     s->check_interval = 20;
     s->cg_max_iters = 50;
@@ -277,6 +280,11 @@ int32_t scs_dims(scs_work *w, int32_t *m, int32_t *n, int64_t *nnz, int64_t *dev
 int32_t scs_counters(scs_work *w, int32_t *iters, int64_t *cg_iters) {
     if (!w || !w->eng) { set_error("null work"); return SCS_INVALID_INPUT; }
     return guarded([&] { return w->eng->counters(iters, cg_iters); });
+}
+
+int32_t scs_psd_counters(scs_work *w, int64_t *calls, int64_t *sweeps, int64_t *fp64_blocks) {
+    if (!w || !w->eng) { set_error("null work"); return SCS_INVALID_INPUT; }
+    return guarded([&] { return w->eng->psd_counters(calls, sweeps, fp64_blocks); });
 }
 
 const char *scs_last_error(void) { return g_last_error.c_str(); }

@@ -41,6 +41,9 @@ struct Scalars {
     int32_t status;     // termination status written by the check
     int32_t dev_error;  // set by a kernel whose bounded wait timed out
     int64_t cg_total;   // CG steps since the last reset
+    unsigned long long psd_calls;    // PSD block projections since setup
+    unsigned long long psd_sweeps;   // their Jacobi sweeps
+    unsigned long long psd_fp64;     // of them reconstructed in FP64
 };
 
 struct ReduceBuf {

@@ -119,6 +119,7 @@ class Engine : public EngineBase {
                 if (!Sh_->active) break;
             }
             launch_K6();
+            if (psd_.npsd) timed(3, [&] { launch_KP(); });
             timed(2, [&] { launch_K7(); });
         }
         SCS_CUDA(cudaStreamSynchronize(stream_));
@@ -126,7 +127,7 @@ class Engine : public EngineBase {
     }
 
     int kernel_time(int kind, double *ms, int64_t *launches) override {
-        if (kind < 0 || kind > 2) return SCS_INVALID_INPUT;
+        if (kind < 0 || kind > 3) return SCS_INVALID_INPUT;
         if (ms) *ms = prof_ms_[kind];
         if (launches) *launches = prof_n_[kind];
         prof_ms_[kind] = 0.0;
@@ -162,6 +163,16 @@ class Engine : public EngineBase {
         if (n) *n = n_;
         if (nnz) *nnz = nnz_;
         if (bytes) *bytes = bytes_;
+    }
+
+    int psd_counters(int64_t *calls, int64_t *sweeps, int64_t *fp64) override {
+        SCS_CUDA(cudaSetDevice(device_));
+        SCS_CUDA(cudaMemcpyAsync(Sh_, S_, sizeof(Scalars), cudaMemcpyDeviceToHost, stream_));
+        SCS_CUDA(cudaStreamSynchronize(stream_));
+        if (calls) *calls = static_cast<int64_t>(Sh_->psd_calls);
+        if (sweeps) *sweeps = static_cast<int64_t>(Sh_->psd_sweeps);
+        if (fp64) *fp64 = static_cast<int64_t>(Sh_->psd_fp64);
+        return 0;
     }
 
     int counters(int32_t *iters, int64_t *cg_iters) override {
@@ -326,9 +337,17 @@ class Engine : public EngineBase {
             avg_len.push_back(qs);
             off += qs;
         }
+        std::vector<int32_t> psd_off;
+        std::vector<int64_t> psd_voff;
+        int64_t vtot = 0;
+        int psd_nmax = 0;
         for (int32_t ss : P.s) {     // PSD blocks: scaled as one block each
             avg_off.push_back(off);
             avg_len.push_back(ss * (ss + 1) / 2);
+            psd_off.push_back(off);
+            psd_voff.push_back(vtot);
+            vtot += psd_mat_elems(ss);
+            psd_nmax = std::max(psd_nmax, static_cast<int>(ss));
             off += ss * (ss + 1) / 2;
         }
         K.exp_off = off;
@@ -342,6 +361,38 @@ class Engine : public EngineBase {
         if (K.nb_elem < 1) K.nb_elem = 1;
         K.nb_soc = (K.nq + kWarps - 1) / kWarps;
         K.nb_exp = (K.ep + kExpPerCta - 1) / kExpPerCta;
+        K.npsd = static_cast<int>(P.s.size());
+        if (K.npsd) {
+            // PSD blocks: eigenvector storage (warm start), per-block step
+            // lengths, and global matrices when three do not fit on chip
+            PsdDev<T> D{};
+            D.npsd = K.npsd;
+            D.ord = upload(P.s);
+            D.off = upload(psd_off);
+            D.voff = upload(psd_voff);
+            D.V = dalloc<T>(vtot);
+            D.dd = dalloc<double>(K.npsd);
+            D.ne_max = psd_ne(psd_nmax);
+            bool on_chip = false;
+            psd_smem_ = psd_smem_bytes<T>(psd_nmax, on_chip);
+            D.smem = on_chip ? 1 : 0;
+            D.small_bytes = static_cast<int>(psd_small_bytes<T>(D.ne_max));
+            D.fp64_cond = st_.psd_fp64_cond;
+            if (!on_chip) {
+                D.work_stride = psd_mat_elems(psd_nmax);
+                D.work = dalloc<T>(static_cast<size_t>(K.npsd) * 2 * D.work_stride);
+            }
+            if (on_chip)
+                SCS_CUDA(cudaFuncSetAttribute(psd_project_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              static_cast<int>(psd_smem_)));
+            else
+                SCS_CUDA(cudaFuncSetAttribute(psd_project_kernel<T, false>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(psd_smem_)));
+            SCS_CUDA(cudaMemsetAsync(D.dd, 0, sizeof(double) * K.npsd, stream_));
+            K.psd_dd = D.dd;
+            psd_ = D;
+            psd_identity();
+        }
         cone_ = K;
         const int32_t *d_avg_off = upload(avg_off), *d_avg_len = upload(avg_len);
         const int navg = static_cast<int>(avg_off.size());
@@ -355,7 +406,6 @@ class Engine : public EngineBase {
         rb_.cap = rb_cap_;
         rb_.counter = dalloc<unsigned>(kSiteCount);
         SCS_CUDA(cudaMemsetAsync(rb_.counter, 0, sizeof(unsigned) * kSiteCount, stream_));
-        S_ = dalloc<Scalars>(1);
 
         // ---- equilibration, Sec. 5 (FP64) ----
         if (st_.normalize) {
@@ -528,6 +578,14 @@ class Engine : public EngineBase {
         SCS_CUDA(cudaStreamSynchronize(stream_));
     }
 
+    // eigenvectors of every PSD block back to I (cold Jacobi start)
+    void psd_identity() {
+        if (!psd_.npsd) return;
+        psd_identity_kernel<T><<<std::min(psd_.npsd, sms_ * 4), kBlock, 0, stream_>>>(psd_.V, psd_.ord, psd_.voff,
+                                                                                   psd_.npsd);
+        SCS_CUDA(cudaGetLastError());
+    }
+
     void fill(double *d, int len, double val) {
         foreach_kernel<<<grid_for(len), kBlock, 0, stream_>>>([=] __device__(int i) { d[i] = val; }, len);
     }
@@ -545,6 +603,7 @@ class Engine : public EngineBase {
 
     // Sec. 3.4: u0 = (0, 0, 1), v0 = (0, 0, 1); CG warm start from zero
     void set_initial_point() {
+        psd_identity();
         SCS_CUDA(cudaMemsetAsync(u_, 0, sizeof(T) * N_, stream_));
         SCS_CUDA(cudaMemsetAsync(v_, 0, sizeof(T) * N_, stream_));
         SCS_CUDA(cudaMemsetAsync(z_, 0, sizeof(T) * n_, stream_));
@@ -598,6 +657,15 @@ class Engine : public EngineBase {
     void launch_K6() {
         smw_kernel<T><<<grid_for(n_ + m_), kBlock, 0, cur_>>>(n_, m_, cT_, bT_, z_, yacc_, S_, rb_);
     }
+    void launch_KP() {
+        if (!psd_.npsd) return;
+        ProjArgs<T> a{n_, m_, N_, u_, v_, pT_, z_, yacc_, S_};
+        PsdStats st{&S_->psd_sweeps, &S_->psd_fp64, &S_->psd_calls};
+        if (psd_.smem)
+            psd_project_kernel<T, true><<<psd_.npsd, kPsdThreads, psd_smem_, cur_>>>(a, psd_, st);
+        else
+            psd_project_kernel<T, false><<<psd_.npsd, kPsdThreads, psd_smem_, cur_>>>(a, psd_, st);
+    }
     void launch_K7() {
         ProjArgs<T> a{n_, m_, N_, u_, v_, pT_, z_, yacc_, S_};
         const int grid = proj_grid();
@@ -638,6 +706,7 @@ class Engine : public EngineBase {
             launch_K5(CondHandle{0, 0});
         }
         launch_K6();
+        launch_KP();
         launch_K7();
     }
 
@@ -685,6 +754,7 @@ class Engine : public EngineBase {
         SCS_CUDA(cudaStreamEndCapture(body_stream_, &body_out));
         cur_ = stream_;
         launch_K6();
+        launch_KP();
         launch_K7();
         cudaGraph_t done_graph;
         SCS_CUDA(cudaStreamEndCapture(stream_, &done_graph));
@@ -715,8 +785,10 @@ class Engine : public EngineBase {
     cudaGraph_t graph_ = nullptr;
     cudaGraphExec_t exec_ = nullptr;
     std::vector<cudaEvent_t> ev_;
-    double prof_ms_[3] = {0, 0, 0};
-    int64_t prof_n_[3] = {0, 0, 0};
+    double prof_ms_[4] = {0, 0, 0, 0};
+    int64_t prof_n_[4] = {0, 0, 0, 0};
+    PsdDev<T> psd_{};
+    size_t psd_smem_ = 0;
 };
 
 }  // namespace scs

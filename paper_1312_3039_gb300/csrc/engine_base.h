@@ -46,6 +46,7 @@ class EngineBase {
     virtual int get_scaling(double *D, double *E, double *sigma, double *rho) = 0;
     virtual void dims(int32_t *m, int32_t *n, int64_t *nnz, int64_t *bytes) = 0;
     virtual int counters(int32_t *iters, int64_t *cg_iters) = 0;
+    virtual int psd_counters(int64_t *calls, int64_t *sweeps, int64_t *fp64) = 0;
     double setup_s = 0.0;
 };
 

@@ -23,7 +23,10 @@
 //   K4  SpMV A^T : z += alpha p,  r -= alpha (p + A^T q),  new r.s, ||r||
 //   K5  update   : y_acc += alpha q (keeps y_acc = r_y + A z),  p = s + beta p
 //   K6  SMW      : gamma = (c^.z_x + b^.y_acc) / (1 + h^T p)
-//   K7  relax + project onto C + dual update (fused, per cone type)
+//   KP  relax + project + dual update of the PSD blocks (one CTA per block,
+//       Jacobi eigensolver; psd.cuh), when the cone has PSD blocks
+//   K7  relax + project onto C + dual update (fused, per cone type) of the
+//       other rows; its last CTA adds the PSD blocks' step lengths
 // Each reduction is a deterministic grid sum whose last CTA updates the
 // scalars (and, inside a CUDA graph, the CG loop's conditional handle).
 //
@@ -40,6 +43,7 @@
 
 #include "common.cuh"
 #include "cones.cuh"
+#include "psd.cuh"
 #include "spmv.cuh"
 
 namespace scs {
@@ -251,6 +255,8 @@ struct ConeDev {
     int ep;                // exponential triples
     int exp_off;           // row offset of the first triple
     int nb_elem, nb_soc, nb_exp;
+    int npsd;              // PSD blocks (projected by psd_project_kernel)
+    const double *psd_dd;  // squared step length of each PSD block's rows
 };
 
 template <typename T>
@@ -364,9 +370,94 @@ __global__ void __launch_bounds__(kBlock) relax_project_kernel(ProjArgs<T> a, Co
     }
     double red[1] = {static_cast<double>(dd)}, tot[1];
     if (grid_sum<1>(red, rb, kSiteProj, tot)) {
-        if (threadIdx.x == 0) {
-            a.S->dstep = sqrt(tot[0]);
-            a.S->k += 1;
+        if (threadIdx.x < 32) {
+            double extra = 0.0;
+            for (int b = threadIdx.x; b < K.npsd; b += 32) extra += K.psd_dd[b];
+            extra = warp_sum(extra);
+            if (threadIdx.x == 0) {
+                a.S->dstep = sqrt(tot[0] + extra);
+                a.S->k += 1;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// KP: relax + project + dual update of the PSD blocks, one CTA per block.
+// The rows of block b start at y-row P.off[b]; the block's eigenvectors
+// persist in P.V between iterations (warm start of the Jacobi sweeps).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct PsdDev {
+    int npsd;
+    const int32_t *ord;    // order of each block
+    const int32_t *off;    // y-row offset of each block's svec
+    const int64_t *voff;   // offset of each block's eigenvector matrix in V
+    T *V;                  // eigenvectors (psd_ne x psd_ld per block)
+    T *work;               // 2 matrices per block when they do not fit on chip
+    int64_t work_stride;   // elements of one matrix in `work`
+    double *dd;            // squared step length of each block
+    int ne_max;            // psd_ne of the largest order
+    int smem;              // X, V, W in shared memory
+    int small_bytes;       // bytes of the small tables at the start of shared memory
+    double fp64_cond;      // FP64 reconstruction above this spread of the positive eigenvalues
+};
+
+template <typename T>
+struct PsdEngineIO {
+    const ProjArgs<T> *a;
+    T gamma, alpha;
+    int base;              // global index of the block's first row
+    T dd;
+    __device__ T in(int64_t s) const {
+        const int idx = base + static_cast<int>(s);
+        return relaxed(*a, idx, gamma, alpha) - a->v[idx];
+    }
+    __device__ void out(int64_t s, T up) {
+        const int idx = base + static_cast<int>(s);
+        const T uo = a->u[idx], vo = a->v[idx];
+        const T t = relaxed(*a, idx, gamma, alpha) - vo;
+        const T vn = up - t;
+        a->u[idx] = up;
+        a->v[idx] = vn;
+        dd += (up - uo) * (up - uo) + (vn - vo) * (vn - vo);
+    }
+};
+
+// kSm: X, V, W in shared memory (else X, W in P.work and V in place in P.V)
+template <typename T, bool kSm>
+__global__ void __launch_bounds__(kPsdThreads, 1) psd_project_kernel(ProjArgs<T> a, PsdDev<T> P, PsdStats st) {
+    extern __shared__ __align__(16) unsigned char psd_smem[];
+    const int b = blockIdx.x;
+    const int n = P.ord[b];
+    const int ne = psd_ne(n), ld = ne + 1;
+    const PsdSmall<T> sm = psd_small_tables<T>(psd_smem, P.ne_max);
+    T *keep = P.V + P.voff[b];
+    T *X, *V, *W;
+    if constexpr (kSm) {
+        X = reinterpret_cast<T *>(psd_smem + P.small_bytes);
+        V = X + ne * ld;
+        W = V + ne * ld;
+    } else {
+        X = P.work + (size_t)b * 2 * P.work_stride;
+        W = X + P.work_stride;
+        V = keep;
+    }
+    PsdEngineIO<T> io{&a, static_cast<T>(a.S->gamma), static_cast<T>(a.S->relax), a.n + P.off[b], T(0)};
+    psd_project_block<T>(io, n, X, V, W, keep, sm, st, P.fp64_cond);
+    const double dd = psd_block_sum(static_cast<double>(io.dd), sm.red);
+    if (threadIdx.x == 0) P.dd[b] = dd;
+}
+
+// V <- I for every PSD block (cold start of the eigenvector warm start)
+template <typename T>
+__global__ void psd_identity_kernel(T *V, const int32_t *ord, const int64_t *voff, int npsd) {
+    for (int b = blockIdx.x; b < npsd; b += gridDim.x) {
+        const int ne = psd_ne(ord[b]), ld = ne + 1;
+        T *M = V + voff[b];
+        for (int e = threadIdx.x; e < ne * ld; e += blockDim.x) {
+            const int i = e / ld, j = e - i * ld;
+            M[e] = (i == j) ? T(1) : T(0);
         }
     }
 }

@@ -1,9 +1,9 @@
 // Stand-alone cone projection of a batch of vectors on the device
 // (scs_project): Euclidean projection onto K or K* block by block, with the
 // squared distance moved summed by a deterministic grid reduction.  The
-// same projections as the iteration's fused kernel (zero/free, nonnegative,
-// second-order, exponential via Moreau); used to put predicted warm starts
-// back into the cones.
+// same projections as the iteration's kernels (zero/free, nonnegative,
+// second-order, PSD by a cold-started Jacobi eigensolver, exponential via
+// Moreau); used to put predicted warm starts back into the cones.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -15,6 +15,7 @@
 #include "common.cuh"
 #include "cones.cuh"
 #include "engine_base.h"
+#include "psd.cuh"
 
 namespace scs {
 
@@ -28,6 +29,8 @@ struct ProjCone {
     int exp_off;
     int64_t count;         // vectors
     int g_elem, g_soc, g_exp;   // CTAs of each region (grid-stride inside)
+    int g_psd;             // CTAs of the PSD launch that ran before (0: none)
+    const double *psd_dd;  // their squared distances
 };
 
 // Regions: [0, g_exp) exponential triples (64 per CTA pass), then
@@ -93,8 +96,60 @@ __global__ void __launch_bounds__(kBlock) cone_project_kernel(ProjCone P, int du
     }
     double red[1] = {dd}, tot[1];
     if (grid_sum<1>(red, rb, kSiteMisc, tot)) {
-        if (threadIdx.x == 0) *dist2 = tot[0];
+        if (threadIdx.x < 32) {
+            double extra = 0.0;
+            for (int c = threadIdx.x; c < P.g_psd; c += 32) extra += P.psd_dd[c];
+            extra = warp_sum(extra);
+            if (threadIdx.x == 0) *dist2 = tot[0] + extra;
+        }
     }
+}
+
+// PSD blocks of a batch: one CTA per (vector, block) pair in grid-stride
+// order, FP64, Jacobi from V = I (nothing is kept between calls).  The
+// CTA's squared distance goes to dd[blockIdx.x].
+struct PsdBatchIO {
+    const double *src;
+    double *dst;
+    int64_t base;
+    double dd;
+    __device__ double in(int64_t s) const { return src[base + s]; }
+    __device__ void out(int64_t s, double p) {
+        const double t = src[base + s];
+        dst[base + s] = p;
+        dd += (p - t) * (p - t);
+    }
+};
+
+template <bool kSm>
+__global__ void __launch_bounds__(kPsdThreads, 1) psd_batch_kernel(const double *__restrict__ v, double *out, int m,
+                                                                const int32_t *ord, const int32_t *off, int nblk,
+                                                                int64_t count, double *work, int64_t work_stride,
+                                                                int small_bytes, int ne_max, double *dd) {
+    extern __shared__ __align__(16) unsigned char psd_smem[];
+    const PsdSmall<double> sm = psd_small_tables<double>(psd_smem, ne_max);
+    double acc = 0.0;
+    for (int64_t pr = blockIdx.x; pr < count * nblk; pr += gridDim.x) {
+        const int64_t vec = pr / nblk;
+        const int blk = static_cast<int>(pr % nblk);
+        const int n = ord[blk];
+        const int ne = psd_ne(n), ld = ne + 1;
+        double *X, *V, *W;
+        if constexpr (kSm) {
+            X = reinterpret_cast<double *>(psd_smem + small_bytes);
+            V = X + ne * ld;
+            W = V + ne * ld;
+        } else {
+            X = work + (size_t)blockIdx.x * 3 * work_stride;
+            V = X + work_stride;
+            W = V + work_stride;
+        }
+        PsdBatchIO io{v, out, vec * m + off[blk], 0.0};
+        psd_project_block<double>(io, n, X, V, W, nullptr, sm, PsdStats{nullptr, nullptr, nullptr}, 0.0);
+        acc += io.dd;
+    }
+    acc = psd_block_sum(acc, sm.red);
+    if (threadIdx.x == 0) dd[blockIdx.x] = acc;
 }
 
 // Region grids for a batch (each region gets CTAs only if it has work).
@@ -111,21 +166,29 @@ inline void project_grid(ProjCone &P, int max_ctas) {
 
 // Validate the cone, fill the SOC tables (host) and the row offsets.
 inline int project_setup(const scs_cone *k, int64_t count, ProjCone &P, std::vector<int32_t> &qoff,
-                         std::vector<int32_t> &qlen, std::string &err) {
+                         std::vector<int32_t> &qlen, std::vector<int32_t> &soff, std::string &err) {
     if (!k || count < 0) { err = "bad argument"; return SCS_INVALID_INPUT; }
-    if (k->z < 0 || k->l < 0 || k->nq < 0 || k->ns < 0 || k->ep < 0 || (k->nq > 0 && !k->q)) {
+    if (k->z < 0 || k->l < 0 || k->nq < 0 || k->ns < 0 || k->ep < 0 || (k->nq > 0 && !k->q) ||
+        (k->ns > 0 && !k->s)) {
         err = "bad cone";
         return SCS_INVALID_INPUT;
     }
-    if (k->ns > 0) { err = "PSD cones are not handled by this build"; return SCS_UNSUPPORTED; }
     int64_t off = (int64_t)k->z + k->l;
     qoff.clear();
     qlen.clear();
+    soff.clear();
     for (int i = 0; i < k->nq; ++i) {
         if (k->q[i] < 1) { err = "SOC size must be >= 1"; return SCS_INVALID_INPUT; }
         qoff.push_back((int32_t)off);
         qlen.push_back(k->q[i]);
         off += k->q[i];
+    }
+    for (int i = 0; i < k->ns; ++i) {
+        if (k->s[i] < 1) { err = "PSD order must be >= 1"; return SCS_INVALID_INPUT; }
+        if (k->s[i] > kPsdMaxOrder) { err = "PSD order above 1024"; return SCS_UNSUPPORTED; }
+        soff.push_back((int32_t)off);
+        off += (int64_t)k->s[i] * (k->s[i] + 1) / 2;
+        if (off > (int64_t)1 << 30) { err = "cone too large"; return SCS_UNSUPPORTED; }
     }
     P.exp_off = (int)off;
     off += 3 * (int64_t)k->ep;
@@ -147,9 +210,9 @@ extern "C" int32_t scs_project(const scs_cone *k, int32_t dual, const double *v,
                                double *dist2, void *stream) {
     using namespace scs;
     ProjCone P{};
-    std::vector<int32_t> qoff, qlen;
+    std::vector<int32_t> qoff, qlen, soff;
     std::string err;
-    int rc = project_setup(k, count, P, qoff, qlen, err);
+    int rc = project_setup(k, count, P, qoff, qlen, soff, err);
     if (rc) return rc;
     if (count == 0 || P.m == 0) {
         if (dist2) *dist2 = 0.0;
@@ -162,20 +225,48 @@ extern "C" int32_t scs_project(const scs_cone *k, int32_t dual, const double *v,
         return SCS_DEVICE_ERROR;
     project_grid(P, sms * 8);
     const int grid = P.g_exp + P.g_soc + P.g_elem;
-    // scratch for this call: partial sums, arrival counters, SOC tables, result
-    double *partials = nullptr, *res = nullptr;
+    // PSD launch: one CTA per (vector, block) pair up to 4 per SM
+    const int nps = static_cast<int>(soff.size());
+    int n_max = 0;
+    for (int i = 0; i < nps; ++i) n_max = std::max(n_max, (int)k->s[i]);
+    const int g_psd = nps ? (int)std::min<int64_t>(count * nps, (int64_t)sms * 4) : 0;
+    bool on_chip = false;
+    const size_t psd_smem = nps ? psd_smem_bytes<double>(n_max, on_chip) : 0;
+    const int64_t wstride = nps ? psd_mat_elems(n_max) : 0;
+    // scratch for this call: partial sums, arrival counters, SOC and PSD
+    // tables, result, PSD partial sums and (large orders) PSD matrices
+    double *partials = nullptr, *res = nullptr, *psd_dd = nullptr, *psd_work = nullptr;
     unsigned *counter = nullptr;
     int32_t *tables = nullptr;
     rc = 0;
+    const size_t ntab = 2 * qoff.size() + 2 * soff.size() + 2;
     if (cudaMalloc(&partials, sizeof(double) * kMaxRed * grid) || cudaMalloc(&counter, sizeof(unsigned) * kSiteCount) ||
-        cudaMalloc(&res, sizeof(double)) || cudaMalloc(&tables, sizeof(int32_t) * (2 * qoff.size() + 2)))
+        cudaMalloc(&res, sizeof(double)) || cudaMalloc(&tables, sizeof(int32_t) * ntab) ||
+        (nps && cudaMalloc(&psd_dd, sizeof(double) * g_psd)) ||
+        (nps && !on_chip && cudaMalloc(&psd_work, sizeof(double) * 3 * wstride * g_psd)))
         rc = SCS_DEVICE_ERROR;
+    int32_t *t_soff = tables + 2 * qoff.size(), *t_sord = t_soff + soff.size();
     if (!rc) {
         if (!qoff.empty() && (cudaMemcpyAsync(tables, qoff.data(), 4 * qoff.size(), cudaMemcpyHostToDevice, s) ||
                               cudaMemcpyAsync(tables + qoff.size(), qlen.data(), 4 * qlen.size(),
                                               cudaMemcpyHostToDevice, s)))
             rc = SCS_DEVICE_ERROR;
+        if (nps && (cudaMemcpyAsync(t_soff, soff.data(), 4 * soff.size(), cudaMemcpyHostToDevice, s) ||
+                    cudaMemcpyAsync(t_sord, k->s, 4 * soff.size(), cudaMemcpyHostToDevice, s)))
+            rc = SCS_DEVICE_ERROR;
         if (cudaMemsetAsync(counter, 0, sizeof(unsigned) * kSiteCount, s)) rc = SCS_DEVICE_ERROR;
+    }
+    if (!rc && nps) {
+        auto kern = on_chip ? psd_batch_kernel<true> : psd_batch_kernel<false>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psd_smem))
+            rc = SCS_DEVICE_ERROR;
+        if (!rc) {
+            kern<<<g_psd, kPsdThreads, psd_smem, s>>>(v, out, P.m, t_sord, t_soff, nps, count, psd_work, wstride,
+                                                       (int)psd_small_bytes<double>(psd_ne(n_max)), psd_ne(n_max),
+                                                       psd_dd);
+            P.g_psd = g_psd;
+            P.psd_dd = psd_dd;
+        }
     }
     if (!rc) {
         P.q_off = tables;
@@ -192,6 +283,8 @@ extern "C" int32_t scs_project(const scs_cone *k, int32_t dual, const double *v,
     cudaFree(counter);
     cudaFree(res);
     cudaFree(tables);
+    cudaFree(psd_dd);
+    cudaFree(psd_work);
     return rc;
 }
 
@@ -226,11 +319,12 @@ extern "C" int32_t scs_project_noalloc(const scs_cone *k, int32_t dual, const do
                                        int64_t count, double *dist2, void *stream) {
     using namespace scs;
     ProjCone P{};
-    std::vector<int32_t> qoff, qlen;
+    std::vector<int32_t> qoff, qlen, soff;
     std::string err;
-    int rc = project_setup(k, count, P, qoff, qlen, err);
+    int rc = project_setup(k, count, P, qoff, qlen, soff, err);
     if (rc) return rc;
     if ((int64_t)qoff.size() > kNoAllocMaxSoc) return SCS_UNSUPPORTED;   // more SOC blocks than the scratch holds
+    if (!soff.empty()) return SCS_UNSUPPORTED;     // PSD blocks need matrix scratch this entry point does not hold
     if (count == 0 || P.m == 0) {
         if (dist2) *dist2 = 0.0;
         return 0;

@@ -1,0 +1,536 @@
+// Projection of one PSD block onto the positive semidefinite cone, one CTA
+// per block (Sec. 6.1: eigendecompose the symmetric matrix and zero its
+// negative eigenvalues; the PSD cone is self-dual, so the same map serves
+// K and K*).
+//
+// Storage: a block of order n is held in svec form, the lower triangle
+// column by column with the off-diagonal entries times sqrt 2 (svec is then
+// an isometry and the Euclidean projection in svec space is the Frobenius
+// projection of the matrix).
+//
+// On the CTA the block is a dense ne x ne matrix, ne = n rounded up to a
+// multiple of 4 (the padding rows and columns are zero and never rotated),
+// row-major with leading dimension ld = ne + 1 (odd, so a column walk hits
+// 32 different shared-memory banks).  Three such matrices X, V, W live in
+// shared memory when they fit, else in a global scratch area of the CTA.
+//
+// Eigensolver: parallel cyclic Jacobi.  A sweep is ne - 1 rounds of the
+// round-robin tournament; each round rotates ne/2 disjoint index pairs at
+// once.  The rotation of pair (p, q) zeroes X[p][q] (the two-by-two
+// symmetric Schur decomposition: tau = (x_qq - x_pp) / (2 x_pq),
+// t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c).
+// One thread applies both sides of the round's rotations to one 2 x 2 block
+// of the lower triangle and mirrors it, so X stays exactly symmetric.  V
+// accumulates the rotations (its columns become the eigenvectors).  A
+// rotation is skipped when |x_pq| <= eps max(sqrt|x_pp x_qq|, ||X||_F / ne).
+// The sweeps stop once ||off(X)||_F <= tol ||X||_F (tol 1e-6 in FP32, 1e-14
+// in FP64): the projection onto the PSD cone is 1-Lipschitz, so taking the
+// diagonal for the eigenvalues then moves the result by at most that much.
+// The round's pairs and rotations sit in shared-memory tables, and each
+// thread walks its 2 x 2 blocks (the lower triangle folded into an
+// h/2 x (h + 1) rectangle) and its rows of V by increments, without integer
+// division in the sweep.
+//
+// Warm start (the iteration's blocks change little from one ADMM step to
+// the next): V from the previous projection is first made orthogonal again
+// by one Newton-Schulz step V <- V (3 I - V^T V) / 2, the input is rotated
+// to X <- V^T X V, and Jacobi continues from that nearly diagonal matrix.
+//
+// Reconstruction P = V diag(max(lambda, 0)) V^T sums over the positive
+// eigenvalues only.  With FP32 storage a block whose positive eigenvalues
+// spread wider than `fp64_cond` (max >= fp64_cond min; 1e6 by default) is
+// summed in FP64: in FP32 the terms of the small eigenvalues would drown in
+// the rounding of the large ones.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace scs {
+
+constexpr int kPsdThreads = 512;
+constexpr int kPsdMaxSweeps = 40;
+constexpr int kPsdMaxOrder = 1024;
+constexpr int kPsdSmemCap = 232448;       // bytes of dynamic shared memory per CTA (opt-in maximum)
+
+template <typename T> struct PsdEps;
+template <> struct PsdEps<float> {
+    static constexpr float v = FLT_EPSILON;
+    static constexpr float off_tol = 1e-6f;
+};
+template <> struct PsdEps<double> {
+    static constexpr double v = DBL_EPSILON;
+    static constexpr double off_tol = 1e-14;
+};
+
+__host__ __device__ inline int psd_ne(int n) { return n < 4 ? 4 : (n + 3) & ~3; }
+__host__ __device__ inline int psd_ld(int n) { return psd_ne(n) + 1; }
+__host__ __device__ inline int64_t psd_svec_len(int n) { return (int64_t)n * (n + 1) / 2; }
+__host__ __device__ inline int64_t psd_mat_elems(int n) { return (int64_t)psd_ne(n) * psd_ld(n); }
+
+// Small per-CTA tables (shared memory in every mode), sized for order ne.
+// Rotation of one index pair of the current round: J = [[c, s], [-s, c]] on
+// columns (p, q), t = s / c; pq = p | q << 16.  One 16-byte (FP32) or 32-byte
+// (FP64) record, read with one wide shared-memory load.
+template <typename T>
+struct alignas(16) PsdRot {
+    T c, s, t;
+    int pq;
+};
+
+template <typename T>
+__host__ __device__ inline size_t psd_small_bytes(int ne) {
+    const size_t h = ne / 2;
+    size_t b = 32 * sizeof(double) + h * sizeof(PsdRot<T>) + ne * sizeof(T) + ne * sizeof(int) + 16 * sizeof(int);
+    return (b + 15) & ~size_t(15);
+}
+template <typename T>
+__host__ __device__ inline size_t psd_mats_bytes(int ne) {
+    return 3 * (size_t)ne * (ne + 1) * sizeof(T);
+}
+// Dynamic shared memory of a launch whose largest block has order n_max;
+// `smem_mats` tells whether the three matrices fit on chip.
+template <typename T>
+inline size_t psd_smem_bytes(int n_max, bool &smem_mats) {
+    const int ne = psd_ne(n_max);
+    const size_t small = psd_small_bytes<T>(ne), mats = psd_mats_bytes<T>(ne);
+    smem_mats = small + mats <= (size_t)kPsdSmemCap;
+    return smem_mats ? small + mats : small;
+}
+
+// Pair k of round r of the round-robin tournament on ne players (ne even):
+// player ne-1 stays, the others turn; every pair meets once in ne-1 rounds.
+__device__ __forceinline__ void psd_pair(int r, int k, int ne, int &p, int &q) {
+    const int m = ne - 1;
+    if (k == 0) {
+        p = r;
+        q = m;
+    } else {
+        p = (r + k) % m;
+        q = (r - k + m) % m;
+    }
+}
+
+// Column j and row i of svec index s of an order-n block
+// (column j starts at j n - j (j - 1) / 2).
+__device__ __forceinline__ void psd_svec_ij(int64_t s, int n, int &i, int &j) {
+    const double b = 2.0 * n + 1.0;
+    int jj = static_cast<int>((b - sqrt(fmax(b * b - 8.0 * (double)s, 0.0))) * 0.5);
+    if (jj < 0) jj = 0;
+    if (jj > n - 1) jj = n - 1;
+    auto start = [n](int c) { return (int64_t)c * n - (int64_t)c * (c - 1) / 2; };
+    while (jj > 0 && start(jj) > s) --jj;
+    while (jj < n - 1 && start(jj + 1) <= s) ++jj;
+    j = jj;
+    i = jj + static_cast<int>(s - start(jj));
+}
+
+template <typename T>
+__device__ __forceinline__ T psd_block_sum(T v, double *red) {
+    // red: at least blockDim.x / 32 slots; result valid in every thread
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = static_cast<double>(v);
+    __syncthreads();
+    T t = lane < nw ? static_cast<T>(red[lane]) : T(0);
+    t = warp_sum(t);
+    __syncthreads();
+    return t;
+}
+
+// C = A^T B over the ne x ne output, inner index j in [0, kdim); rows of A
+// and B are contiguous (leading dimension ld).  Each thread owns a 4 x 4
+// tile with rows ti + r ne/4 and columns tk + c ne/4, so the lanes of a warp
+// read consecutive words of B and one broadcast word of A.  epi(i, k, acc).
+template <typename Acc, typename T, typename Epi>
+__device__ __forceinline__ void psd_gemm_atb(const T *A, const T *B, int ne, int ld, int kdim, Epi epi) {
+    const int q4 = ne >> 2;
+    const int tiles = q4 * q4;
+    for (int t = threadIdx.x; t < tiles; t += blockDim.x) {
+        const int ti = t / q4, tk = t - ti * q4;
+        Acc acc[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = Acc(0);
+        for (int j = 0; j < kdim; ++j) {
+            const T *a = A + (size_t)j * ld, *b = B + (size_t)j * ld;
+            Acc ar[4], bc[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) ar[r] = static_cast<Acc>(a[ti + r * q4]);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) bc[c] = static_cast<Acc>(b[tk + c * q4]);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fma(ar[r], bc[c], acc[r][c]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) epi(ti + r * q4, tk + c * q4, acc[r][c]);
+    }
+}
+
+// P[i][k] = sum over the positive eigenvalues j of lam_j Vt[j][i] Vt[j][k]
+// (Vt = V^T, rows are eigenvectors), written into P (full square).
+template <typename Acc, typename T>
+__device__ __forceinline__ void psd_reconstruct(const T *Vt, const T *lam, const int *pos, int npos, T *P, int ne,
+                                                int ld) {
+    const int q4 = ne >> 2;
+    const int tiles = q4 * q4;
+    for (int t = threadIdx.x; t < tiles; t += blockDim.x) {
+        const int ti = t / q4, tk = t - ti * q4;
+        Acc acc[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = Acc(0);
+        for (int jj = 0; jj < npos; ++jj) {
+            const int j = pos[jj];
+            const T *row = Vt + (size_t)j * ld;
+            const Acc w = static_cast<Acc>(lam[j]);
+            Acc ar[4], bc[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) ar[r] = w * static_cast<Acc>(row[ti + r * q4]);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) bc[c] = static_cast<Acc>(row[tk + c * q4]);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fma(ar[r], bc[c], acc[r][c]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) P[(size_t)(ti + r * q4) * ld + tk + c * q4] = static_cast<T>(acc[r][c]);
+    }
+}
+
+// dst = src^T (ne x ne)
+template <typename T>
+__device__ __forceinline__ void psd_transpose(const T *src, T *dst, int ne, int ld) {
+    for (int e = threadIdx.x; e < ne * ne; e += blockDim.x) {
+        const int i = e / ne, j = e - i * ne;
+        dst[(size_t)j * ld + i] = src[(size_t)i * ld + j];
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void psd_identity(T *M, int ne, int ld) {
+    for (int e = threadIdx.x; e < ne * ne; e += blockDim.x) {
+        const int i = e / ne, j = e - i * ne;
+        M[(size_t)i * ld + j] = i == j ? T(1) : T(0);
+    }
+}
+
+template <typename T>
+struct PsdSmall {
+    PsdRot<T> *rot;    // rotation of each pair of the current round
+    T *lam;            // eigenvalues
+    int *pos;          // indices of the positive eigenvalues
+    int *flags;        // [0..1] rotation flags of alternate rounds, [2] count, [3] ill
+    double *red;       // 32 block-reduction slots
+};
+
+template <typename T>
+__device__ __forceinline__ PsdSmall<T> psd_small_tables(unsigned char *base, int ne) {
+    PsdSmall<T> s;
+    const int h = ne / 2;
+    s.red = reinterpret_cast<double *>(base);
+    s.rot = reinterpret_cast<PsdRot<T> *>(s.red + 32);
+    s.lam = reinterpret_cast<T *>(s.rot + h);
+    s.pos = reinterpret_cast<int *>(s.lam + ne);
+    s.flags = s.pos + ne;
+    return s;
+}
+
+// ||off(X)||_F^2 (valid in every thread)
+template <typename T>
+__device__ __forceinline__ T psd_off2(const T *X, int ne, int ld, double *red) {
+    T o = T(0);
+    int i = threadIdx.x / ne, j = threadIdx.x - (threadIdx.x / ne) * ne;
+    const int di = blockDim.x / ne, dj = blockDim.x - di * ne;
+    for (int e = threadIdx.x; e < ne * ne; e += blockDim.x) {
+        if (i != j) {
+            const T x = X[(size_t)i * ld + j];
+            o += x * x;
+        }
+        i += di;
+        j += dj;
+        if (j >= ne) {
+            j -= ne;
+            ++i;
+        }
+    }
+    return psd_block_sum(o, red);
+}
+
+// Both sides of the round's rotations on the 2 x 2 block (i, j), i > j, of
+// the lower triangle, mirrored into the upper one.
+template <typename T>
+__device__ __forceinline__ void psd_rotate_block(T *X, int ld, const PsdRot<T> &ri, const PsdRot<T> &rj) {
+    const int pi = ri.pq & 0xffff, qi = ri.pq >> 16, pj = rj.pq & 0xffff, qj = rj.pq >> 16;
+    const int o_pp = pi * ld + pj, o_pq = pi * ld + qj, o_qp = qi * ld + pj, o_qq = qi * ld + qj;
+    const T a = X[o_pp], b = X[o_pq], c = X[o_qp], d = X[o_qq];
+    // rows: J_i^T from the left
+    const T a1 = ri.c * a - ri.s * c, b1 = ri.c * b - ri.s * d;
+    const T c1 = ri.s * a + ri.c * c, d1 = ri.s * b + ri.c * d;
+    // columns: J_j from the right
+    const T a2 = rj.c * a1 - rj.s * b1, b2 = rj.s * a1 + rj.c * b1;
+    const T c2 = rj.c * c1 - rj.s * d1, d2 = rj.s * c1 + rj.c * d1;
+    X[o_pp] = a2;
+    X[o_pq] = b2;
+    X[o_qp] = c2;
+    X[o_qq] = d2;
+    X[pj * ld + pi] = a2;
+    X[qj * ld + pi] = b2;
+    X[pj * ld + qi] = c2;
+    X[qj * ld + qi] = d2;
+}
+
+// Cyclic Jacobi on the symmetric X (ne x ne), accumulating V <- V J on the
+// first nrows_v rows of V.  Returns the number of sweeps run.
+//
+// Work split (fixed for the whole call, so the sweep has no integer
+// division): the lower 2 x 2 blocks (i >= j) are folded into h/2 rows of
+// h + 1 blocks (fold row r holds triangle rows r and h - 1 - r); `tpr`
+// threads share a fold row, taking every tpr-th block of it.  Each V row is
+// owned by threads that take every ks-th pair.
+template <typename T>
+__device__ __forceinline__ int psd_jacobi(T *X, T *V, int ne, int ld, int nrows_v, const PsdSmall<T> &sm, T fro) {
+    const int h = ne >> 1;
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const T eps = PsdEps<T>::v;
+    const T floor_abs = eps * fro / static_cast<T>(ne);
+    const T stop2 = (PsdEps<T>::off_tol * fro) * (PsdEps<T>::off_tol * fro);
+    const int nfold = h >> 1, rw = h + 1;
+    const int tpr = nt / nfold < 1 ? 1 : nt / nfold;
+    const int frow = tid / tpr, fcol0 = tid - frow * tpr;
+    const bool has_fold = frow < nfold;
+    const int ia = frow, ib = h - 1 - frow;          // the two triangle rows of this fold row
+    // V: rows [0, nrows_v) x pairs [0, h)
+    const bool v_small = nrows_v <= nt;
+    const int ks = v_small ? nt / nrows_v : 1;
+    const int vrow = v_small ? tid % nrows_v : tid, vk0 = v_small ? tid / nrows_v : 0;
+    if (psd_off2(X, ne, ld, sm.red) <= stop2) return 0;
+    if (tid == 0) {
+        sm.flags[0] = 0;
+        sm.flags[1] = 0;
+    }
+    __syncthreads();
+    int sweeps = 0, round = 0;
+    while (sweeps < kPsdMaxSweeps) {
+        ++sweeps;
+        bool any = false;
+        for (int r = 0; r < ne - 1; ++r, ++round) {
+            int *fl = sm.flags + (round & 1);
+            for (int k = tid; k < h; k += nt) {
+                int p, q;
+                psd_pair(r, k, ne, p, q);
+                const T app = X[p * ld + p], aqq = X[q * ld + q], apq = X[p * ld + q];
+                PsdRot<T> rt;
+                rt.c = T(1);
+                rt.s = T(0);
+                rt.t = T(0);
+                rt.pq = p | (q << 16);
+                const T thr = fmax(eps * sqrt(fabs(app * aqq)), floor_abs);
+                if (fabs(apq) > thr) {
+                    const T tau = (aqq - app) / (T(2) * apq);
+                    const T at = fabs(tau);
+                    const T root = at > T(1) ? at * sqrt(T(1) + (T(1) / at) / at) : sqrt(T(1) + at * at);
+                    T t = T(1) / (at + root);
+                    if (tau < T(0)) t = -t;
+                    rt.c = T(1) / sqrt(T(1) + t * t);
+                    rt.s = t * rt.c;
+                    rt.t = t;
+                    *fl = 1;
+                }
+                sm.rot[k] = rt;
+            }
+            if (tid == 0) sm.flags[(round + 1) & 1] = 0;
+            __syncthreads();
+            const bool rot = *fl != 0;
+            any = any || rot;
+            if (rot) {
+                if (has_fold) {
+                    const PsdRot<T> ra = sm.rot[ia], rb = sm.rot[ib];
+                    for (int cc = fcol0; cc < rw; cc += tpr) {
+                        const bool lo = cc <= frow;
+                        const PsdRot<T> &ri = lo ? ra : rb;
+                        const int j = lo ? cc : cc - frow - 1;
+                        const int i = lo ? ia : ib;
+                        const PsdRot<T> rj = sm.rot[j];
+                        if (ri.s == T(0) && rj.s == T(0)) continue;
+                        if (i == j) {
+                            const int p = ri.pq & 0xffff, q = ri.pq >> 16;
+                            const T apq = X[p * ld + q];
+                            X[p * ld + p] -= ri.t * apq;
+                            X[q * ld + q] += ri.t * apq;
+                            X[p * ld + q] = T(0);
+                            X[q * ld + p] = T(0);
+                        } else {
+                            psd_rotate_block(X, ld, ri, rj);
+                        }
+                    }
+                }
+                // V <- V J (columns p, q of every row)
+                if (v_small) {
+                    if (vk0 < ks) {
+                        T *vr = V + vrow * ld;
+                        for (int k = vk0; k < h; k += ks) {
+                            const PsdRot<T> rk = sm.rot[k];
+                            if (rk.s == T(0)) continue;
+                            const int p = rk.pq & 0xffff, q = rk.pq >> 16;
+                            const T vp = vr[p], vq = vr[q];
+                            vr[p] = rk.c * vp - rk.s * vq;
+                            vr[q] = rk.s * vp + rk.c * vq;
+                        }
+                    }
+                } else {
+                    for (int row = tid; row < nrows_v; row += nt) {
+                        T *vr = V + (size_t)row * ld;
+                        for (int k = 0; k < h; ++k) {
+                            const PsdRot<T> rk = sm.rot[k];
+                            if (rk.s == T(0)) continue;
+                            const int p = rk.pq & 0xffff, q = rk.pq >> 16;
+                            const T vp = vr[p], vq = vr[q];
+                            vr[p] = rk.c * vp - rk.s * vq;
+                            vr[q] = rk.s * vp + rk.c * vq;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (!any || psd_off2(X, ne, ld, sm.red) <= stop2) break;
+    }
+    return sweeps;
+}
+
+// Statistics of the projections (device counters, summed with atomics).
+struct PsdStats {
+    unsigned long long *sweeps;     // Jacobi sweeps
+    unsigned long long *fp64;       // blocks reconstructed in FP64
+    unsigned long long *calls;      // block projections
+};
+
+// Project one block.  io.in(s) returns svec entry s of the point to project;
+// io.out(s, p) receives svec entry s of the projection.  X, V, W: matrix
+// storage (shared or global); Vkeep: where the eigenvectors persist between
+// calls (nullptr: cold start, nothing kept; equal to V: kept in place).
+template <typename T, typename IO>
+__device__ __forceinline__ void psd_project_block(IO &io, int n, T *X, T *V, T *W, T *Vkeep, const PsdSmall<T> &sm,
+                                  PsdStats stats, double fp64_cond) {
+    const int ne = psd_ne(n), ld = ne + 1;
+    const int64_t len = psd_svec_len(n);
+    const T isq2 = T(0.70710678118654752440);
+    const bool warm = Vkeep != nullptr;
+    // ---- V: the previous eigenvectors, made orthogonal again, or I
+    if (warm) {
+        if (Vkeep != V)
+            for (int e = threadIdx.x; e < ne * ne; e += blockDim.x) {
+                const int i = e / ne, j = e - i * ne;
+                V[(size_t)i * ld + j] = Vkeep[(size_t)i * ld + j];
+            }
+        __syncthreads();
+        // W = V^T V; H = (3 I - W) / 2 in W; X = V^T; V = X^T H = V H
+        psd_gemm_atb<T>(V, V, ne, ld, ne, [&](int i, int k, T acc) {
+            W[(size_t)i * ld + k] = (i == k ? T(1.5) : T(0)) - T(0.5) * acc;
+        });
+        psd_transpose(V, X, ne, ld);
+        __syncthreads();
+        psd_gemm_atb<T>(X, W, ne, ld, ne, [&](int i, int k, T acc) { V[(size_t)i * ld + k] = acc; });
+        __syncthreads();
+    } else {
+        psd_identity(V, ne, ld);
+    }
+    // ---- X = smat(input), zero padding
+    for (int e = threadIdx.x; e < ne * ne; e += blockDim.x) {
+        const int i = e / ne, j = e - i * ne;
+        if (i >= n || j >= n) X[(size_t)i * ld + j] = T(0);
+    }
+    for (int64_t s = threadIdx.x; s < len; s += blockDim.x) {
+        int i, j;
+        psd_svec_ij(s, n, i, j);
+        T x = io.in(s);
+        if (i != j) x *= isq2;
+        X[(size_t)i * ld + j] = x;
+        X[(size_t)j * ld + i] = x;
+    }
+    __syncthreads();
+    if (warm) {
+        // X <- V^T X V, then mirrored from its lower triangle
+        psd_gemm_atb<T>(X, V, ne, ld, ne, [&](int i, int k, T acc) { W[(size_t)i * ld + k] = acc; });
+        __syncthreads();
+        psd_gemm_atb<T>(V, W, ne, ld, ne, [&](int i, int k, T acc) { X[(size_t)i * ld + k] = acc; });
+        __syncthreads();
+        for (int e = threadIdx.x; e < ne * ne; e += blockDim.x) {
+            const int i = e / ne, j = e - i * ne;
+            if (i < j) X[(size_t)i * ld + j] = X[(size_t)j * ld + i];
+        }
+        __syncthreads();
+    }
+    // ---- Frobenius norm, Jacobi
+    T f2 = T(0);
+    for (int e = threadIdx.x; e < ne * ne; e += blockDim.x) {
+        const int i = e / ne, j = e - i * ne;
+        const T x = X[(size_t)i * ld + j];
+        f2 += x * x;
+    }
+    f2 = psd_block_sum(f2, sm.red);
+    const int sweeps = psd_jacobi(X, V, ne, ld, n, sm, sqrt(f2));
+    // ---- eigenvalues, positive set, conditioning
+    for (int j = threadIdx.x; j < ne; j += blockDim.x) sm.lam[j] = X[(size_t)j * ld + j];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int np = 0;
+        T pmax = T(0), pmin = T(INFINITY);
+        for (int j = 0; j < n; ++j) {
+            const T l = sm.lam[j];
+            if (l > T(0)) {
+                sm.pos[np++] = j;
+                pmax = fmax(pmax, l);
+                pmin = fmin(pmin, l);
+            }
+        }
+        sm.flags[2] = np;
+        sm.flags[3] = (sizeof(T) < 8 && np > 0 && static_cast<double>(pmax) >= fp64_cond * static_cast<double>(pmin))
+                          ? 1 : 0;
+        if (stats.calls) {
+            atomicAdd(stats.calls, 1ull);
+            atomicAdd(stats.sweeps, (unsigned long long)sweeps);
+            if (sm.flags[3]) atomicAdd(stats.fp64, 1ull);
+        }
+    }
+    psd_transpose(V, W, ne, ld);       // W = V^T: eigenvectors as rows
+    __syncthreads();
+    const int npos = sm.flags[2];
+    if (sm.flags[3])
+        psd_reconstruct<double>(W, sm.lam, sm.pos, npos, X, ne, ld);
+    else
+        psd_reconstruct<T>(W, sm.lam, sm.pos, npos, X, ne, ld);
+    __syncthreads();
+    // ---- output in svec form (lower triangle of the symmetric P)
+    const T sq2 = T(1.41421356237309504880);
+    for (int64_t s = threadIdx.x; s < len; s += blockDim.x) {
+        int i, j;
+        psd_svec_ij(s, n, i, j);
+        T p = i == j ? X[(size_t)i * ld + j] : T(0.5) * (X[(size_t)i * ld + j] + X[(size_t)j * ld + i]) * sq2;
+        io.out(s, p);
+    }
+    // ---- keep the eigenvectors for the next call
+    if (warm && Vkeep != V)
+        for (int e = threadIdx.x; e < ne * ne; e += blockDim.x) {
+            const int i = e / ne, j = e - i * ne;
+            Vkeep[(size_t)i * ld + j] = V[(size_t)i * ld + j];
+        }
+    __syncthreads();
+}
+
+}  // namespace scs

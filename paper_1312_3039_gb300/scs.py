@@ -42,6 +42,7 @@ class Settings(C.Structure):
     _fields_ = [("eps_pri", C.c_double), ("eps_dual", C.c_double), ("eps_gap", C.c_double),
                 ("eps_infeas", C.c_double), ("eps_unbdd", C.c_double), ("alpha", C.c_double),
                 ("cg_rate", C.c_double), ("cg_adapt", C.c_double), ("cg_tol_rel", C.c_double), ("time_limit_s", C.c_double),
+                ("psd_fp64_cond", C.c_double),
                 ("max_iters", C.c_int32), ("check_interval", C.c_int32), ("cg_max_iters", C.c_int32),
                 ("normalize", C.c_int32), ("scale_passes", C.c_int32), ("block_scale", C.c_int32),
                 ("precision", C.c_int32),
@@ -97,6 +98,8 @@ def lib():
         L.scs_dims.restype = I32
         L.scs_counters.argtypes = [P, C.POINTER(I32), I64]
         L.scs_counters.restype = I32
+        L.scs_psd_counters.argtypes = [P, I64, I64, I64]
+        L.scs_psd_counters.restype = I32
         L.scs_project.argtypes = [C.POINTER(ConeC), I32, C.c_void_p, C.c_void_p, C.c_int64, D, C.c_void_p]
         L.scs_project.restype = I32
         if hasattr(L, "scs_project_noalloc"):
@@ -251,6 +254,12 @@ class Solver:
         cg = C.c_int64(0)
         self._check(lib().scs_counters(self._w, C.byref(it), C.byref(cg)))
         return it.value, cg.value
+
+    def psd_counters(self):
+        """(block projections, Jacobi sweeps, blocks reconstructed in FP64)."""
+        a, b, c = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+        self._check(lib().scs_psd_counters(self._w, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
 
     def dims(self):
         m, n = C.c_int32(0), C.c_int32(0)

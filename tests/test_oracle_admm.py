@@ -270,3 +270,15 @@ def test_weak_duality_band(seed):
     gap = abs(P.c @ r.x + P.b @ r.y)
     assert P.p_star - P.c @ r.x <= np.linalg.norm(P.y_star) * rp + 1e-9
     assert P.c @ r.x - P.p_star <= gap + np.linalg.norm(P.x_star) * rd + 1e-9
+
+
+def test_sdp_solve_known_optimum():
+    """Sec. 6.1 PSD cone in the whole iteration: a small SDP built from a
+    complementary PSD pair (one block with eigenvalues over 1e-7..1) solves
+    to the generator's optimum, with s in K and y in K*."""
+    P = synth.sdp(seed=4, n=60, n_psd=3, order=6, n_nonneg=20, density=0.2, n_ill=1)
+    st = exact_settings(eps_pri=1e-7, eps_dual=1e-7, eps_gap=1e-7)
+    r = admm.solve(P.A, P.b, P.c, P.cone, st)
+    assert r.status == admm.SOLVED
+    assert abs(r.pobj - P.p_star) <= 1e-5 * (1 + abs(P.p_star))
+    assert cones.in_K(r.s, P.cone, 1e-7) and cones.in_Kdual(r.y, P.cone, 1e-7)
