@@ -39,8 +39,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["mixed", "mixed_small", "sdp", "sdp_small", "sdp_blocks", "lp"],
+    ap.add_argument("--workload", choices=["mixed", "mixed_small", "sdp", "sdp_small", "sdp_blocks", "lp",
+                                           "portfolio_batch", "portfolio_batch_small"],
                     default="mixed")
+    ap.add_argument("--plain-sample", type=int, default=64,
+                    help="programs of a batched workload solved one by one by the plain solver")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-1e-4 solve")
@@ -224,6 +227,8 @@ def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
+    if args.workload.startswith("portfolio_batch"):
+        return run_reference_batch(args)
     P, desc = make_problem(args.workload, args.seed)
     from oracle import admm
     t0 = time.perf_counter()
@@ -247,6 +252,33 @@ def run_reference(args):
                                    f"(setup {setup:.1f} s not timed)"},
         "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_reference_batch(args):
+    """Reference arm of a batched workload: the FP64 oracle solving the
+    programs of a stratified sample one by one (one thread)."""
+    import multiprocessing as mp
+    q = mp.get_context("spawn").Queue()
+    per_step = max(args.cpu_seconds / max(args.steps, 1), 1.0)
+    t0 = time.perf_counter()
+    got = []
+    for _ in range(args.steps):
+        cpu_batch_job(args.workload, args.seed, per_step, q)
+        got.append(q.get())
+    el = time.perf_counter() - t0
+    done = sum(r.get("programs", 0) for r in got)
+    _, desc = batch_programs(args.workload, args.seed)
+    value = done / el if el > 0 else None
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "programs/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (Sec. 6.3 portfolio form, seed %d)" % args.seed,
+            "config": {"workload": desc, "precision": "fp64", "linsys": "direct (oracle)"},
+            "cpu_baseline": {"value": value, "unit": "programs/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{done} programs of a stratified sample, one thread"},
+            "e2e": {"value": value, "unit": "programs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -430,10 +462,190 @@ def run_gb300(args):
     return 0
 
 
+BATCH_DESC = ("{count} portfolio SOCPs (long-only factor model, Sec. 6.3 form with one risk SOC): n ~ U[20, 500] "
+              "assets, k = n/10 factors, F ~ N(0,1), mu ~ U(0,1); zero 1, nonneg n, SOC k+2 per program")
+
+
+def batch_programs(workload, seed):
+    from paper_1312_3039_gb300 import synth
+    count = 4096 if workload == "portfolio_batch" else 256
+    progs = synth.portfolio_batch(seed, count=count)
+    return progs, BATCH_DESC.format(count=count)
+
+
+def cpu_batch_job(workload, seed, seconds, queue):
+    """CPU baseline of a batched workload: the FP64 oracle (direct method,
+    one thread) solving programs of a stratified sample for about `seconds`."""
+    try:
+        progs, _ = batch_programs(workload, seed)
+        from oracle import admm
+        order = sorted(range(len(progs)), key=lambda i: progs[i].n)
+        pick = order[::max(1, len(order) // 64)]
+        t0 = time.perf_counter()
+        done = 0
+        for i in pick:
+            P = progs[i]
+            admm.solve(P.A, P.b, P.c, P.cone, admm.Settings())
+            done += 1
+            if time.perf_counter() - t0 >= seconds:
+                break
+        queue.put({"programs": done, "seconds": time.perf_counter() - t0, "of": len(pick)})
+    except Exception as e:
+        queue.put({"error": repr(e)})
+
+
+def run_batch(args):
+    """Batched workload: every program solved to the 1e-4 tests by one
+    persistent launch (a CUDA graph) per step; the plain solver (scs_init +
+    scs_solve per program) on a stratified sample gives the looped time."""
+    world, rank, local = dist_env()
+    cpu_proc = cpu_q = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        cpu_q = ctx.Queue()
+        cpu_proc = ctx.Process(target=cpu_batch_job, args=(args.workload, args.seed, args.cpu_seconds, cpu_q),
+                               daemon=True)
+        cpu_proc.start()
+    import numpy as np
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_1312_3039_gb300 import scs
+    progs, desc = batch_programs(args.workload, args.seed)
+    count = len(progs)
+    tuples = [(P.A, P.b, P.c, P.cone) for P in progs]
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    common = dict(precision=1, device=local, cuda_stream=stream.cuda_stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def reduce(x, op):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=op)
+        return float(t.item())
+
+    # end to end: host CSC -> scs_batch_init (setup launch + autotuner) ->
+    # scs_batch_solve -> x, y, s and infos on the host
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    bt = scs.Batch(tuples, **common)
+    init_s = time.perf_counter() - t0
+    xs, ys, ss, infos = bt.solve()
+    torch.cuda.synchronize()
+    e2e_s = reduce(time.perf_counter() - t0, torch.distributed.ReduceOp.MAX if world > 1 else None)
+    cfg = bt.config()
+    for _ in range(max(0, args.warmup - 1)):
+        bt.solve()
+    # timed: `steps` cold batched solves (graph launch .. last program done)
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    dev_ms = 0.0
+    for _ in range(args.steps):
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        xs, ys, ss, infos = bt.solve()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dev_ms += e0.elapsed_time(e1)
+    clk = clocks.stop()
+    bt.close()
+    ms = reduce(dev_ms, torch.distributed.ReduceOp.MAX if world > 1 else None)
+    total = reduce(float(count * args.steps), torch.distributed.ReduceOp.SUM if world > 1 else None)
+    value = total / (ms / 1e3)
+    st = np.array([f["status"] for f in infos])
+    iters = np.array([f["iters"] for f in infos])
+    cg = np.array([f["cg_iters"] for f in infos])
+    # plain solver, one program at a time, on a stratified sample
+    order = sorted(range(count), key=lambda i: progs[i].n)
+    pick = order[::max(1, count // args.plain_sample)]
+    plain_s = 0.0
+    plain_status = []
+    for i in pick:
+        P = progs[i]
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        r = scs.solve(P.A, P.b, P.c, P.cone, **common)
+        torch.cuda.synchronize()
+        plain_s += time.perf_counter() - t1
+        plain_status.append(int(r[0] == infos[i]["status"] and r[4]["iters"] == infos[i]["iters"]))
+    plain_total = plain_s / len(pick) * count
+    # algorithmic bytes of the products: per program (2 + 2 CG) SpMVs per
+    # iteration, each streaming A^'s CSR (8 B per nonzero + 4 B per row) and
+    # gathering its input once
+    byt = 0.0
+    for i, P in enumerate(progs):
+        per = 8.0 * P.A.nnz + 4.0 * (P.m + P.n) + 4.0 * (P.n + P.m)
+        byt += per * (2 * iters[i] + 2 * cg[i]) / 2.0
+    peak, peak_src = measured_hbm_peak()
+    achieved = byt * args.steps / (ms / 1e3) / 1e9
+    cpu = None
+    if cpu_proc is not None:
+        try:
+            r = cpu_q.get(timeout=900)
+        except Exception as e:
+            r = {"error": "no result: " + repr(e)}
+        cpu_proc.join(timeout=10)
+        if "error" in r:
+            cpu = {"value": None, "unit": "programs/s", "cores": 1, "kind": "oracle", "sample": r["error"]}
+        else:
+            cpu = {"value": r["programs"] / r["seconds"], "unit": "programs/s", "cores": 1, "kind": "oracle",
+                   "sample": f"{r['programs']} of a stratified sample of {r['of']} programs solved to 1e-4 by the "
+                             f"FP64 oracle (direct method, one thread) in {r['seconds']:.1f} s"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "programs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (Sec. 6.3 portfolio form, seed %d)" % args.seed,
+            "config": {"workload": desc, "precision": "fp32 A/CG/iterates, fp64 scaling and tests",
+                       "step": "one batched solve of every program to the 1e-4 tests (cold start)",
+                       "l2": "each program's A stays in L1/L2 while its CTA solves it (<= 200 KB)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "autotuned": cfg},
+            "batched": {"programs": count, "solve_s": ms / args.steps / 1e3, "status_counts":
+                        {str(k): int(v) for k, v in zip(*np.unique(st, return_counts=True))},
+                        "iters_mean": float(iters.mean()), "iters_max": int(iters.max()),
+                        "cg_per_iter": float(cg.sum() / max(iters.sum(), 1)),
+                        "plain_looped_s_est": plain_total, "plain_sample": len(pick),
+                        "plain_sample_same_status_and_iters": sum(plain_status),
+                        "speedup_vs_plain": plain_total / (ms / args.steps / 1e3),
+                        "init_s": init_s},
+            "roofline": {"bound": "hbm", "kernel": "batch solve_kernel (all products of all programs)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_source": peak_src, "traffic": None,
+                         "note": "operands L2/L1-resident while a team works on them: HBM peak as denominator"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": count / e2e_s, "unit": "programs/s", "seconds": e2e_s,
+                    "h2d_bytes_per_step": float(sum(12 * P.A.nnz + 8 * (P.n + 1) + 8 * (P.m + P.n) for P in progs)),
+                    "d2h_bytes_per_step": float(sum(8 * (P.n + 2 * P.m) for P in progs) + 120 * count),
+                    "includes": "scs_batch_init (host CSC->CSR, H2D, setup launch, autotuner) + scs_batch_solve + "
+                                "D2H of x, y, s, info"},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload.startswith("portfolio_batch"):
+        return run_batch(args)
     return run_gb300(args)
 
 

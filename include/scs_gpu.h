@@ -228,6 +228,51 @@ int32_t scs_project(const scs_cone *k, int32_t dual, const double *v, double *ou
 int32_t scs_project_noalloc(const scs_cone *k, int32_t dual, const double *v, double *out, int64_t count,
                             double *dist2, void *stream);
 
+/* ---- batched persistent solver ----------------------------------------------
+ * Many independent small programs solved together: the same iteration as
+ * scs_solve (Eq. "e-SCS", indirect subspace step Sec. 4.1, equilibration
+ * Sec. 5, tests Sec. 3.5), one CTA per program at a time inside one
+ * persistent launch captured in a CUDA graph, the program's iterates and CG
+ * vectors in shared memory.  Extends the paper's repeated-solve setting
+ * (Sec. 4.2) to many programs at once; the paper has no batched form.
+ * Cones: zero, nonnegative and second-order only (SCS_UNSUPPORTED
+ * otherwise); a program must fit one CTA's shared memory (about 4 (2 N + 6 n
+ * + 4 m) bytes in FP32, N = n + m + 1).  No time limit. */
+typedef struct scs_batch scs_batch;
+
+/* count programs: A[i] (CSC, host), b and c concatenated in program order
+ * (sum of m_i, sum of n_i doubles), cones k[i]; settings as for scs_init
+ * (precision 0: FP64, 1: FP32 iterates with FP64 tests).  Runs the setup
+ * launch (equilibration, Jacobi diagonal, p = M^-1 h per program) and the
+ * autotuner (team size and long-row split timed on a sample of programs).
+ * Returns NULL with *err set on failure. */
+scs_batch *scs_batch_init(int32_t count, const scs_csc *A, const double *b, const double *c, const scs_cone *k,
+                          const scs_settings *st, int32_t *err);
+
+/* Solve every program from a cold start, or from the points of
+ * scs_batch_warm_start.  x (sum n_i), y, s (sum m_i) in program order receive
+ * each solution or certificate as scs_solve does; info[count] the per-program
+ * status and counters (setup_s / solve_s are the batch's).  Any pointer may be
+ * NULL.  Returns 0, or an error status for the whole call. */
+int32_t scs_batch_solve(scs_batch *w, double *x, double *y, double *s, scs_info *info);
+
+/* Sec. 4.2 warm start of every program (concatenated host arrays; NULL
+ * entries are zero); used by the next scs_batch_solve only. */
+int32_t scs_batch_warm_start(scs_batch *w, const double *x, const double *y, const double *s);
+
+/* Exactly `iters` iterations of every program from its current iterates,
+ * without termination tests (parity tests, timing). */
+int32_t scs_batch_iterate(scs_batch *w, int32_t iters);
+
+/* Scaled iterates u, v (n_i + m_i + 1 doubles each, host) of program index. */
+int32_t scs_batch_get_iterates(scs_batch *w, int32_t index, double *u, double *v);
+
+/* What the autotuner chose (threads per program, rows longer than row_split
+ * nonzeros summed by a warp) and the time it and the setup took (ms). */
+int32_t scs_batch_config(scs_batch *w, int32_t *threads, int32_t *row_split, double *tune_ms, double *setup_ms);
+
+void scs_batch_finish(scs_batch *w);
+
 /* Human-readable description of the most recent error on this thread. */
 const char *scs_last_error(void);
 

@@ -26,8 +26,12 @@ thread_local std::string g_last_error;
 
 void set_error(const std::string &s) { g_last_error = s; }
 
-int validate_and_build(const scs_csc *A, const double *b, const double *c, const scs_cone *k,
-                       scs::HostProblem &P) {
+}  // namespace
+
+void scs::set_last_error(const std::string &s) { set_error(s); }
+
+int scs::validate_and_build(const scs_csc *A, const double *b, const double *c, const scs_cone *k,
+                            scs::HostProblem &P) {
     if (!A || !b || !c || !k) { set_error("null argument"); return SCS_INVALID_INPUT; }
     if (A->m <= 0 || A->n <= 0) { set_error("m and n must be positive"); return SCS_INVALID_INPUT; }
     if (!A->colptr || (!A->rowidx && A->colptr[A->n] > 0) || (!A->val && A->colptr[A->n] > 0)) {
@@ -133,6 +137,8 @@ int validate_and_build(const scs_csc *A, const double *b, const double *c, const
     P.s.assign(k->s, k->s + k->ns);
     return 0;
 }
+
+namespace {
 
 int validate_settings(const scs_settings &s) {
     if (!(s.alpha > 0.0 && s.alpha < 2.0)) { set_error("alpha must lie in (0, 2)"); return SCS_INVALID_INPUT; }

@@ -33,6 +33,12 @@ struct HostProblem {
     std::vector<int32_t> q, s;
 };
 
+// Validate A (CSC), b, c and the cone and build the host CSR layouts
+// (api.cu); returns 0 or an SCS_* status after setting the error text.
+int validate_and_build(const scs_csc *A, const double *b, const double *c, const scs_cone *k, HostProblem &P);
+// Error text returned by scs_last_error() on this thread.
+void set_last_error(const std::string &s);
+
 class EngineBase {
    public:
     virtual ~EngineBase() {}

@@ -106,6 +106,21 @@ def lib():
             L.scs_project_noalloc.argtypes = [C.POINTER(ConeC), I32, C.c_void_p, C.c_void_p, C.c_int64, D,
                                               C.c_void_p]
             L.scs_project_noalloc.restype = I32
+        L.scs_batch_init.argtypes = [I32, C.POINTER(CSC), D, D, C.POINTER(ConeC), C.POINTER(Settings),
+                                     C.POINTER(I32)]
+        L.scs_batch_init.restype = P
+        L.scs_batch_solve.argtypes = [P, D, D, D, C.POINTER(Info)]
+        L.scs_batch_solve.restype = I32
+        L.scs_batch_warm_start.argtypes = [P, D, D, D]
+        L.scs_batch_warm_start.restype = I32
+        L.scs_batch_iterate.argtypes = [P, I32]
+        L.scs_batch_iterate.restype = I32
+        L.scs_batch_get_iterates.argtypes = [P, I32, D, D]
+        L.scs_batch_get_iterates.restype = I32
+        L.scs_batch_config.argtypes = [P, C.POINTER(I32), C.POINTER(I32), D, D]
+        L.scs_batch_config.restype = I32
+        L.scs_batch_finish.argtypes = [P]
+        L.scs_batch_finish.restype = None
         L.scs_last_error.argtypes = []
         L.scs_last_error.restype = C.c_char_p
         _lib_handle = L
@@ -289,3 +304,103 @@ def solve(A, b, c, cone, **kw):
     """One-shot solve; returns ``(status, x, y, s, info)``."""
     with Solver(A, b, c, cone, **kw) as S:
         return S.solve()
+
+
+class Batch:
+    """Many independent programs solved by one persistent launch
+    (``scs_batch_init`` / ``scs_batch_solve``); ``problems`` is a list of
+    ``(A, b, c, cone)``."""
+
+    def __init__(self, problems, settings: Settings | None = None, **kw):
+        import scipy.sparse as sp
+        self.count = len(problems)
+        self._keep = []
+        cscs = (CSC * self.count)()
+        cones = (ConeC * self.count)()
+        self.ns, self.ms = [], []
+        bs, cs = [], []
+        for i, (A, b, c, cone) in enumerate(problems):
+            A = sp.csc_matrix(A)
+            m, n = A.shape
+            cp = np.ascontiguousarray(A.indptr, dtype=np.int64)
+            ri = np.ascontiguousarray(A.indices, dtype=np.int32)
+            va = np.ascontiguousarray(A.data, dtype=np.float64)
+            q = np.ascontiguousarray(list(getattr(cone, "q", ())) or [0], dtype=np.int32)
+            sd = np.ascontiguousarray(list(getattr(cone, "s", ())) or [0], dtype=np.int32)
+            self._keep += [cp, ri, va, q, sd]
+            cscs[i] = CSC(m, n, cp.ctypes.data_as(C.POINTER(C.c_int64)), ri.ctypes.data_as(C.POINTER(C.c_int32)),
+                          va.ctypes.data_as(C.POINTER(C.c_double)))
+            cones[i] = ConeC(int(cone.z), int(cone.l), q.ctypes.data_as(C.POINTER(C.c_int32)),
+                             len(getattr(cone, "q", ())), sd.ctypes.data_as(C.POINTER(C.c_int32)),
+                             len(getattr(cone, "s", ())), int(cone.ep))
+            self.ns.append(n)
+            self.ms.append(m)
+            bs.append(np.asarray(b, dtype=np.float64))
+            cs.append(np.asarray(c, dtype=np.float64))
+        self._b = np.ascontiguousarray(np.concatenate(bs))
+        self._c = np.ascontiguousarray(np.concatenate(cs))
+        self.xoff = np.concatenate([[0], np.cumsum(self.ns)]).astype(np.int64)
+        self.yoff = np.concatenate([[0], np.cumsum(self.ms)]).astype(np.int64)
+        st = settings if settings is not None else default_settings()
+        for k, v in kw.items():
+            setattr(st, k, v)
+        self.settings = st
+        err = C.c_int32(0)
+        self._w = lib().scs_batch_init(self.count, cscs, _dptr(self._b), _dptr(self._c), cones, C.byref(st),
+                                       C.byref(err))
+        if not self._w:
+            raise ScsError(err.value, last_error())
+
+    def _check(self, rc):
+        if rc != 0:
+            raise ScsError(rc, last_error())
+        return rc
+
+    def solve(self):
+        """Return ``(xs, ys, ss, infos)``: per-program arrays and info dicts."""
+        x = np.empty(int(self.xoff[-1]))
+        y = np.empty(int(self.yoff[-1]))
+        s = np.empty(int(self.yoff[-1]))
+        info = (Info * self.count)()
+        self._check(lib().scs_batch_solve(self._w, _dptr(x), _dptr(y), _dptr(s), info))
+        xs = [x[self.xoff[i]:self.xoff[i + 1]] for i in range(self.count)]
+        ys = [y[self.yoff[i]:self.yoff[i + 1]] for i in range(self.count)]
+        ss = [s[self.yoff[i]:self.yoff[i + 1]] for i in range(self.count)]
+        return xs, ys, ss, [info[i].as_dict() for i in range(self.count)]
+
+    def warm_start(self, xs=None, ys=None, ss=None):
+        cat = lambda parts: None if parts is None else np.ascontiguousarray(np.concatenate(parts), dtype=np.float64)
+        x, y, s = cat(xs), cat(ys), cat(ss)
+        return self._check(lib().scs_batch_warm_start(self._w, _dptr(x), _dptr(y), _dptr(s)))
+
+    def iterate(self, iters):
+        return self._check(lib().scs_batch_iterate(self._w, int(iters)))
+
+    def iterates(self, index):
+        N = self.ns[index] + self.ms[index] + 1
+        u, v = np.empty(N), np.empty(N)
+        self._check(lib().scs_batch_get_iterates(self._w, int(index), _dptr(u), _dptr(v)))
+        return u, v
+
+    def config(self):
+        t, sp_ = C.c_int32(0), C.c_int32(0)
+        tm, sm = C.c_double(0), C.c_double(0)
+        self._check(lib().scs_batch_config(self._w, C.byref(t), C.byref(sp_), C.byref(tm), C.byref(sm)))
+        return {"threads": t.value, "row_split": sp_.value, "tune_ms": tm.value, "setup_ms": sm.value}
+
+    def close(self):
+        if getattr(self, "_w", None):
+            lib().scs_batch_finish(self._w)
+            self._w = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
