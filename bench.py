@@ -40,8 +40,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--workload", choices=["mixed", "mixed_small", "sdp", "sdp_small", "sdp_blocks", "lp",
-                                           "portfolio_batch", "portfolio_batch_small"],
+                                           "portfolio_batch", "portfolio_batch_small", "lasso_warm",
+                                           "lasso_warm_small"],
                     default="mixed")
+    ap.add_argument("--train", type=int, default=None, help="training members of a lasso_warm workload")
+    ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--plain-sample", type=int, default=64,
                     help="programs of a batched workload solved one by one by the plain solver")
     ap.add_argument("--seed", type=int, default=0)
@@ -640,12 +643,109 @@ def run_batch(args):
     return 0
 
 
+LASSO_DESC = ("parametric lasso family (Sec. 6.2 SOCP form): F 1000x400 N(0,1)/sqrt(1000), theta in R^64, "
+              "g = G theta, mu = mu0 (1 + tanh(a.theta/8)/2); n=801 m=1802; network 64-512-512-512-4406 GELU, "
+              "BF16; {train} training solves, {held} held-out members")
+
+
+def run_lasso_warm(args):
+    """Learned warm start: the family solver generates the training states,
+    the network trains on them, and held-out members are solved cold and
+    warm-started (inference, projection and warm start inside the timed
+    warm solve); the plain solver (scs_solve per member) cold and warm on a
+    sample of the held-out members."""
+    world, rank, local = dist_env()
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1312_3039_gb300 import scs, synth
+    from paper_1312_3039_gb300.warmstart import LearnedWarmStart
+    small = args.workload == "lasso_warm_small"
+    ntrain = args.train or (4096 if small else 100000)
+    nheld = 1024 if small else 10000
+    fam = synth.lasso_family(args.seed)
+    ws = LearnedWarmStart(fam, scs, torch, batch=1024, seed=args.seed)
+    th_tr = fam.thetas(args.seed + 100, ntrain)
+    th_te = fam.thetas(args.seed + 200, nheld)
+    t0 = time.perf_counter()
+    infos_tr, gen_s, states = ws.solve_family(th_tr)
+    gen_wall = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    hist = ws.fit(th_tr, states, epochs=args.epochs, lr=1e-3)
+    torch.cuda.synchronize()
+    fit_s = time.perf_counter() - t1
+    steps = args.epochs * (ntrain // ws.batch)
+    flop_step = 6.0 * ws.batch * sum(a * b for a, b in zip(ws.sizes[:-1], ws.sizes[1:]))
+    del states
+    # held-out: warm-up solve, then `steps` timed cold and warm solves
+    clocks = ClockSampler(local)
+    ws.solve_family(th_te[:1024])
+    clocks.start()
+    cold_s, warm_s = 0.0, 0.0
+    for _ in range(args.steps):
+        cold, cs, _ = ws.solve_family(th_te)
+        warm, wsec, _ = ws.solve_family(th_te, warm=ws.predict_warm)
+        cold_s += cs
+        warm_s += wsec
+    clk = clocks.stop()
+    ci = np.array([f["iters"] for f in cold])
+    wi = np.array([f["iters"] for f in warm])
+    # plain solver (scs_solve per member, indirect CG), cold and warm-started
+    # from the network's prediction mapped to the caller's units
+    pick = list(range(0, nheld, max(1, nheld // args.plain_sample)))
+    xh, yh, sh = ws.predict_warm(th_te[pick])
+    xh, yh, sh = xh.cpu().numpy(), yh.cpu().numpy(), sh.cpu().numpy()
+    pc_s = pw_s = 0.0
+    pci, pwi = [], []
+    for k, i in enumerate(pick):
+        P = fam.problem(th_te[i])
+        with scs.Solver(P.A, P.b, P.c, P.cone, precision=1) as S:
+            D, E, sg, rh = S.scaling()
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            st, *_r, info = S.solve()
+            pc_s += time.perf_counter() - a
+            pci.append(info["iters"])
+            a = time.perf_counter()
+            S.warm_start(E * xh[k] / sg, D * yh[k] / rh, sh[k] / (sg * D))
+            st2, *_r2, info2 = S.solve()
+            pw_s += time.perf_counter() - a
+            pwi.append(info2["iters"])
+    ws.close()
+    line = {
+        "metric": METRIC, "value": args.steps * nheld / warm_s, "unit": "held-out members/s (warm-started)",
+        "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": 1e3 * warm_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 solve, bf16 network",
+        "data": "synthetic (Sec. 6.2 lasso form, seed %d)" % args.seed,
+        "config": {"workload": LASSO_DESC.format(train=ntrain, held=nheld),
+                   "step": "one family solve of every held-out member to the 1e-4 tests"},
+        "warm_vs_cold": {"cold_s": cold_s / args.steps, "warm_s": warm_s / args.steps,
+                         "time_ratio": warm_s / cold_s, "iters_cold_mean": float(ci.mean()),
+                         "iters_warm_mean": float(wi.mean()), "iters_cold_median": float(np.median(ci)),
+                         "iters_warm_median": float(np.median(wi)),
+                         "warm_solved": float(np.mean([f["status"] == 1 for f in warm]))},
+        "plain_solver_sample": {"members": len(pick), "cold_s": pc_s, "warm_s": pw_s,
+                                "iters_cold_mean": float(np.mean(pci)), "iters_warm_mean": float(np.mean(pwi)),
+                                "family_cold_s_same_members": cold_s / args.steps * len(pick) / nheld,
+                                "family_warm_s_same_members": warm_s / args.steps * len(pick) / nheld},
+        "training": {"members": ntrain, "generation_s": gen_s, "generation_wall_s": gen_wall, "fit_s": fit_s,
+                     "epochs": args.epochs, "steps": steps, "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
+                     "train_tflops": flop_step * steps / fit_s / 1e12},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload.startswith("portfolio_batch"):
         return run_batch(args)
+    if args.workload.startswith("lasso_warm"):
+        return run_lasso_warm(args)
     return run_gb300(args)
 
 

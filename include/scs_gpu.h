@@ -273,6 +273,97 @@ int32_t scs_batch_config(scs_batch *w, int32_t *threads, int32_t *row_split, dou
 
 void scs_batch_finish(scs_batch *w);
 
+/* ---- family solver: members sharing A and the cone -------------------------
+ * Many programs with the same A and cone and their own b, c (the setting of
+ * Sec. 4.2 where only b and c change between solves).  The equilibration
+ * D, E (Sec. 5) depends on A only and is shared; sigma, rho are per member.
+ * The subspace step uses the dense (I + A^T A)^-1, formed once in FP64 on the
+ * device, so one iteration of all members is three dense products over the
+ * member columns (FP32 or FP64 GEMMs) plus one fused update launch; the
+ * Sec. 3.5 tests run every check_interval iterations.  Cones: zero,
+ * nonnegative, SOC; dense A^ must have at most 2^31 entries.  The paper has
+ * no batched family form; each member follows the paper's iteration with an
+ * exact subspace solve. */
+typedef struct scs_family scs_family;
+
+/* A (CSC, host, shared), cone, count members; b: count x m, c: count x n
+ * (host, member-major).  Returns NULL with *err set on failure. */
+scs_family *scs_family_init(const scs_csc *A, const scs_cone *k, int32_t count, const double *b, const double *c,
+                            const scs_settings *st, int32_t *err);
+
+/* New b, c for every member (same layout); the shared inverse is kept. */
+int32_t scs_family_set_data(scs_family *w, const double *b, const double *c);
+
+/* Warm start of every member for the next solve, u0 = (x^, y^, 1),
+ * v0 = (0, s^, 0) (Sec. 4.2).  device_scaled = 0: host arrays in the
+ * caller's units (count x n, m, m); 1: device FP64 arrays already in each
+ * member's scaled space.  NULL arrays are zero. */
+int32_t scs_family_warm_start(scs_family *w, const double *x, const double *y, const double *s,
+                              int32_t device_scaled);
+
+/* Iterate every member until each has passed a test (or max_iters); x, y, s
+ * (count x n, m, m) receive each member's solution or certificate as
+ * scs_solve gives it, in host memory (device_out = 0) or device memory (1);
+ * info[count] (host) the status and iteration count at which each member
+ * stopped.  Any pointer may be NULL. */
+int32_t scs_family_solve(scs_family *w, double *x, double *y, double *s, scs_info *info, int32_t device_out);
+
+/* Exactly `iters` iterations of every member, no tests (parity tests). */
+int32_t scs_family_iterate(scs_family *w, int32_t iters);
+
+/* Scaled iterates u, v (n + m + 1 each, host) of one member. */
+int32_t scs_family_get_iterates(scs_family *w, int32_t index, double *u, double *v);
+
+/* Each member's scaled HSD state when it stopped, divided by its u_tau
+ * (so (x^, y^, s^, 1) for a solved member), as float, count x (n + 2m + 1),
+ * copied to dst (host or device). */
+int32_t scs_family_snapshots(scs_family *w, float *dst);
+
+int32_t scs_family_dims(scs_family *w, int32_t *n, int32_t *m, int32_t *count);
+void scs_family_finish(scs_family *w);
+
+/* ---- learned warm start --------------------------------------------------
+ * A multilayer perceptron (d_in -> hidden x layers (GELU) -> d_out) that maps a
+ * family member's parameter theta to its predicted scaled state
+ * (u_x, u_y, v_s, u_tau); trained by MSE with Adam; BF16 tensor-core
+ * products with FP32 accumulation and FP32 master weights.  The paper has no
+ * learned component: this extends the warm start of Sec. 4.2.  All device
+ * pointers; calls run on the network's stream (NULL: a private one). */
+typedef struct scs_mlp scs_mlp;
+
+/* batch: rows of every forward / training call, a positive multiple of 128. */
+scs_mlp *scs_mlp_create(int32_t d_in, int32_t hidden, int32_t layers, int32_t d_out, int32_t batch, void *stream,
+                        int32_t *err);
+int64_t scs_mlp_param_count(scs_mlp *w);
+/* Host FP32 parameters, per layer W (out x in, row-major) then b (out);
+ * setting them also clears the optimiser state. */
+int32_t scs_mlp_set_params(scs_mlp *w, const float *params);
+int32_t scs_mlp_get_params(scs_mlp *w, float *params);
+/* y (batch x d_out, FP32, device or host) = network(x) for x (batch x d_in,
+ * FP32, device); synchronises. */
+int32_t scs_mlp_forward(scs_mlp *w, const float *x, float *y);
+/* Loss and gradients (host, packed like the parameters) for targets t
+ * (batch x d_out, FP32, device); grads or loss may be NULL. */
+int32_t scs_mlp_gradients(scs_mlp *w, const float *x, const float *t, float *grads, float *loss);
+/* One Adam step (learning rate lr) on a batch; *loss (host) if not NULL
+ * (then the call synchronises). */
+int32_t scs_mlp_train_step(scs_mlp *w, const float *x, const float *t, float lr, float *loss);
+void scs_mlp_destroy(scs_mlp *w);
+
+/* Device helpers of the warm-start pipeline (FP32 row-major data):
+ * per-column mean and standard deviation; in-place standardisation
+ * (d - mean) / sd; row gather dst[r] = src[idx[r]]. */
+int32_t scs_column_stats(const float *data, int64_t rows, int32_t cols, float *mean, float *sd, void *stream);
+int32_t scs_standardize(float *data, int64_t rows, int32_t cols, const float *mean, const float *sd, void *stream);
+int32_t scs_gather_rows(const float *src, int32_t cols, const int64_t *idx, int64_t count, float *dst, void *stream);
+/* A standardised prediction (count rows of ld >= n + 2m + 1 floats: u_x, u_y,
+ * v_s, u_tau) to the scaled warm start x^ = u_x / tau, y^ = u_y / tau,
+ * s^ = v_s / tau with tau = max(u_tau, tau_min) (FP64 device arrays count x n,
+ * m, m); project y^ onto K* and s^ onto K afterwards (scs_project). */
+int32_t scs_warm_from_prediction(const float *pred, int64_t ld, const float *mean, const float *sd, int32_t n,
+                                 int32_t m, int64_t count, double tau_min, double *xh, double *yh, double *sh,
+                                 void *stream);
+
 /* Human-readable description of the most recent error on this thread. */
 const char *scs_last_error(void);
 

@@ -1,0 +1,672 @@
+// Warm-start network: a multilayer perceptron theta -> predicted scaled
+// solution state (u_x, u_y, v_s, u_tau) of a family member, trained and run
+// by the kernels of this file (the paper has no learned component; it
+// extends Sec. 4.2's warm start).
+//
+// Layers d_in -> h -> ... -> h -> d_out, GELU after every hidden layer
+// (GELU(z) = z Phi(z)), linear output; loss = mean squared error over the
+// outputs of a batch; Adam on FP32 master weights.  Products run on the
+// tensor cores in BF16 with FP32 accumulation: one GEMM kernel of the form
+// C[M x N] = A[M x K] B[N x K]^T (both operands K-contiguous), used as
+//   forward   Z   = X W^T + b          (A = X,   B = W)
+//   backward  dX  = dZ W               (A = dZ,  B = W^T)
+//   backward  dW  = dZ^T X             (A = dZ^T, B = X^T)
+// with fused epilogues (bias + GELU with the pre-activation kept; bias; plain).
+// Shapes are padded so that every launch meets the kernel's tiling exactly
+// (M % 128, N % 64, K % 32, rows 16-byte aligned); padding rows and columns
+// of the weights are zero and stay zero (their gradients are zero).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/scs_gpu.h"
+#include "common.cuh"
+#include "engine_base.h"
+
+namespace scs {
+namespace mlp {
+
+constexpr int BM = 128, BN = 64, BK = 32, kGemmThreads = 128;
+constexpr int kLds = BK + 8;   // shared-memory row stride (bf16): 80 bytes, conflict-free ldmatrix
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+__device__ __forceinline__ void ldmatrix_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// epilogues: called with (row, col, value at col, value at col + 1)
+struct EpiHidden {   // Z = acc + b (FP32); A = GELU(Z) (BF16)
+    float *Z;
+    __nv_bfloat16 *A;
+    const float *bias;
+    int ldz, lda;
+    __device__ void operator()(int r, int c, float v0, float v1) const {
+        const float z0 = v0 + bias[c], z1 = v1 + bias[c + 1];
+        *reinterpret_cast<float2 *>(Z + (size_t)r * ldz + c) = make_float2(z0, z1);
+        *reinterpret_cast<__nv_bfloat162 *>(A + (size_t)r * lda + c) = __floats2bfloat162_rn(gelu(z0), gelu(z1));
+    }
+};
+struct EpiBias {     // Z = acc + b (FP32)
+    float *Z;
+    const float *bias;
+    int ldz;
+    __device__ void operator()(int r, int c, float v0, float v1) const {
+        *reinterpret_cast<float2 *>(Z + (size_t)r * ldz + c) = make_float2(v0 + bias[c], v1 + bias[c + 1]);
+    }
+};
+struct EpiPlain {    // C = acc (FP32)
+    float *C;
+    int ldc;
+    __device__ void operator()(int r, int c, float v0, float v1) const {
+        *reinterpret_cast<float2 *>(C + (size_t)r * ldc + c) = make_float2(v0, v1);
+    }
+};
+
+// C[M x N] = A[M x K] B[N x K]^T; grid (N / BN, M / BM); 4 warps, each a
+// 64 x 32 tile of m16n8k16 products; two-stage cp.async pipeline over K.
+template <typename Epi>
+__global__ void __launch_bounds__(kGemmThreads) gemm_nt_kernel(const __nv_bfloat16 *__restrict__ A, int lda,
+                                                               const __nv_bfloat16 *__restrict__ B, int ldb, int K,
+                                                               Epi epi) {
+    __shared__ __align__(16) __nv_bfloat16 sA[2][BM * kLds];
+    __shared__ __align__(16) __nv_bfloat16 sB[2][BN * kLds];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp >> 1, wn = warp & 1;
+    const int bm = blockIdx.y * BM, bn = blockIdx.x * BN;
+    const __nv_bfloat16 *Ab = A + (size_t)bm * lda, *Bb = B + (size_t)bn * ldb;
+    auto load = [&](int stage, int k0) {
+        // A: 128 rows x 4 chunks of 8 bf16; B: 64 rows x 4 chunks
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int ch = tid + i * kGemmThreads, r = ch >> 2, c = (ch & 3) * 8;
+            cp_async16(&sA[stage][r * kLds + c], Ab + (size_t)r * lda + k0 + c);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int ch = tid + i * kGemmThreads, r = ch >> 2, c = (ch & 3) * 8;
+            cp_async16(&sB[stage][r * kLds + c], Bb + (size_t)r * ldb + k0 + c);
+        }
+    };
+    float acc[4][4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+    const int KT = K / BK;
+    load(0, 0);
+    cp_commit();
+    for (int kt = 0; kt < KT; ++kt) {
+        if (kt + 1 < KT) {
+            load((kt + 1) & 1, (kt + 1) * BK);
+            cp_commit();
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
+        }
+        __syncthreads();
+        const __nv_bfloat16 *a_s = sA[kt & 1], *b_s = sB[kt & 1];
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            uint32_t af[4][4], bf[2][4];
+#pragma unroll
+            for (int mi = 0; mi < 4; ++mi) {
+                const int r = wm * 64 + mi * 16 + (lane & 15), c = kk + (lane >> 4) * 8;
+                ldmatrix_x4(af[mi][0], af[mi][1], af[mi][2], af[mi][3], a_s + r * kLds + c);
+            }
+#pragma unroll
+            for (int nj = 0; nj < 2; ++nj) {
+                const int r = wn * 32 + nj * 16 + (lane & 7) + ((lane >> 4) << 3), c = kk + ((lane >> 3) & 1) * 8;
+                ldmatrix_x4(bf[nj][0], bf[nj][1], bf[nj][2], bf[nj][3], b_s + r * kLds + c);
+            }
+#pragma unroll
+            for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni)
+                    mma_bf16(acc[mi][ni], af[mi], bf[ni >> 1][(ni & 1) * 2], bf[ni >> 1][(ni & 1) * 2 + 1]);
+        }
+        __syncthreads();
+    }
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) {
+            const int r = bm + wm * 64 + mi * 16 + g, c = bn + wn * 32 + ni * 8 + 2 * t;
+            epi(r, c, acc[mi][ni][0], acc[mi][ni][1]);
+            epi(r + 8, c, acc[mi][ni][2], acc[mi][ni][3]);
+        }
+}
+
+// dst[c][r] = src[r][c] for r < rows, c < cols (BF16; 32 x 32 tiles)
+static __global__ void transpose_kernel(const __nv_bfloat16 *__restrict__ src, int lds, __nv_bfloat16 *__restrict__ dst,
+                                        int ldd, int rows, int cols) {
+    __shared__ __nv_bfloat16 tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        tile[i][threadIdx.x] = (r < rows && c < cols) ? src[(size_t)r * lds + c] : __float2bfloat16(0.f);
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (c < cols && r < rows) dst[(size_t)c * ldd + r] = tile[threadIdx.x][i];
+    }
+}
+
+// X (rows x cols FP32, ld cols) -> BF16 (ld ldd, zero columns up to ldd)
+static __global__ void to_bf16_kernel(const float *__restrict__ x, int rows, int cols, __nv_bfloat16 *__restrict__ y,
+                                      int ldd) {
+    const int64_t total = (int64_t)rows * ldd;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = static_cast<int>(e / ldd), c = static_cast<int>(e % ldd);
+        y[e] = __float2bfloat16(c < cols ? x[(size_t)r * cols + c] : 0.f);
+    }
+}
+
+// output layer: dZ = 2 (Y - T) / (rows dout) on the first dout columns, 0 on
+// the padding; FP32 (bias gradient) and BF16 copies; per-CTA loss partials
+static __global__ void loss_grad_kernel(const float *__restrict__ Y, int ldy, const float *__restrict__ T, int dout,
+                                        int rows, float *__restrict__ dz32, __nv_bfloat16 *__restrict__ dz16,
+                                        double *__restrict__ part) {
+    __shared__ double red[8];
+    const double scale = 2.0 / ((double)rows * dout);
+    double acc = 0.0;
+    const int64_t total = (int64_t)rows * ldy;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = static_cast<int>(e / ldy), c = static_cast<int>(e % ldy);
+        float g = 0.f;
+        if (c < dout) {
+            const float d = Y[e] - T[(size_t)r * dout + c];
+            acc += (double)d * d;
+            g = static_cast<float>(scale * d);
+        }
+        dz32[e] = g;
+        dz16[e] = __float2bfloat16(g);
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        part[blockIdx.x] = s;
+    }
+}
+
+static __global__ void sum_parts_kernel(const double *__restrict__ part, int n, double scale, double *out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += part[i];
+        *out = s * scale;
+    }
+}
+
+// hidden layer: dZ = dA * GELU'(Z) (FP32 and BF16)
+static __global__ void gelu_back_kernel(const float *__restrict__ dA, const float *__restrict__ Z, int64_t len,
+                                        float *__restrict__ dz32, __nv_bfloat16 *__restrict__ dz16) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+        const float g = dA[e] * gelu_grad(Z[e]);
+        dz32[e] = g;
+        dz16[e] = __float2bfloat16(g);
+    }
+}
+
+// db[c] = sum over rows of dZ[r][c] (one thread per column, rows in order)
+static __global__ void colsum_kernel(const float *__restrict__ dz, int rows, int cols, float *__restrict__ db) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    float s = 0.f;
+    for (int r = 0; r < rows; ++r) s += dz[(size_t)r * cols + c];
+    db[c] = s;
+}
+
+// Adam (bias-corrected) on FP32 master values
+static __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                                   float *__restrict__ v, int64_t len, float lr, float b1, float b2, float eps,
+                                   float c1, float c2) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+        const float gg = g[e];
+        const float mm = b1 * m[e] + (1.f - b1) * gg;
+        const float vv = b2 * v[e] + (1.f - b2) * gg * gg;
+        m[e] = mm;
+        v[e] = vv;
+        p[e] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+    }
+}
+
+// BF16 copies W (out_p x in_p) and W^T (in_p x out_p) of a FP32 master
+static __global__ void weights_bf16_kernel(const float *__restrict__ W, int out_p, int in_p,
+                                           __nv_bfloat16 *__restrict__ W16, __nv_bfloat16 *__restrict__ Wt16) {
+    const int64_t total = (int64_t)out_p * in_p;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int o = static_cast<int>(e / in_p), i = static_cast<int>(e % in_p);
+        const __nv_bfloat16 w = __float2bfloat16(W[e]);
+        W16[e] = w;
+        Wt16[(size_t)i * out_p + o] = w;
+    }
+}
+
+inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
+
+class Net {
+   public:
+    Net(int din, int h, int layers, int dout, int batch, cudaStream_t s) : din_(din), h_(h), L_(layers + 1), dout_(dout),
+                                                                           batch_(batch), stream_(s) {
+        if (din < 1 || h < 1 || layers < 1 || dout < 1 || batch < BM || batch % BM)
+            throw CudaError("network sizes: batch must be a positive multiple of 128", SCS_INVALID_INPUT);
+        for (int l = 0; l < L_; ++l) {
+            const int in = l == 0 ? din : h, out = l == L_ - 1 ? dout : h;
+            // a layer reads its input with the previous layer's padded width
+            const int in_p = l == 0 ? round_up(in, 64) : layers_.back().out_p, out_p = round_up(out, 128);
+            Layer Y;
+            Y.in = in;
+            Y.out = out;
+            Y.in_p = in_p;
+            Y.out_p = out_p;
+            Y.W = alloc<float>((size_t)out_p * in_p);
+            Y.b = alloc<float>(out_p);
+            Y.gW = alloc<float>((size_t)out_p * in_p);
+            Y.gb = alloc<float>(out_p);
+            Y.mW = alloc<float>((size_t)out_p * in_p);
+            Y.vW = alloc<float>((size_t)out_p * in_p);
+            Y.mb = alloc<float>(out_p);
+            Y.vb = alloc<float>(out_p);
+            Y.W16 = alloc<__nv_bfloat16>((size_t)out_p * in_p);
+            Y.Wt16 = alloc<__nv_bfloat16>((size_t)out_p * in_p);
+            Y.Z = alloc<float>((size_t)batch * out_p);
+            Y.A16 = alloc<__nv_bfloat16>((size_t)batch * out_p);
+            Y.dz32 = alloc<float>((size_t)batch * out_p);
+            Y.dz16 = alloc<__nv_bfloat16>((size_t)batch * out_p);
+            Y.dzt16 = alloc<__nv_bfloat16>((size_t)batch * out_p);
+            Y.at16 = alloc<__nv_bfloat16>((size_t)batch * in_p);
+            Y.dA = alloc<float>((size_t)batch * in_p);
+            for (float *p : {Y.W, Y.mW, Y.vW}) SCS_CUDA(cudaMemsetAsync(p, 0, sizeof(float) * out_p * in_p, stream_));
+            for (float *p : {Y.b, Y.mb, Y.vb}) SCS_CUDA(cudaMemsetAsync(p, 0, sizeof(float) * out_p, stream_));
+            layers_.push_back(Y);
+        }
+        x16_ = alloc<__nv_bfloat16>((size_t)batch * layers_[0].in_p);
+        part_ = alloc<double>(1024);
+        loss_ = alloc<double>(1);
+        SCS_CUDA(cudaStreamSynchronize(stream_));
+    }
+    ~Net() {
+        for (void *p : allocs_) cudaFree(p);
+    }
+
+    int64_t param_count() const {
+        int64_t c = 0;
+        for (const Layer &Y : layers_) c += (int64_t)Y.out * Y.in + Y.out;
+        return c;
+    }
+
+    // packed host layout: per layer W (out x in, row-major) then b (out)
+    void set_params(const float *h) {
+        const float *p = h;
+        for (Layer &Y : layers_) {
+            std::vector<float> W((size_t)Y.out_p * Y.in_p, 0.f), b(Y.out_p, 0.f);
+            for (int o = 0; o < Y.out; ++o)
+                for (int i = 0; i < Y.in; ++i) W[(size_t)o * Y.in_p + i] = *p++;
+            for (int o = 0; o < Y.out; ++o) b[o] = *p++;
+            SCS_CUDA(cudaMemcpyAsync(Y.W, W.data(), sizeof(float) * W.size(), cudaMemcpyHostToDevice, stream_));
+            SCS_CUDA(cudaMemcpyAsync(Y.b, b.data(), sizeof(float) * b.size(), cudaMemcpyHostToDevice, stream_));
+            SCS_CUDA(cudaMemsetAsync(Y.mW, 0, sizeof(float) * W.size(), stream_));
+            SCS_CUDA(cudaMemsetAsync(Y.vW, 0, sizeof(float) * W.size(), stream_));
+            SCS_CUDA(cudaMemsetAsync(Y.mb, 0, sizeof(float) * b.size(), stream_));
+            SCS_CUDA(cudaMemsetAsync(Y.vb, 0, sizeof(float) * b.size(), stream_));
+            SCS_CUDA(cudaStreamSynchronize(stream_));
+        }
+        step_ = 0;
+        refresh_bf16();
+    }
+    void get(float *h, bool grads) {
+        float *p = h;
+        for (Layer &Y : layers_) {
+            std::vector<float> W((size_t)Y.out_p * Y.in_p), b(Y.out_p);
+            SCS_CUDA(cudaMemcpyAsync(W.data(), grads ? Y.gW : Y.W, sizeof(float) * W.size(), cudaMemcpyDeviceToHost,
+                                     stream_));
+            SCS_CUDA(cudaMemcpyAsync(b.data(), grads ? Y.gb : Y.b, sizeof(float) * b.size(), cudaMemcpyDeviceToHost,
+                                     stream_));
+            SCS_CUDA(cudaStreamSynchronize(stream_));
+            for (int o = 0; o < Y.out; ++o)
+                for (int i = 0; i < Y.in; ++i) *p++ = W[(size_t)o * Y.in_p + i];
+            for (int o = 0; o < Y.out; ++o) *p++ = b[o];
+        }
+    }
+
+    void refresh_bf16() {
+        for (Layer &Y : layers_) {
+            weights_bf16_kernel<<<grid((int64_t)Y.out_p * Y.in_p), 256, 0, stream_>>>(Y.W, Y.out_p, Y.in_p, Y.W16,
+                                                                                    Y.Wt16);
+        }
+        SCS_CUDA(cudaGetLastError());
+    }
+
+    // forward of `batch_` rows of x (device FP32, batch x din); the output
+    // layer's Z (FP32, batch x out_p) holds the prediction
+    void forward(const float *x) {
+        const Layer &F = layers_[0];
+        to_bf16_kernel<<<grid((int64_t)batch_ * F.in_p), 256, 0, stream_>>>(x, batch_, din_, x16_, F.in_p);
+        const __nv_bfloat16 *in = x16_;
+        for (int l = 0; l < L_; ++l) {
+            Layer &Y = layers_[l];
+            if (l < L_ - 1) gemm(in, Y.in_p, Y.W16, Y.in_p, batch_, Y.out_p, Y.in_p, EpiHidden{Y.Z, Y.A16, Y.b, Y.out_p, Y.out_p});
+            else gemm(in, Y.in_p, Y.W16, Y.in_p, batch_, Y.out_p, Y.in_p, EpiBias{Y.Z, Y.b, Y.out_p});
+            in = Y.A16;
+        }
+        SCS_CUDA(cudaGetLastError());
+    }
+
+    // forward + backward: gradients in gW, gb; loss (device double)
+    void backward(const float *x, const float *t) {
+        forward(x);
+        Layer &O = layers_[L_ - 1];
+        const int nb = 264;
+        loss_grad_kernel<<<nb, 256, 0, stream_>>>(O.Z, O.out_p, t, dout_, batch_, O.dz32, O.dz16, part_);
+        sum_parts_kernel<<<1, 32, 0, stream_>>>(part_, nb, 1.0 / ((double)batch_ * dout_), loss_);
+        for (int l = L_ - 1; l >= 0; --l) {
+            Layer &Y = layers_[l];
+            const __nv_bfloat16 *in16 = l == 0 ? x16_ : layers_[l - 1].A16;
+            if (l < L_ - 1) {
+                // dZ = dA_out * GELU'(Z), dA_out from the layer above
+                gelu_back_kernel<<<grid((int64_t)batch_ * Y.out_p), 256, 0, stream_>>>(
+                    layers_[l + 1].dA, Y.Z, (int64_t)batch_ * Y.out_p, Y.dz32, Y.dz16);
+            }
+            // dZ^T and input^T (BF16)
+            transpose(Y.dz16, Y.out_p, Y.dzt16, batch_, batch_, Y.out_p);
+            transpose(in16, Y.in_p, Y.at16, batch_, batch_, Y.in_p);
+            // dW = dZ^T X: (out_p x batch) (in_p x batch)^T
+            gemm(Y.dzt16, batch_, Y.at16, batch_, Y.out_p, Y.in_p, batch_, EpiPlain{Y.gW, Y.in_p});
+            colsum_kernel<<<(Y.out_p + 255) / 256, 256, 0, stream_>>>(Y.dz32, batch_, Y.out_p, Y.gb);
+            // dX = dZ W: (batch x out_p) (in_p x out_p)^T
+            if (l > 0) gemm(Y.dz16, Y.out_p, Y.Wt16, Y.out_p, batch_, Y.in_p, Y.out_p, EpiPlain{Y.dA, Y.in_p});
+        }
+        SCS_CUDA(cudaGetLastError());
+    }
+
+    void adam(float lr) {
+        ++step_;
+        const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+        const float c1 = 1.f - std::pow(b1, (float)step_), c2 = 1.f - std::pow(b2, (float)step_);
+        for (Layer &Y : layers_) {
+            const int64_t nw = (int64_t)Y.out_p * Y.in_p;
+            adam_kernel<<<grid(nw), 256, 0, stream_>>>(Y.W, Y.gW, Y.mW, Y.vW, nw, lr, b1, b2, eps, c1, c2);
+            adam_kernel<<<grid(Y.out_p), 256, 0, stream_>>>(Y.b, Y.gb, Y.mb, Y.vb, Y.out_p, lr, b1, b2, eps, c1, c2);
+        }
+        refresh_bf16();
+    }
+
+    double loss_host() {
+        double h = 0.0;
+        SCS_CUDA(cudaMemcpyAsync(&h, loss_, sizeof(double), cudaMemcpyDeviceToHost, stream_));
+        SCS_CUDA(cudaStreamSynchronize(stream_));
+        return h;
+    }
+
+    // prediction of the last forward: rows x dout (FP32) into y
+    void copy_output(float *y) {
+        const Layer &O = layers_[L_ - 1];
+        SCS_CUDA(cudaMemcpy2DAsync(y, sizeof(float) * dout_, O.Z, sizeof(float) * O.out_p, sizeof(float) * dout_,
+                                   batch_, cudaMemcpyDefault, stream_));
+    }
+
+    template <typename Epi>
+    void gemm(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, int M, int N, int K, Epi epi) {
+        if (M % BM || N % BN || K % BK || lda % 8 || ldb % 8 || (reinterpret_cast<uintptr_t>(A) & 15) ||
+            (reinterpret_cast<uintptr_t>(B) & 15))
+            throw CudaError("GEMM shape outside the kernel's tiling", SCS_INVALID_INPUT);
+        gemm_nt_kernel<Epi><<<dim3(N / BN, M / BM), kGemmThreads, 0, stream_>>>(A, lda, B, ldb, K, epi);
+    }
+    void transpose(const __nv_bfloat16 *src, int lds, __nv_bfloat16 *dst, int ldd, int rows, int cols) {
+        transpose_kernel<<<dim3((cols + 31) / 32, (rows + 31) / 32), dim3(32, 8), 0, stream_>>>(src, lds, dst, ldd,
+                                                                                               rows, cols);
+    }
+    int grid(int64_t len) const { return static_cast<int>(std::min<int64_t>((len + 255) / 256, 4096)); }
+
+    template <typename U>
+    U *alloc(size_t n) {
+        void *p = nullptr;
+        SCS_CUDA(cudaMalloc(&p, sizeof(U) * (n ? n : 1)));
+        allocs_.push_back(p);
+        return static_cast<U *>(p);
+    }
+
+    struct Layer {
+        int in, out, in_p, out_p;
+        float *W, *b, *gW, *gb, *mW, *vW, *mb, *vb;
+        __nv_bfloat16 *W16, *Wt16;
+        float *Z, *dz32, *dA;      // pre-activation; dZ; gradient w.r.t. this layer's input
+        __nv_bfloat16 *A16, *dz16, *dzt16, *at16;
+    };
+
+    int din_, h_, L_, dout_, batch_;
+    int step_ = 0;
+    cudaStream_t stream_;
+    std::vector<Layer> layers_;
+    std::vector<void *> allocs_;
+    __nv_bfloat16 *x16_ = nullptr;
+    double *part_ = nullptr, *loss_ = nullptr;
+};
+
+// ---------------------------------------------------------------------------
+// data helpers of the warm-start pipeline
+// ---------------------------------------------------------------------------
+// mean and standard deviation of every column (FP64 sums, one thread a column)
+static __global__ void column_stats_kernel(const float *__restrict__ d, int64_t rows, int cols, float *mean,
+                                           float *sd) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    double s = 0.0, s2 = 0.0;
+    for (int64_t r = 0; r < rows; ++r) {
+        const double v = d[r * cols + c];
+        s += v;
+        s2 += v * v;
+    }
+    const double mu = s / (double)rows;
+    const double var = fmax(s2 / (double)rows - mu * mu, 0.0);
+    mean[c] = static_cast<float>(mu);
+    sd[c] = static_cast<float>(fmax(sqrt(var), 1e-6 * (1.0 + fabs(mu))));
+}
+
+static __global__ void standardize_kernel(float *__restrict__ d, int64_t rows, int cols, const float *__restrict__ mean,
+                                          const float *__restrict__ sd) {
+    const int64_t total = rows * cols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = static_cast<int>(e % cols);
+        d[e] = (d[e] - mean[c]) / sd[c];
+    }
+}
+
+static __global__ void gather_rows_kernel(const float *__restrict__ src, int cols, const int64_t *__restrict__ idx,
+                                          int64_t count, float *__restrict__ dst) {
+    const int64_t total = count * cols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / cols;
+        const int c = static_cast<int>(e % cols);
+        dst[e] = src[idx[r] * cols + c];
+    }
+}
+
+// prediction (standardized (u_x, u_y, v_s, u_tau)) -> scaled warm start
+// x^ = u_x / tau, y^ = u_y / tau, s^ = v_s / tau with tau = max(u_tau, tau_min)
+static __global__ void warm_from_pred_kernel(const float *__restrict__ pred, int64_t ld, const float *__restrict__ mean,
+                                             const float *__restrict__ sd, int n, int m, int64_t count, double tau_min,
+                                             double *__restrict__ xh, double *__restrict__ yh, double *__restrict__ sh) {
+    const int w = n + 2 * m;
+    const int64_t total = count * w;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = e / w;
+        const int c = static_cast<int>(e % w);
+        const float *p = pred + b * ld;
+        const double tau = fmax((double)p[w] * sd[w] + mean[w], tau_min);
+        const double v = ((double)p[c] * sd[c] + mean[c]) / tau;
+        if (c < n) xh[b * n + c] = v;
+        else if (c < n + m) yh[b * m + c - n] = v;
+        else sh[b * m + c - n - m] = v;
+    }
+}
+
+}  // namespace mlp
+}  // namespace scs
+
+struct scs_mlp {
+    scs::mlp::Net *net = nullptr;
+    cudaStream_t stream = nullptr;
+    bool own = false;
+};
+
+namespace {
+template <typename F>
+int32_t mlp_guarded(F f) {
+    try {
+        return f();
+    } catch (const scs::CudaError &e) {
+        scs::set_last_error(e.what());
+        return e.code;
+    } catch (const std::exception &e) {
+        scs::set_last_error(e.what());
+        return SCS_DEVICE_ERROR;
+    }
+}
+int grid_of(int64_t len) { return static_cast<int>(std::min<int64_t>((len + 255) / 256, 4096)); }
+}  // namespace
+
+extern "C" {
+
+scs_mlp *scs_mlp_create(int32_t d_in, int32_t hidden, int32_t layers, int32_t d_out, int32_t batch, void *stream,
+                        int32_t *err) {
+    scs_mlp *w = new scs_mlp;
+    int32_t e = mlp_guarded([&]() -> int32_t {
+        if (stream) {
+            w->stream = static_cast<cudaStream_t>(stream);
+        } else {
+            SCS_CUDA(cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking));
+            w->own = true;
+        }
+        w->net = new scs::mlp::Net(d_in, hidden, layers, d_out, batch, w->stream);
+        return 0;
+    });
+    if (e) {
+        delete w->net;
+        if (w->own && w->stream) cudaStreamDestroy(w->stream);
+        delete w;
+        w = nullptr;
+    }
+    if (err) *err = e;
+    return w;
+}
+
+int64_t scs_mlp_param_count(scs_mlp *w) { return w && w->net ? w->net->param_count() : -1; }
+
+int32_t scs_mlp_set_params(scs_mlp *w, const float *params) {
+    if (!w || !w->net || !params) return SCS_INVALID_INPUT;
+    return mlp_guarded([&] { w->net->set_params(params); return 0; });
+}
+
+int32_t scs_mlp_get_params(scs_mlp *w, float *params) {
+    if (!w || !w->net || !params) return SCS_INVALID_INPUT;
+    return mlp_guarded([&] { w->net->get(params, false); return 0; });
+}
+
+int32_t scs_mlp_forward(scs_mlp *w, const float *x, float *y) {
+    if (!w || !w->net || !x || !y) return SCS_INVALID_INPUT;
+    return mlp_guarded([&] {
+        w->net->forward(x);
+        w->net->copy_output(y);
+        SCS_CUDA(cudaStreamSynchronize(w->stream));
+        return 0;
+    });
+}
+
+int32_t scs_mlp_gradients(scs_mlp *w, const float *x, const float *t, float *grads, float *loss) {
+    if (!w || !w->net || !x || !t) return SCS_INVALID_INPUT;
+    return mlp_guarded([&] {
+        w->net->backward(x, t);
+        if (grads) w->net->get(grads, true);
+        if (loss) *loss = static_cast<float>(w->net->loss_host());
+        return 0;
+    });
+}
+
+int32_t scs_mlp_train_step(scs_mlp *w, const float *x, const float *t, float lr, float *loss) {
+    if (!w || !w->net || !x || !t) return SCS_INVALID_INPUT;
+    return mlp_guarded([&] {
+        w->net->backward(x, t);
+        w->net->adam(lr);
+        if (loss) *loss = static_cast<float>(w->net->loss_host());
+        return 0;
+    });
+}
+
+void scs_mlp_destroy(scs_mlp *w) {
+    if (!w) return;
+    delete w->net;
+    if (w->own && w->stream) cudaStreamDestroy(w->stream);
+    delete w;
+}
+
+int32_t scs_column_stats(const float *data, int64_t rows, int32_t cols, float *mean, float *sd, void *stream) {
+    if (!data || rows <= 0 || cols <= 0 || !mean || !sd) return SCS_INVALID_INPUT;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    scs::mlp::column_stats_kernel<<<(cols + 127) / 128, 128, 0, s>>>(data, rows, cols, mean, sd);
+    return cudaGetLastError() == cudaSuccess ? 0 : SCS_DEVICE_ERROR;
+}
+
+int32_t scs_standardize(float *data, int64_t rows, int32_t cols, const float *mean, const float *sd, void *stream) {
+    if (!data || rows <= 0 || cols <= 0 || !mean || !sd) return SCS_INVALID_INPUT;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    scs::mlp::standardize_kernel<<<grid_of(rows * cols), 256, 0, s>>>(data, rows, cols, mean, sd);
+    return cudaGetLastError() == cudaSuccess ? 0 : SCS_DEVICE_ERROR;
+}
+
+int32_t scs_gather_rows(const float *src, int32_t cols, const int64_t *idx, int64_t count, float *dst, void *stream) {
+    if (!src || cols <= 0 || !idx || count < 0 || !dst) return SCS_INVALID_INPUT;
+    if (!count) return 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    scs::mlp::gather_rows_kernel<<<grid_of(count * cols), 256, 0, s>>>(src, cols, idx, count, dst);
+    return cudaGetLastError() == cudaSuccess ? 0 : SCS_DEVICE_ERROR;
+}
+
+int32_t scs_warm_from_prediction(const float *pred, int64_t ld, const float *mean, const float *sd, int32_t n,
+                                 int32_t m, int64_t count, double tau_min, double *xh, double *yh, double *sh,
+                                 void *stream) {
+    if (!pred || !mean || !sd || n <= 0 || m <= 0 || count < 0 || ld < n + 2 * m + 1 || !xh || !yh || !sh ||
+        !(tau_min > 0))
+        return SCS_INVALID_INPUT;
+    if (!count) return 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    scs::mlp::warm_from_pred_kernel<<<grid_of(count * (n + 2 * m)), 256, 0, s>>>(pred, ld, mean, sd, n, m, count,
+                                                                                  tau_min, xh, yh, sh);
+    return cudaGetLastError() == cudaSuccess ? 0 : SCS_DEVICE_ERROR;
+}
+
+}  // extern "C"

@@ -121,6 +121,50 @@ def lib():
         L.scs_batch_config.restype = I32
         L.scs_batch_finish.argtypes = [P]
         L.scs_batch_finish.restype = None
+        L.scs_family_init.argtypes = [C.POINTER(CSC), C.POINTER(ConeC), I32, D, D, C.POINTER(Settings),
+                                      C.POINTER(I32)]
+        L.scs_family_init.restype = P
+        L.scs_family_set_data.argtypes = [P, D, D]
+        L.scs_family_set_data.restype = I32
+        L.scs_family_warm_start.argtypes = [P, C.c_void_p, C.c_void_p, C.c_void_p, I32]
+        L.scs_family_warm_start.restype = I32
+        L.scs_family_solve.argtypes = [P, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Info), I32]
+        L.scs_family_solve.restype = I32
+        L.scs_family_iterate.argtypes = [P, I32]
+        L.scs_family_iterate.restype = I32
+        L.scs_family_get_iterates.argtypes = [P, I32, D, D]
+        L.scs_family_get_iterates.restype = I32
+        L.scs_family_snapshots.argtypes = [P, C.c_void_p]
+        L.scs_family_snapshots.restype = I32
+        L.scs_family_dims.argtypes = [P, C.POINTER(I32), C.POINTER(I32), C.POINTER(I32)]
+        L.scs_family_dims.restype = I32
+        L.scs_family_finish.argtypes = [P]
+        L.scs_family_finish.restype = None
+        V = C.c_void_p
+        L.scs_mlp_create.argtypes = [I32, I32, I32, I32, I32, V, C.POINTER(I32)]
+        L.scs_mlp_create.restype = P
+        L.scs_mlp_param_count.argtypes = [P]
+        L.scs_mlp_param_count.restype = C.c_int64
+        L.scs_mlp_set_params.argtypes = [P, V]
+        L.scs_mlp_set_params.restype = I32
+        L.scs_mlp_get_params.argtypes = [P, V]
+        L.scs_mlp_get_params.restype = I32
+        L.scs_mlp_forward.argtypes = [P, V, V]
+        L.scs_mlp_forward.restype = I32
+        L.scs_mlp_gradients.argtypes = [P, V, V, V, C.POINTER(C.c_float)]
+        L.scs_mlp_gradients.restype = I32
+        L.scs_mlp_train_step.argtypes = [P, V, V, C.c_float, C.POINTER(C.c_float)]
+        L.scs_mlp_train_step.restype = I32
+        L.scs_mlp_destroy.argtypes = [P]
+        L.scs_mlp_destroy.restype = None
+        L.scs_column_stats.argtypes = [V, C.c_int64, I32, V, V, V]
+        L.scs_column_stats.restype = I32
+        L.scs_standardize.argtypes = [V, C.c_int64, I32, V, V, V]
+        L.scs_standardize.restype = I32
+        L.scs_gather_rows.argtypes = [V, I32, V, C.c_int64, V, V]
+        L.scs_gather_rows.restype = I32
+        L.scs_warm_from_prediction.argtypes = [V, C.c_int64, V, V, I32, I32, C.c_int64, C.c_double, V, V, V, V]
+        L.scs_warm_from_prediction.restype = I32
         L.scs_last_error.argtypes = []
         L.scs_last_error.restype = C.c_char_p
         _lib_handle = L
@@ -404,3 +448,196 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Family:
+    """Members that share A and the cone and differ in b, c
+    (``scs_family_*``): one dense direct iteration of all members at once.
+    ``B`` (count x m) and ``Cs`` (count x n) hold the members' b and c."""
+
+    def __init__(self, A, cone, B, Cs, settings: Settings | None = None, **kw):
+        import scipy.sparse as sp
+        A = sp.csc_matrix(A)
+        self.m, self.n = A.shape
+        B = np.ascontiguousarray(B, dtype=np.float64)
+        Cs = np.ascontiguousarray(Cs, dtype=np.float64)
+        self.count = B.shape[0]
+        assert B.shape == (self.count, self.m) and Cs.shape == (self.count, self.n)
+        self._keep = [np.ascontiguousarray(A.indptr, dtype=np.int64), np.ascontiguousarray(A.indices, dtype=np.int32),
+                      np.ascontiguousarray(A.data, dtype=np.float64)]
+        cp, ri, va = self._keep
+        csc = CSC(self.m, self.n, cp.ctypes.data_as(C.POINTER(C.c_int64)), ri.ctypes.data_as(C.POINTER(C.c_int32)),
+                  va.ctypes.data_as(C.POINTER(C.c_double)))
+        kc, keep = cone_struct(cone)
+        self._keep.append(keep)
+        st = settings if settings is not None else default_settings()
+        for k, v in kw.items():
+            setattr(st, k, v)
+        self.settings = st
+        err = C.c_int32(0)
+        self._w = lib().scs_family_init(C.byref(csc), C.byref(kc), self.count, _dptr(B), _dptr(Cs), C.byref(st),
+                                        C.byref(err))
+        if not self._w:
+            raise ScsError(err.value, last_error())
+
+    def _check(self, rc):
+        if rc != 0:
+            raise ScsError(rc, last_error())
+        return rc
+
+    def set_data(self, B, Cs):
+        B = np.ascontiguousarray(B, dtype=np.float64)
+        Cs = np.ascontiguousarray(Cs, dtype=np.float64)
+        return self._check(lib().scs_family_set_data(self._w, _dptr(B), _dptr(Cs)))
+
+    def warm_start(self, X=None, Y=None, S=None):
+        """Host arrays (count x n / m / m) in the caller's units (Sec. 4.2)."""
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (X, Y, S)]
+        ptrs = [None if a is None else a.ctypes.data for a in arrs]
+        return self._check(lib().scs_family_warm_start(self._w, *ptrs, 0))
+
+    def warm_start_scaled_device(self, x_ptr, y_ptr, s_ptr):
+        """Device pointers (FP64, count x n / m / m) of scaled x^, y^, s^."""
+        return self._check(lib().scs_family_warm_start(self._w, x_ptr, y_ptr, s_ptr, 1))
+
+    def solve(self):
+        """Return ``(X, Y, S, infos)`` (count x n, count x m, count x m)."""
+        X = np.empty((self.count, self.n))
+        Y = np.empty((self.count, self.m))
+        S = np.empty((self.count, self.m))
+        info = (Info * self.count)()
+        self._check(lib().scs_family_solve(self._w, X.ctypes.data, Y.ctypes.data, S.ctypes.data, info, 0))
+        return X, Y, S, [info[i].as_dict() for i in range(self.count)]
+
+    def solve_info(self):
+        """Solve, returning only the per-member infos (outputs stay on the device)."""
+        info = (Info * self.count)()
+        self._check(lib().scs_family_solve(self._w, None, None, None, info, 0))
+        return [info[i].as_dict() for i in range(self.count)]
+
+    def iterate(self, iters):
+        return self._check(lib().scs_family_iterate(self._w, int(iters)))
+
+    def iterates(self, index):
+        N = self.n + self.m + 1
+        u, v = np.empty(N), np.empty(N)
+        self._check(lib().scs_family_get_iterates(self._w, int(index), _dptr(u), _dptr(v)))
+        return u, v
+
+    def snapshots(self, dst_ptr):
+        """Copy the members' (u_x, u_y, v_s, u_tau) at their first passing test
+        (float32, count x (n + 2m + 1)) to dst_ptr (host or device)."""
+        return self._check(lib().scs_family_snapshots(self._w, dst_ptr))
+
+    def close(self):
+        if getattr(self, "_w", None):
+            lib().scs_family_finish(self._w)
+            self._w = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _rc(rc):
+    if rc != 0:
+        raise ScsError(rc, last_error())
+    return rc
+
+
+class MLP:
+    """The warm-start network (``scs_mlp_*``): BF16 tensor-core kernels with
+    FP32 master weights.  Pointers are device addresses (ints)."""
+
+    def __init__(self, d_in, hidden, layers, d_out, batch, stream=None):
+        err = C.c_int32(0)
+        self.d_in, self.hidden, self.layers, self.d_out, self.batch = d_in, hidden, layers, d_out, batch
+        self._w = lib().scs_mlp_create(d_in, hidden, layers, d_out, batch, stream, C.byref(err))
+        if not self._w:
+            raise ScsError(err.value, last_error())
+
+    def param_count(self):
+        return int(lib().scs_mlp_param_count(self._w))
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        assert flat.size == self.param_count()
+        return _rc(lib().scs_mlp_set_params(self._w, flat.ctypes.data))
+
+    def get_params(self):
+        out = np.empty(self.param_count(), dtype=np.float32)
+        _rc(lib().scs_mlp_get_params(self._w, out.ctypes.data))
+        return out
+
+    def forward(self, x_ptr, y_ptr):
+        return _rc(lib().scs_mlp_forward(self._w, x_ptr, y_ptr))
+
+    def gradients(self, x_ptr, t_ptr):
+        g = np.empty(self.param_count(), dtype=np.float32)
+        loss = C.c_float(0)
+        _rc(lib().scs_mlp_gradients(self._w, x_ptr, t_ptr, g.ctypes.data, C.byref(loss)))
+        return loss.value, g
+
+    def train_step(self, x_ptr, t_ptr, lr, want_loss=False):
+        loss = C.c_float(0)
+        _rc(lib().scs_mlp_train_step(self._w, x_ptr, t_ptr, float(lr), C.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def close(self):
+        if getattr(self, "_w", None):
+            lib().scs_mlp_destroy(self._w)
+            self._w = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def column_stats(data_ptr, rows, cols, mean_ptr, sd_ptr, stream=None):
+    return _rc(lib().scs_column_stats(data_ptr, rows, cols, mean_ptr, sd_ptr, stream))
+
+
+def standardize(data_ptr, rows, cols, mean_ptr, sd_ptr, stream=None):
+    return _rc(lib().scs_standardize(data_ptr, rows, cols, mean_ptr, sd_ptr, stream))
+
+
+def gather_rows(src_ptr, cols, idx_ptr, count, dst_ptr, stream=None):
+    return _rc(lib().scs_gather_rows(src_ptr, cols, idx_ptr, count, dst_ptr, stream))
+
+
+def warm_from_prediction(pred_ptr, ld, mean_ptr, sd_ptr, n, m, count, tau_min, xh_ptr, yh_ptr, sh_ptr, stream=None):
+    return _rc(lib().scs_warm_from_prediction(pred_ptr, ld, mean_ptr, sd_ptr, n, m, count, tau_min, xh_ptr, yh_ptr,
+                                              sh_ptr, stream))
+
+
+def pack_params(params):
+    """[(W, b), ...] -> flat float32 in the library's layout."""
+    return np.concatenate([np.concatenate([np.asarray(W, np.float64).ravel(), np.asarray(b, np.float64)])
+                           for W, b in params]).astype(np.float32)
+
+
+def unpack_params(flat, sizes):
+    out, p = [], 0
+    for fin, fout in zip(sizes[:-1], sizes[1:]):
+        W = flat[p:p + fin * fout].reshape(fout, fin)
+        p += fin * fout
+        b = flat[p:p + fout]
+        p += fout
+        out.append((W, b))
+    return out

@@ -400,3 +400,91 @@ def random_cone(seed=0, n=30, m=None, cone=None, density=0.3) -> Problem:
         A[int(rng.integers(0, m)), j] = rng.standard_normal()
     A = sp.csc_matrix(A)
     return from_pair(A, cone, rng, meta=dict(workload="random_cone", seed=seed))
+
+
+# ---------------------------------------------------------------------------
+# Parametric lasso family (Sec. 6.2 SOCP form) for the learned warm start
+# ---------------------------------------------------------------------------
+
+@dataclass
+class LassoFamily:
+    """minimize (1/2)||F z - g||^2 + mu ||z||_1 over z in R^p, as the SOCP of
+    Sec. 6.2 with variables x = (z, t, w) in R^(2p+1):
+
+        minimize (1/2) w + mu 1^T t
+        s.t.  -t <= z <= t,   ||(1 - w, 2 (F z - g))|| <= 1 + w,
+
+    standard form A x + s = b, s in K = R+^(2p) x SOC(q + 2):
+        rows 0..p-1    (z - t <= 0):  A = [ I, -I, 0],  b = 0
+        rows p..2p-1   (-z - t <= 0): A = [-I, -I, 0],  b = 0
+        SOC head       1 + w:         A = [0, 0, -1],   b = 1
+        SOC            1 - w:         A = [0, 0,  1],   b = 1
+        SOC tail       2 (F z - g):   A = [-2F, 0, 0],  b = -2 g
+    c = (0, mu 1, 1/2).  A is the same for every member; theta in R^d moves
+    only b (through g = G theta) and c (through mu = mu0 (1 + tanh(a.theta/8)/2),
+    which stays positive; mu0 is 0.1 times the median of ||F^T g||_inf over
+    1000 draws of theta, the paper's mu = 0.1 mu_max rule)."""
+
+    F: np.ndarray
+    G: np.ndarray
+    a: np.ndarray
+    mu0: float
+    A: sp.csc_matrix
+    cone: Cone
+
+    @property
+    def p(self):
+        return self.F.shape[1]
+
+    @property
+    def q(self):
+        return self.F.shape[0]
+
+    @property
+    def d(self):
+        return self.G.shape[1]
+
+    def mu(self, theta):
+        return self.mu0 * (1.0 + 0.5 * np.tanh(self.a @ theta / 8.0))
+
+    def bc(self, theta):
+        """(b, c) of the member theta."""
+        p, q = self.p, self.q
+        g = self.G @ theta
+        b = np.zeros(2 * p + q + 2)
+        b[2 * p] = 1.0
+        b[2 * p + 1] = 1.0
+        b[2 * p + 2:] = -2.0 * g
+        c = np.zeros(2 * p + 1)
+        c[p:2 * p] = self.mu(theta)
+        c[2 * p] = 0.5
+        return b, c
+
+    def problem(self, theta) -> Problem:
+        b, c = self.bc(theta)
+        return Problem(A=self.A, b=b, c=c, cone=self.cone, kind="feasible",
+                       meta=dict(workload="lasso", theta=np.asarray(theta)))
+
+    def thetas(self, seed, count):
+        return np.random.default_rng(seed).standard_normal((count, self.d))
+
+
+def lasso_family(seed=0, p=400, q=1000, d=64) -> LassoFamily:
+    rng = np.random.default_rng(seed)
+    F = rng.standard_normal((q, p)) / math.sqrt(q)
+    G = rng.standard_normal((q, d)) / 8.0
+    a = rng.standard_normal(d)
+    th = rng.standard_normal((1000, d))
+    mu0 = 0.1 * float(np.median(np.abs((G @ th.T).T @ F).max(axis=1)))
+    Ip = sp.identity(p, format="csc")
+    Z = sp.csc_matrix((p, p))
+    top = sp.hstack([Ip, -Ip, sp.csc_matrix((p, 1))])
+    mid = sp.hstack([-Ip, -Ip, sp.csc_matrix((p, 1))])
+    head = sp.csc_matrix(np.concatenate([np.zeros(2 * p), [-1.0]])[None, :])
+    head2 = sp.csc_matrix(np.concatenate([np.zeros(2 * p), [1.0]])[None, :])
+    tail = sp.hstack([sp.csc_matrix(-2.0 * F), sp.csc_matrix((q, p)), sp.csc_matrix((q, 1))])
+    A = sp.csc_matrix(sp.vstack([top, mid, head, head2, tail]))
+    del Z
+    cone = Cone(l=2 * p, q=(q + 2,))
+    assert A.shape == (cone.m, 2 * p + 1)
+    return LassoFamily(F=F, G=G, a=a, mu0=mu0, A=A, cone=cone)

