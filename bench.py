@@ -56,6 +56,28 @@ def parse():
     return ap.parse_args()
 
 
+def reduce_scalar(x, op, device="cuda"):
+    """x reduced over the ranks of the default process group ("max" or
+    "sum"); x itself when there is no group.  device: where the backend
+    exchanges tensors ("cuda" for NCCL, "cpu" for gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def replica_rate(units_local, seconds_local, device="cuda"):
+    """Whole-job rate of independent replicas: the units every rank did,
+    divided by the slowest rank's time (the timed region ends when the last
+    replica ends).  Returns (rate, units_total, seconds_max)."""
+    units = reduce_scalar(units_local, "sum", device)
+    secs = reduce_scalar(seconds_local, "max", device)
+    return units / secs, units, secs
+
+
 def dist_env():
     return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -317,18 +339,10 @@ def run_gb300(args):
             torch.distributed.barrier()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_scalar(x, "max")
 
     def sum_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t)
-        return float(t.item())
+        return reduce_scalar(x, "sum")
 
     S = scs.Solver(P.A, P.b, P.c, P.cone, time_limit_s=args.solve_seconds, **common)
     # warm-up iterations, then exactly `steps` timed iterations
@@ -342,16 +356,17 @@ def run_gb300(args):
     e1 = torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")      # ncu --nvtx-include "timed/" selects these launches
     e0.record(stream)
     S.iterate(args.steps, sync=False)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
     it1, cg1 = S.counters()
-    ms = max_over_ranks(e0.elapsed_time(e1))
-    iters_done = sum_over_ranks(it1 - it0)
-    value = iters_done / (ms / 1e3)
+    value, iters_done, secs = replica_rate(it1 - it0, e0.elapsed_time(e1) / 1e3)
+    ms = secs * 1e3
     cg_steps = cg1 - cg0
     # K1, K2, K6, K7 (+ the PSD kernel) per iteration and K3, K4, K5 per CG step
     launches = (5 if getattr(P.cone, "s", ()) else 4) * (it1 - it0) + 3 * cg_steps
@@ -359,7 +374,11 @@ def run_gb300(args):
     # roofline of the dominant kernel (CUDA events around each SpMV launch)
     has_psd = bool(getattr(P.cone, "s", ()))
     psd0 = S.psd_counters() if has_psd else None
+    # launched one by one (not through the graph: ncu does not profile kernel
+    # nodes of graphs with conditional nodes): ncu --nvtx-include "profiled/"
+    torch.cuda.nvtx.range_push("profiled")
     S.iterate_profiled(5)
+    torch.cuda.nvtx.range_pop()
     prof = {k: S.kernel_time(k) for k in (0, 1, 2, 3)}
     it_p, cg_p = S.counters()
     # counters include the profiled iterations: take CG steps of those 5 from the launch counts
@@ -529,11 +548,7 @@ def run_batch(args):
             torch.distributed.barrier()
 
     def reduce(x, op):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=op)
-        return float(t.item())
+        return reduce_scalar(x, op)
 
     # end to end: host CSC -> scs_batch_init (setup launch + autotuner) ->
     # scs_batch_solve -> x, y, s and infos on the host
@@ -544,7 +559,7 @@ def run_batch(args):
     init_s = time.perf_counter() - t0
     xs, ys, ss, infos = bt.solve()
     torch.cuda.synchronize()
-    e2e_s = reduce(time.perf_counter() - t0, torch.distributed.ReduceOp.MAX if world > 1 else None)
+    e2e_s = reduce(time.perf_counter() - t0, "max")
     cfg = bt.config()
     for _ in range(max(0, args.warmup - 1)):
         bt.solve()
@@ -564,9 +579,8 @@ def run_batch(args):
         dev_ms += e0.elapsed_time(e1)
     clk = clocks.stop()
     bt.close()
-    ms = reduce(dev_ms, torch.distributed.ReduceOp.MAX if world > 1 else None)
-    total = reduce(float(count * args.steps), torch.distributed.ReduceOp.SUM if world > 1 else None)
-    value = total / (ms / 1e3)
+    value, total, secs = replica_rate(count * args.steps, dev_ms / 1e3)
+    ms = secs * 1e3
     st = np.array([f["status"] for f in infos])
     iters = np.array([f["iters"] for f in infos])
     cg = np.array([f["cg_iters"] for f in infos])
