@@ -285,9 +285,17 @@ class Engine : public EngineBase {
     void setup(const HostProblem &P) {
         // sparse layouts
         // stored layouts of A and A^T; region grids for 8 CTAs per SM
-        const int spmv_ctas = sms_ * 8;
-        SpmvLayout<double> LA = spmv_layout(P.a_rowptr, P.a_col, P.a_val, spmv_ctas);
-        SpmvLayout<double> LAt = spmv_layout(P.at_rowptr, P.at_col, P.at_val, spmv_ctas);
+        // one full wave per product: CTAs = SMs x the resident CTAs per SM of
+        // the heaviest iteration epilogue that uses the layout
+        auto occ = [](auto kern) {
+            int n = 0;
+            SCS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kBlock, 0));
+            return std::max(1, std::min(n, 8));
+        };
+        const int occ_a = std::min(occ(spmv_kernel<T, T, T, EpiAInit<T>>), occ(spmv_kernel<T, T, T, EpiACG<T>>));
+        const int occ_at = std::min(occ(spmv_kernel<T, T, T, EpiAtInit<T>>), occ(spmv_kernel<T, T, T, EpiAtCG<T>>));
+        SpmvLayout<double> LA = spmv_layout(P.a_rowptr, P.a_col, P.a_val, sms_ * occ_a);
+        SpmvLayout<double> LAt = spmv_layout(P.at_rowptr, P.at_col, P.at_val, sms_ * occ_at);
         int32_t *a_rowptr = upload(LA.rowptr), *a_col = upload(LA.col), *a_rowid = upload(LA.rowid);
         double *a_val64 = upload(LA.val);
         int32_t *at_rowptr = upload(LAt.rowptr), *at_col = upload(LAt.col), *at_rowid = upload(LAt.rowid);
