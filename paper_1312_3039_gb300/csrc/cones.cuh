@@ -1,4 +1,5 @@
-// Device cone projections, FP64.  The iteration projects the y-part of u onto
+// Device cone projections, FP64 (and an FP32 exponential-cone projection for
+// the mixed-precision iteration).  The iteration projects the y-part of u onto
 // the dual cone K* (Eq. "e-hsdnice": C = R^n x K* x R+): the dual of the zero
 // cone is R (identity), the nonnegative and second-order cones are
 // self-dual, and the dual exponential cone is reached through Moreau
@@ -156,6 +157,93 @@ __host__ __device__ inline void proj_exp(double r0, double s0, double t0, double
 __host__ __device__ inline void proj_exp_dual(double u, double v, double w, double &pu, double &pv, double &pw) {
     double a, b, c;
     proj_exp(-u, -v, -w, a, b, c);
+    pu = u + a; pv = v + b; pw = w + c;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 version for the mixed-precision iteration (its iterates are FP32):
+// the same special cases, bracket, bisection and Newton steps, all in FP32
+// (GB300's FP64 rate is a small fraction of its FP32 rate), converged to
+// |step| <= 2e-7 max(1, |rho|); the better-conditioned of the two
+// expressions of the projection is returned.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ bool exp_member_f(float x, float y, float z) {
+    if (y > 0.0f) {
+        const float q = x / y;
+        return q < 80.0f && y * expf(q) <= z;
+    }
+    return y == 0.0f && x <= 0.0f && z >= 0.0f;
+}
+
+__host__ __device__ __forceinline__ bool exp_dual_member_f(float u, float v, float w) {
+    if (u < 0.0f) {
+        const float q = v / u;
+        return q < 80.0f && -u * expf(q) <= 2.718281828459045f * w;
+    }
+    return u == 0.0f && v >= 0.0f && w >= 0.0f;
+}
+
+__host__ __device__ inline void proj_exp_f(float r0, float s0, float t0, float &px, float &py, float &pz) {
+    if (exp_member_f(r0, s0, t0)) { px = r0; py = s0; pz = t0; return; }
+    if (exp_dual_member_f(-r0, -s0, -t0)) { px = 0.0f; py = 0.0f; pz = 0.0f; return; }
+    if (r0 <= 0.0f && s0 <= 0.0f) { px = r0; py = 0.0f; pz = fmaxf(t0, 0.0f); return; }
+    const float nrm = fmaxf(fabsf(r0), fmaxf(fabsf(s0), fabsf(t0)));
+    const float r = r0 / nrm, s = s0 / nrm, t = t0 / nrm;
+    const bool lo_open = !(r > 0.0f), hi_open = !(s > 0.0f);
+    float lo = lo_open ? 0.0f : 1.0f - s / r;
+    float hi = hi_open ? 0.0f : r / s;
+    const ExpCurveF ff{r, s, t};
+    float h, dh;
+    if (lo_open) {
+        float step = 1.0f;
+        for (int it = 0; it < 60; ++it) {
+            ff.eval(hi - step, h, dh);
+            if (h < 0.0f) break;
+            step *= 2.0f;
+        }
+        lo = hi - step;
+    }
+    if (hi_open) {
+        float step = 1.0f;
+        for (int it = 0; it < 60; ++it) {
+            ff.eval(lo + step, h, dh);
+            if (h > 0.0f) break;
+            step *= 2.0f;
+        }
+        hi = lo + step;
+    }
+    float rho = 0.5f * (lo + hi);
+    for (int it = 0; it < 120; ++it) {
+        ff.eval(rho, h, dh);
+        if (h == 0.0f) break;
+        if (h < 0.0f) lo = rho; else hi = rho;
+        const float tol = 2e-7f * fmaxf(1.0f, fabsf(rho));
+        if (hi - lo <= 1.0f && isfinite(dh) && dh > 0.0f) {
+            const float step = h / dh;
+            if (fabsf(step) <= tol) { rho -= step; break; }
+            const float c = rho - step;
+            if (c > lo && c < hi) { rho = c; continue; }
+        }
+        rho = 0.5f * (lo + hi);
+        if (hi - lo <= tol) break;
+    }
+    const float den = rho * rho - rho + 1.0f;
+    const float y = ((rho - 1.0f) * r + s) / den;
+    const float mu = (r - rho * s) / den;
+    const float ep = expf(rho), em = expf(-rho);
+    const float err_p = (fabsf(rho - 1.0f) * fabsf(r) + fabsf(s)) / den * sqrtf(rho * rho + 1.0f + ep * ep);
+    const float err_d = (fabsf(r) + fabsf(rho) * fabsf(s)) / den * sqrtf(1.0f + (rho - 1.0f) * (rho - 1.0f) + em * em) +
+                        sqrtf(r * r + s * s + t * t);
+    if (err_p <= err_d) {
+        px = nrm * (y * rho); py = nrm * y; pz = nrm * (y * ep);
+    } else {
+        px = nrm * (r - mu); py = nrm * (s + mu * (rho - 1.0f)); pz = nrm * (t + mu * em);
+    }
+}
+
+__host__ __device__ inline void proj_exp_dual_f(float u, float v, float w, float &pu, float &pv, float &pw) {
+    float a, b, c;
+    proj_exp_f(-u, -v, -w, a, b, c);
     pu = u + a; pv = v + b; pw = w + c;
 }
 

@@ -41,6 +41,8 @@
 
 #include <math.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "cones.cuh"
 #include "psd.cuh"
@@ -288,18 +290,22 @@ __global__ void __launch_bounds__(kBlock) relax_project_kernel(ProjArgs<T> a, Co
         const int tri = bid * kExpPerCta + threadIdx.x;
         if (threadIdx.x < kExpPerCta && tri < K.ep) {
             const int off = a.n + K.exp_off + 3 * tri;
-            double t[3], up[3];
+            T t[3], up[3];
             T uo[3], vo[3];
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
                 uo[e] = a.u[off + e];
                 vo[e] = a.v[off + e];
-                t[e] = static_cast<double>(relaxed(a, off + e, gamma, alpha)) - static_cast<double>(vo[e]);
+                t[e] = relaxed(a, off + e, gamma, alpha) - vo[e];
             }
-            proj_exp_dual(t[0], t[1], t[2], up[0], up[1], up[2]);
+            // in the precision of the iterates (FP32: no FP64 in this kernel)
+            if constexpr (std::is_same<T, float>::value)
+                proj_exp_dual_f(t[0], t[1], t[2], up[0], up[1], up[2]);
+            else
+                proj_exp_dual(t[0], t[1], t[2], up[0], up[1], up[2]);
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
-                const T un = static_cast<T>(up[e]), vn = static_cast<T>(up[e] - t[e]);
+                const T un = up[e], vn = up[e] - t[e];
                 a.u[off + e] = un;
                 a.v[off + e] = vn;
                 dd += (un - uo[e]) * (un - uo[e]) + (vn - vo[e]) * (vn - vo[e]);

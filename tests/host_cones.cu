@@ -10,3 +10,13 @@ extern "C" void host_proj_exp(const double *in, double *out, int n, int dual) {
             scs::proj_exp(in[3 * i], in[3 * i + 1], in[3 * i + 2], out[3 * i], out[3 * i + 1], out[3 * i + 2]);
     }
 }
+
+// FP32 version (the mixed-precision iteration's)
+extern "C" void host_proj_exp_f(const float *in, float *out, int n, int dual) {
+    for (int i = 0; i < n; ++i) {
+        if (dual)
+            scs::proj_exp_dual_f(in[3 * i], in[3 * i + 1], in[3 * i + 2], out[3 * i], out[3 * i + 1], out[3 * i + 2]);
+        else
+            scs::proj_exp_f(in[3 * i], in[3 * i + 1], in[3 * i + 2], out[3 * i], out[3 * i + 1], out[3 * i + 2]);
+    }
+}

@@ -40,3 +40,18 @@ def test_exp_projection_matches_oracle(lib, dual):
     ref = np.array([cones.proj_exp_dual(v) if dual else cones.proj_exp(v) for v in V])
     err = np.linalg.norm(out - ref, axis=1) / np.maximum(1.0, np.linalg.norm(V, axis=1))
     assert err.max() <= 1e-12, (V[np.argmax(err)], out[np.argmax(err)], ref[np.argmax(err)])
+
+
+@pytest.mark.parametrize("dual", [0, 1])
+def test_exp_projection_fp32_matches_oracle(lib, dual):
+    """The FP32 projection of the mixed-precision iteration, on FP32 inputs,
+    within a few FP32 ulps (relative to ||v||) of the FP64 oracle's projection
+    of the same inputs."""
+    V = points(20 + dual, 6000).astype(np.float32)
+    out = np.zeros_like(V)
+    lib.host_proj_exp_f(V.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p), len(V), dual)
+    Vd = V.astype(np.float64)
+    ref = np.array([cones.proj_exp_dual(v) if dual else cones.proj_exp(v) for v in Vd])
+    err = np.linalg.norm(out - ref, axis=1) / np.linalg.norm(Vd, axis=1)
+    assert err.max() <= 2e-5, (Vd[np.argmax(err)], out[np.argmax(err)], ref[np.argmax(err)], err.max())
+    assert np.median(err) <= 1e-6
