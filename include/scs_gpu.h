@@ -348,7 +348,23 @@ int32_t scs_mlp_gradients(scs_mlp *w, const float *x, const float *t, float *gra
 /* One Adam step (learning rate lr) on a batch; *loss (host) if not NULL
  * (then the call synchronises). */
 int32_t scs_mlp_train_step(scs_mlp *w, const float *x, const float *t, float lr, float *loss);
+/* Products on the 5th-generation tensor cores (tcgen05.mma with tensor-memory
+ * accumulators, the default when every padded size allows it) or on the
+ * warp-level mma.sync kernel (tcgen05 = 0); SCS_UNSUPPORTED if a padded size
+ * is outside the tcgen05 kernel's tiling (multiples of 64, batch of 128). */
+int32_t scs_mlp_set_tensor_path(scs_mlp *w, int32_t tcgen05);
+/* 0, or SCS_DEVICE_ERROR if a tcgen05 product's bounded wait ever timed out
+ * (its output is then not written); synchronises. */
+int32_t scs_mlp_error(scs_mlp *w);
 void scs_mlp_destroy(scs_mlp *w);
+
+/* The network's product alone, for tests and tuning: C (M x N, FP32, ld ldc)
+ * = A (M x K, BF16, ld lda) B (N x K, BF16, ld ldb)^T on the device, through
+ * the tcgen05 kernel (tcgen05 = 1: M % 128, N % 64, K % 64) or the mma.sync
+ * kernel (M % 128, N % 64, K % 32); rows 16-byte aligned.  Allocates a small
+ * status word; synchronises `stream`. */
+int32_t scs_bf16_gemm(const void *A, int32_t lda, const void *B, int32_t ldb, int32_t M, int32_t N, int32_t K,
+                      float *C, int32_t ldc, int32_t tcgen05, void *stream);
 
 /* Device helpers of the warm-start pipeline (FP32 row-major data):
  * per-column mean and standard deviation; in-place standardisation

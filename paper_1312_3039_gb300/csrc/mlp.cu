@@ -167,6 +167,178 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_nt_kernel(const __nv_bfloat
         }
 }
 
+// ---------------------------------------------------------------------------
+// The same product on the 5th-generation tensor cores (tcgen05): one thread
+// issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) on 128 x 64 tiles whose
+// accumulator lives in tensor memory (64 or 128 columns), operands staged in
+// shared memory by cp.async in the K-major layout with the 128-byte swizzle
+// (8-row atoms of 128-byte rows, 1024 bytes apart).  Six stages; each stage's
+// MMAs signal an mbarrier (tcgen05.commit) that the loader waits on before
+// refilling the stage.  The epilogue reads the accumulator with
+// tcgen05.ld (each warp its 32 TMEM lanes = 32 rows).  Every mbarrier wait is
+// bounded: on time-out the kernel sets *err, waits (bounded) for its own MMAs,
+// frees its tensor memory and returns.
+// ---------------------------------------------------------------------------
+constexpr int TBM = 128, TBN = 64, TBK = 64, kTcThreads = 128;   // TBN: the narrowest tile
+constexpr int kTcStages = 6, kTcAhead = kTcStages - 2;               // prefetch distance 4
+constexpr int kTcStageA = TBM * TBK * 2;                              // bytes
+template <int BNt>
+__host__ __device__ constexpr int tc_stage_b() { return BNt * TBK * 2; }
+template <int BNt>
+__host__ __device__ constexpr int tc_smem() { return kTcStages * (kTcStageA + tc_stage_b<BNt>()) + 1024 + 128; }
+constexpr uint32_t kTcSpin = 1u << 20;
+
+__device__ __forceinline__ uint64_t tc_smem_desc(uint32_t addr) {
+    // K-major, 128-byte swizzle: 8-row atoms of 128-byte rows (64 BF16 of K),
+    // 1024 bytes apart (SBO); LBO unused for this layout (1); fixed 0b001 at
+    // bits 46-48; layout type 2 (SWIZZLE_128B) at bits 61-63.  A K step of
+    // 16 elements moves the start address by 32 bytes inside the atom.
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// byte offset of 16-byte chunk c (0..7) of row r in a 128-byte-swizzled tile
+__device__ __forceinline__ int tc_sw128(int r, int c) { return (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4); }
+// kind::f16 instruction descriptor: D FP32, A and B BF16, both K-major, N, M
+__host__ __device__ constexpr uint32_t tc_idesc(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
+    for (uint32_t it = 0; it < kTcSpin; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// C tile 128 x BNt per CTA; kTcStages shared-memory stages, loads kTcAhead
+// k-blocks ahead: the stage of k-block kt + kTcAhead is refilled once the
+// MMAs of k-block kt - 2 (its previous user) have completed, so those of
+// kt - 1 are still queued while kt issues.
+template <typename Epi, int BNt>
+__global__ void __launch_bounds__(kTcThreads, 1) gemm_nt_tc_kernel(const __nv_bfloat16 *__restrict__ A, int lda,
+                                                                   const __nv_bfloat16 *__restrict__ B, int ldb, int K,
+                                                                   Epi epi, int *err) {
+    constexpr int kStageB = tc_stage_b<BNt>();
+    extern __shared__ __align__(16) unsigned char tc_raw[];
+    const uint32_t raw = smem_u32(tc_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char *gbase = tc_raw + (base - raw);
+    unsigned char *misc = gbase + kTcStages * (kTcStageA + kStageB);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(misc);                  // [kTcStages]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(misc + 8 * kTcStages);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int bm = blockIdx.y * TBM, bn = blockIdx.x * BNt;
+    auto sA = [&](int st) { return base + st * kTcStageA; };
+    auto sB = [&](int st) { return base + kTcStages * kTcStageA + st * kStageB; };
+    auto gA = [&](int st) { return gbase + st * kTcStageA; };
+    auto gB = [&](int st) { return gbase + kTcStages * kTcStageA + st * kStageB; };
+    auto barS = [&](int st) { return smem_u32(&bar[st]); };
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                     "n"(BNt));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        for (int st = 0; st < kTcStages; ++st) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(barS(st)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const uint32_t tmem = *tmem_slot;
+
+    auto load = [&](int stage, int k0) {
+        // A: 128 rows x 8 chunks of 16 bytes; B: BNt rows x 8 chunks; each row
+        // of 64 BF16 is 128 bytes, chunks placed by the 128-byte swizzle
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int ch = tid + i * kTcThreads, r = ch >> 3, kc = ch & 7;
+            cp_async16(gA(stage) + tc_sw128(r, kc), A + (size_t)(bm + r) * lda + k0 + kc * 8);
+        }
+#pragma unroll
+        for (int i = 0; i < BNt / 16; ++i) {
+            const int ch = tid + i * kTcThreads, r = ch >> 3, kc = ch & 7;
+            cp_async16(gB(stage) + tc_sw128(r, kc), B + (size_t)(bn + r) * ldb + k0 + kc * 8);
+        }
+    };
+    const int KT = K / TBK;
+    bool ok = true;
+    int issued = 0;
+#pragma unroll
+    for (int j = 0; j < kTcAhead; ++j) {
+        if (j < KT) load(j, j * TBK);
+        cp_commit();
+    }
+    for (int kt = 0; kt < KT; ++kt) {
+        const int s = kt % kTcStages;
+        const int nk = kt + kTcAhead;
+        if (nk < KT) {
+            // stage nk mod S was last read by the MMAs of k-block kt - 2
+            if (kt >= 2) ok = __syncthreads_and(tc_wait(barS((kt - 2) % kTcStages), ((kt - 2) / kTcStages) & 1)) != 0;
+            if (!ok) break;
+            load(nk % kTcStages, nk * TBK);
+        }
+        cp_commit();
+        cp_wait<kTcAhead>();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            const uint32_t idesc = tc_idesc(TBM, BNt);
+#pragma unroll
+            for (int k = 0; k < TBK / 16; ++k) {
+                const uint64_t ad = tc_smem_desc(sA(s) + k * 32), bd = tc_smem_desc(sB(s) + k * 32);
+                const uint32_t acc = (kt > 0 || k > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                barS(s)));
+        }
+        issued = kt + 1;
+    }
+    cp_wait<0>();            // no copy of ours left in flight
+    // the last commit covers every MMA issued before it (bounded wait, also
+    // after a time-out: the tensor memory is freed only after it)
+    if (issued > 0) {
+        const int last = issued - 1;
+        const bool done = __syncthreads_and(tc_wait(barS(last % kTcStages), (last / kTcStages) & 1)) != 0;
+        ok = ok && done;
+    }
+    if (!ok && tid == 0) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    if (ok) {
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        const int r = bm + warp * 32 + lane;
+#pragma unroll
+        for (int c0 = 0; c0 < BNt; c0 += 16) {
+            uint32_t v[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15}, [%16];\n"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(tmem + lane_base + (uint32_t)c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 16; j += 2) epi(r, bn + c0 + j, __uint_as_float(v[j]), __uint_as_float(v[j + 1]));
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(BNt));
+}
+
 // dst[c][r] = src[r][c] for r < rows, c < cols (BF16; 32 x 32 tiles)
 static __global__ void transpose_kernel(const __nv_bfloat16 *__restrict__ src, int lds, __nv_bfloat16 *__restrict__ dst,
                                         int ldd, int rows, int cols) {
@@ -278,6 +450,41 @@ static __global__ void weights_bf16_kernel(const float *__restrict__ W, int out_
 
 inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
+// C = A B^T through either kernel; the shape must meet the kernel's tiling
+template <typename Epi>
+void launch_gemm(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, int M, int N, int K, Epi epi,
+                 bool tc, int *err, cudaStream_t stream) {
+    if (lda % 8 || ldb % 8 || (reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15))
+        throw CudaError("GEMM operands must have 16-byte aligned rows", SCS_INVALID_INPUT);
+    if (tc) {
+        if (M % TBM || N % TBN || K % TBK)
+            throw CudaError("GEMM shape outside the tcgen05 kernel's tiling", SCS_INVALID_INPUT);
+        if (N % 128 == 0) {
+            static bool attr = false;
+            if (!attr) {
+                SCS_CUDA(cudaFuncSetAttribute(gemm_nt_tc_kernel<Epi, 128>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<128>()));
+                attr = true;
+            }
+            gemm_nt_tc_kernel<Epi, 128><<<dim3(N / 128, M / TBM), kTcThreads, tc_smem<128>(), stream>>>(
+                A, lda, B, ldb, K, epi, err);
+        } else {
+            static bool attr = false;
+            if (!attr) {
+                SCS_CUDA(cudaFuncSetAttribute(gemm_nt_tc_kernel<Epi, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              tc_smem<64>()));
+                attr = true;
+            }
+            gemm_nt_tc_kernel<Epi, 64><<<dim3(N / 64, M / TBM), kTcThreads, tc_smem<64>(), stream>>>(
+                A, lda, B, ldb, K, epi, err);
+        }
+    } else {
+        if (M % BM || N % BN || K % BK) throw CudaError("GEMM shape outside the kernel's tiling", SCS_INVALID_INPUT);
+        gemm_nt_kernel<Epi><<<dim3(N / BN, M / BM), kGemmThreads, 0, stream>>>(A, lda, B, ldb, K, epi);
+    }
+    SCS_CUDA(cudaGetLastError());
+}
+
 class Net {
    public:
     Net(int din, int h, int layers, int dout, int batch, cudaStream_t s) : din_(din), h_(h), L_(layers + 1), dout_(dout),
@@ -315,6 +522,12 @@ class Net {
             layers_.push_back(Y);
         }
         x16_ = alloc<__nv_bfloat16>((size_t)batch * layers_[0].in_p);
+        // tcgen05 products when every padded size meets that kernel's tiling
+        tcgen05_ = batch % TBM == 0 && batch % TBK == 0;
+        for (const Layer &Y : layers_)
+            tcgen05_ = tcgen05_ && Y.in_p % TBK == 0 && Y.out_p % TBN == 0 && Y.out_p % TBK == 0;
+        err_ = alloc<int>(1);
+        SCS_CUDA(cudaMemsetAsync(err_, 0, sizeof(int), stream_));
         part_ = alloc<double>(1024);
         loss_ = alloc<double>(1);
         SCS_CUDA(cudaStreamSynchronize(stream_));
@@ -441,10 +654,7 @@ class Net {
 
     template <typename Epi>
     void gemm(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, int M, int N, int K, Epi epi) {
-        if (M % BM || N % BN || K % BK || lda % 8 || ldb % 8 || (reinterpret_cast<uintptr_t>(A) & 15) ||
-            (reinterpret_cast<uintptr_t>(B) & 15))
-            throw CudaError("GEMM shape outside the kernel's tiling", SCS_INVALID_INPUT);
-        gemm_nt_kernel<Epi><<<dim3(N / BN, M / BM), kGemmThreads, 0, stream_>>>(A, lda, B, ldb, K, epi);
+        launch_gemm(A, lda, B, ldb, M, N, K, epi, tcgen05_, err_, stream_);
     }
     void transpose(const __nv_bfloat16 *src, int lds, __nv_bfloat16 *dst, int ldd, int rows, int cols) {
         transpose_kernel<<<dim3((cols + 31) / 32, (rows + 31) / 32), dim3(32, 8), 0, stream_>>>(src, lds, dst, ldd,
@@ -470,6 +680,8 @@ class Net {
 
     int din_, h_, L_, dout_, batch_;
     int step_ = 0;
+    bool tcgen05_ = false;   // products on tcgen05 (else mma.sync); chosen at construction
+    int *err_ = nullptr;     // set by a tcgen05 product whose wait timed out
     cudaStream_t stream_;
     std::vector<Layer> layers_;
     std::vector<void *> allocs_;
@@ -624,6 +836,48 @@ int32_t scs_mlp_train_step(scs_mlp *w, const float *x, const float *t, float lr,
         w->net->adam(lr);
         if (loss) *loss = static_cast<float>(w->net->loss_host());
         return 0;
+    });
+}
+
+int32_t scs_mlp_set_tensor_path(scs_mlp *w, int32_t tcgen05) {
+    if (!w || !w->net) return SCS_INVALID_INPUT;
+    if (tcgen05) {
+        for (const auto &Y : w->net->layers_)
+            if (Y.in_p % scs::mlp::TBK || Y.out_p % scs::mlp::TBN || w->net->batch_ % scs::mlp::TBM ||
+                Y.out_p % scs::mlp::TBK || w->net->batch_ % scs::mlp::TBK)
+                return SCS_UNSUPPORTED;
+    }
+    w->net->tcgen05_ = tcgen05 != 0;
+    return 0;
+}
+
+int32_t scs_mlp_error(scs_mlp *w) {
+    if (!w || !w->net) return SCS_INVALID_INPUT;
+    int h = 0;
+    if (cudaMemcpy(&h, w->net->err_, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SCS_DEVICE_ERROR;
+    return h ? SCS_DEVICE_ERROR : 0;
+}
+
+int32_t scs_bf16_gemm(const void *A, int32_t lda, const void *B, int32_t ldb, int32_t M, int32_t N, int32_t K,
+                      float *C, int32_t ldc, int32_t tcgen05, void *stream) {
+    if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0 || ldc < N || ldc % 2) return SCS_INVALID_INPUT;
+    return mlp_guarded([&]() -> int32_t {
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        int *err = nullptr;
+        SCS_CUDA(cudaMalloc(&err, sizeof(int)));
+        int h = 0;
+        try {
+            SCS_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+            scs::mlp::launch_gemm(static_cast<const __nv_bfloat16 *>(A), lda, static_cast<const __nv_bfloat16 *>(B),
+                                  ldb, M, N, K, scs::mlp::EpiPlain{C, ldc}, tcgen05 != 0, err, s);
+            SCS_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+            SCS_CUDA(cudaStreamSynchronize(s));
+        } catch (...) {
+            cudaFree(err);
+            throw;
+        }
+        cudaFree(err);
+        return h ? SCS_DEVICE_ERROR : 0;
     });
 }
 

@@ -157,6 +157,12 @@ def lib():
         L.scs_mlp_train_step.restype = I32
         L.scs_mlp_destroy.argtypes = [P]
         L.scs_mlp_destroy.restype = None
+        L.scs_mlp_set_tensor_path.argtypes = [P, I32]
+        L.scs_mlp_set_tensor_path.restype = I32
+        L.scs_mlp_error.argtypes = [P]
+        L.scs_mlp_error.restype = I32
+        L.scs_bf16_gemm.argtypes = [V, I32, V, I32, I32, I32, I32, V, I32, I32, V]
+        L.scs_bf16_gemm.restype = I32
         L.scs_column_stats.argtypes = [V, C.c_int64, I32, V, V, V]
         L.scs_column_stats.restype = I32
         L.scs_standardize.argtypes = [V, C.c_int64, I32, V, V, V]
@@ -566,6 +572,13 @@ class MLP:
 
     def param_count(self):
         return int(lib().scs_mlp_param_count(self._w))
+
+    def set_tensor_path(self, tcgen05):
+        """True: tcgen05 products (the default when the sizes allow); False: mma.sync."""
+        return _rc(lib().scs_mlp_set_tensor_path(self._w, 1 if tcgen05 else 0))
+
+    def error(self):
+        return lib().scs_mlp_error(self._w)
 
     def set_params(self, flat):
         flat = np.ascontiguousarray(flat, dtype=np.float32)

@@ -1,0 +1,61 @@
+"""The network's product on tcgen05 (tensor-memory accumulators, one
+issuing thread, mbarrier-tracked completion) against the mma.sync kernel and
+an FP64 reference of the same BF16 operands, on one tile, a K loop of many
+stages, several tiles in M and N and the network's widest K; then the whole
+network's gradients on the tcgen05 path against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    from paper_1312_3039_gb300 import build, scs
+    build.build()
+    return torch, scs
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 64, 64), (128, 64, 512), (384, 192, 256), (256, 512, 4480)])
+def test_tcgen05_product(env, M, N, K):
+    torch, scs = env
+    rng = np.random.default_rng(M + N + K)
+    A = torch.tensor(rng.standard_normal((M, K)), dtype=torch.bfloat16, device="cuda")
+    B = torch.tensor(rng.standard_normal((N, K)), dtype=torch.bfloat16, device="cuda")
+    ref = A.double().cpu().numpy() @ B.double().cpu().numpy().T
+    out = {}
+    for tc in (0, 1):
+        C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+        rc = scs.lib().scs_bf16_gemm(A.data_ptr(), K, B.data_ptr(), K, M, N, K, C.data_ptr(), N, tc, None)
+        assert rc == 0, (tc, rc, scs.last_error())
+        out[tc] = C.cpu().numpy().astype(np.float64)
+    scale = np.abs(ref).max()
+    np.testing.assert_allclose(out[1], ref, rtol=0, atol=1e-5 * scale * np.sqrt(K / 64))
+    np.testing.assert_allclose(out[1], out[0], rtol=0, atol=1e-5 * scale * np.sqrt(K / 64))
+
+
+def test_network_gradients_on_tcgen05(env):
+    torch, scs = env
+    rng = np.random.default_rng(7)
+    sizes = [64, 512, 512, 512, 4406]
+    B = 128
+    params = omlp.init_params(rng, sizes)
+    params = [(W, rng.standard_normal(b.shape) * 0.05) for W, b in params]
+    X = rng.standard_normal((B, 64))
+    T = rng.standard_normal((B, 4406))
+    pr = [(omlp.bf16_round(W), b.astype(np.float32).astype(np.float64)) for W, b in params]
+    loss_ref, g_ref = omlp.loss_and_grads(pr, omlp.bf16_round(X.astype(np.float32)), T.astype(np.float32))
+    with scs.MLP(64, 512, 3, 4406, B) as net:
+        net.set_params(scs.pack_params(params))
+        assert scs.lib().scs_mlp_set_tensor_path(net._w, 1) == 0
+        dx = torch.tensor(X, dtype=torch.float32, device="cuda")
+        dt = torch.tensor(T, dtype=torch.float32, device="cuda")
+        loss, g = net.gradients(dx.data_ptr(), dt.data_ptr())
+        assert scs.lib().scs_mlp_error(net._w) == 0
+    assert abs(loss - loss_ref) <= 2e-2 * loss_ref
+    for li, ((gW, gb), (rW, rb)) in enumerate(zip(scs.unpack_params(g.astype(np.float64), sizes), g_ref)):
+        e = np.linalg.norm(gW - rW) / np.linalg.norm(rW)
+        assert e < 5e-2, (li, e)
