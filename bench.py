@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-1e-4 solve")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--solve-seconds", type=float, default=30.0, help="time limit of the time-to-1e-4 leg")
+    ap.add_argument("--solve-seconds", type=float, default=90.0, help="time limit of the time-to-1e-4 leg")
+    ap.add_argument("--solve-iters", type=int, default=100000, help="iteration limit of the time-to-1e-4 leg")
     return ap.parse_args()
 
 
@@ -344,7 +345,7 @@ def run_gb300(args):
     def sum_over_ranks(x):
         return reduce_scalar(x, "sum")
 
-    S = scs.Solver(P.A, P.b, P.c, P.cone, time_limit_s=args.solve_seconds, **common)
+    S = scs.Solver(P.A, P.b, P.c, P.cone, time_limit_s=args.solve_seconds, max_iters=args.solve_iters, **common)
     # warm-up iterations, then exactly `steps` timed iterations
     S.iterate(args.warmup)
     torch.cuda.synchronize()
