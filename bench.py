@@ -706,6 +706,13 @@ def run_lasso_warm(args):
     clk = clocks.stop()
     ci = np.array([f["iters"] for f in cold])
     wi = np.array([f["iters"] for f in warm])
+    # family solver: the three FP32 products of an iteration, 2 (nm + n^2 + mn)
+    # flops per member, counted for each member's own iterations (members that
+    # finished early are dropped from the products at the next compaction)
+    nn, mm = fam.A.shape[1], fam.A.shape[0]
+    fam_flops = float(ci.sum()) * 2.0 * (2.0 * nn * mm + nn * nn)
+    fam_tflops = fam_flops / (cold_s / args.steps) / 1e12
+    fp32_peak = fp32_alu_peak_tflops(clk.get("sm_mhz"))
     # plain solver (scs_solve per member, indirect CG), cold and warm-started
     # from the network's prediction mapped to the caller's units
     pick = list(range(0, nheld, max(1, nheld // args.plain_sample)))
@@ -747,6 +754,10 @@ def run_lasso_warm(args):
         "training": {"members": ntrain, "generation_s": gen_s, "generation_wall_s": gen_wall, "fit_s": fit_s,
                      "epochs": args.epochs, "steps": steps, "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
                      "train_tflops": flop_step * steps / fit_s / 1e12},
+        "roofline": {"bound": "alu", "kernel": "family solver iteration (three FP32 GEMMs over the members)",
+                     "achieved": fam_tflops, "peak": fp32_peak, "unit": "TFLOP/s", "frac": fam_tflops / fp32_peak,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x sampled SM clock",
+                     "traffic": None},
         "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk,
     }
     print(json.dumps(line), flush=True)
