@@ -365,9 +365,13 @@ class Engine : public EngineBase {
         }
         K.q_off = upload(qoff);
         K.q_len = upload(P.q);
-        K.nb_elem = (n_ + K.z + K.l + kBlock - 1) / kBlock;
-        if (K.nb_elem < 1) K.nb_elem = 1;
-        K.nb_soc = (K.nq + kWarps - 1) / kWarps;
+        // element and SOC ranges: at most one wave of resident CTAs each
+        int occ_p = 0;
+        SCS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, relax_project_kernel<T>, kBlock, 0));
+        const int64_t wave = static_cast<int64_t>(sms_) * std::max(1, occ_p);
+        K.nb_elem = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(
+            wave, (static_cast<int64_t>(n_) + K.z + K.l + kBlock - 1) / kBlock)));
+        K.nb_soc = static_cast<int>(std::min<int64_t>(wave, (K.nq + kWarps - 1) / kWarps));
         K.nb_exp = (K.ep + kExpPerCta - 1) / kExpPerCta;
         K.npsd = static_cast<int>(P.s.size());
         if (K.npsd) {

@@ -242,10 +242,16 @@ __global__ void __launch_bounds__(kBlock) smw_kernel(int n, int m, const T *__re
 // ---------------------------------------------------------------------------
 // K7: relax, project onto C = R^n x K* x R+, update v  (one launch)
 //   block ranges: [0, nb_exp)       exponential triples, kExpPerCta per CTA
-//                                   (long FP64 chains: started first, spread
-//                                   over many SMs)
-//                 [.., + nb_soc)    one warp per second-order block
-//                 [.., + nb_elem)   x-part, zero rows, nonnegative rows, tau
+//                                   (long dependent chains: started first,
+//                                   spread over many SMs)
+//                 [.., + nb_soc)    second-order blocks, one warp per block,
+//                                   warps striding over the blocks
+//                 [.., + nb_elem)   x-part, zero rows, nonnegative rows, tau:
+//                                   threads striding over the rows, four rows'
+//                                   loads issued before their stores
+//   nb_soc and nb_elem are capped at one wave of resident CTAs: one CTA per
+//   256 rows made ~1e4 CTAs whose partial sums, arrival atomics and final
+//   reduction cost more than the streaming itself.
 // ---------------------------------------------------------------------------
 constexpr int kExpPerCta = 64;
 
@@ -313,8 +319,7 @@ __global__ void __launch_bounds__(kBlock) relax_project_kernel(ProjArgs<T> a, Co
         }
     } else if (bid - K.nb_exp < K.nb_soc) {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int blk = (bid - K.nb_exp) * kWarps + warp;
-        if (blk < K.nq) {
+        for (int blk = (bid - K.nb_exp) * kWarps + warp; blk < K.nq; blk += K.nb_soc * kWarps) {
             const int off = a.n + K.q_off[blk];
             const int len = K.q_len[blk];
             // t = u_bar - v over the block; projection onto SOC (self-dual)
@@ -345,20 +350,35 @@ __global__ void __launch_bounds__(kBlock) relax_project_kernel(ProjArgs<T> a, Co
     } else {
         const int ebid = bid - K.nb_exp - K.nb_soc;
         const int nlin = a.n + K.z + K.l;
-        const int idx = ebid * kBlock + threadIdx.x;
-        if (idx < nlin) {
-            const T ub = relaxed(a, idx, gamma, alpha);
-            const T uo = a.u[idx];
-            if (idx < a.n) {
-                a.u[idx] = ub;                       // R^n: identity, v_x stays 0
-                dd += (ub - uo) * (ub - uo);
-            } else {
-                const T vo = a.v[idx];
-                const T t = ub - vo;
-                const T up = (idx < a.n + K.z) ? t : (t > T(0) ? t : T(0));   // K* of {0} is R
-                a.u[idx] = up;
-                a.v[idx] = up - t;
-                dd += (up - uo) * (up - uo) + (up - t - vo) * (up - t - vo);
+        const int stride = K.nb_elem * kBlock;
+        constexpr int kU = 4;
+        for (int64_t base = ebid * kBlock + threadIdx.x; base < nlin; base += static_cast<int64_t>(kU) * stride) {
+            T ub[kU], uo[kU], vo[kU];
+#pragma unroll
+            for (int j = 0; j < kU; ++j) {
+                const int64_t i64 = base + static_cast<int64_t>(j) * stride;
+                if (i64 < nlin) {
+                    const int idx = static_cast<int>(i64);
+                    ub[j] = relaxed(a, idx, gamma, alpha);
+                    uo[j] = a.u[idx];
+                    vo[j] = idx < a.n ? T(0) : a.v[idx];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kU; ++j) {
+                const int64_t i64 = base + static_cast<int64_t>(j) * stride;
+                if (i64 >= nlin) break;
+                const int idx = static_cast<int>(i64);
+                if (idx < a.n) {
+                    a.u[idx] = ub[j];                    // R^n: identity, v_x stays 0
+                    dd += (ub[j] - uo[j]) * (ub[j] - uo[j]);
+                } else {
+                    const T t = ub[j] - vo[j];
+                    const T up = (idx < a.n + K.z) ? t : (t > T(0) ? t : T(0));   // K* of {0} is R
+                    a.u[idx] = up;
+                    a.v[idx] = up - t;
+                    dd += (up - uo[j]) * (up - uo[j]) + (up - t - vo[j]) * (up - t - vo[j]);
+                }
             }
         }
         if (ebid == 0 && threadIdx.x == 0) {
