@@ -114,7 +114,7 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NV], ReduceBuf rb, int site
 // grid-sum call sites (each has its own arrival counter)
 enum Site : int {
     kSiteAInit = 0, kSiteAtInit, kSiteACG, kSiteAtCG, kSiteCGUpd, kSiteSmw,
-    kSiteChkA, kSiteChkAt, kSiteProj, kSiteMisc, kSiteMisc2, kSiteCount
+    kSiteChkA, kSiteChkAt, kSiteProj, kSiteMisc, kSiteMisc2, kSiteAz, kSiteCount
 };
 
 }  // namespace scs

@@ -108,7 +108,7 @@ class Engine : public EngineBase {
             for (auto &e : ev_) SCS_CUDA(cudaEventCreate(&e));
         }
         for (int it = 0; it < iters; ++it) {
-            timed(0, [&] { launch_K1(); });
+            launch_K1();                  // kind 0 times the CG products q = A p only
             timed(1, [&] { launch_K2(CondHandle{0, 0}); });
             for (int c = 0; c < st_.cg_max_iters; ++c) {
                 timed(0, [&] { launch_K3(); });
@@ -325,6 +325,7 @@ class Engine : public EngineBase {
         diag_ = dalloc<T>(n_);
         q_ = dalloc<T>(m_);
         yacc_ = dalloc<T>(m_);
+        az_ = dalloc<T>(m_);
         double *tmp_m = dalloc<double>(m_), *tmp_n = dalloc<double>(n_);
         double *red_out = dalloc<double>(4);
 
@@ -642,10 +643,13 @@ class Engine : public EngineBase {
         if (grid > rb_cap_ || grid < 1) throw CudaError("reduction grid exceeds its buffer", SCS_DEVICE_ERROR);
     }
 
+    // K1 (the product, every kAzEvery-th iteration) and K1' (from the carried
+    // A z): both are launched, the one whose iteration it is not returns at once
     void launch_K1() {
         guard(A_.grid());
-        EpiAInit<T> e{u_, v_, bT_, yacc_, S_, n_, N_, 0.0};
+        EpiAInit<T> e{u_, v_, bT_, yacc_, az_, S_, n_, N_, 0.0};
         spmv_kernel<T, T, T, EpiAInit<T>><<<A_.grid(), kBlock, 0, cur_>>>(A_, z_, e, rb_);
+        yacc_init_kernel<T><<<grid_for(m_), kBlock, 0, cur_>>>(n_, m_, N_, u_, v_, bT_, az_, yacc_, S_, rb_);
     }
     void launch_K2(CondHandle h) {
         guard(At_.grid());
@@ -663,8 +667,8 @@ class Engine : public EngineBase {
         spmv_kernel<T, T, T, EpiAtCG<T>><<<At_.grid(), kBlock, 0, cur_>>>(At_, q_, e, rb_);
     }
     void launch_K5(CondHandle h) {
-        cg_update_kernel<T><<<grid_for(std::max(n_, m_)), kBlock, 0, cur_>>>(n_, m_, q_, yacc_, r_, diag_, pv_, S_,
-                                                                              h, rb_);
+        cg_update_kernel<T><<<grid_for(std::max(n_, m_)), kBlock, 0, cur_>>>(n_, m_, q_, yacc_, az_, r_, diag_, pv_,
+                                                                              S_, h, rb_);
     }
     void launch_K6() {
         smw_kernel<T><<<grid_for(n_ + m_), kBlock, 0, cur_>>>(n_, m_, cT_, bT_, z_, yacc_, S_, rb_);
@@ -792,6 +796,7 @@ class Engine : public EngineBase {
     double *b_ = nullptr, *c_ = nullptr, *D_ = nullptr, *E_ = nullptr;
     double *p_ = nullptr, *ax_ = nullptr, *out_ = nullptr;
     T *z_ = nullptr, *r_ = nullptr, *pv_ = nullptr, *diag_ = nullptr, *q_ = nullptr, *yacc_ = nullptr;
+    T *az_ = nullptr;      // A^ z_x carried between iterations (kernels.cuh, K1')
     std::vector<double> Dh_, Eh_;
     double sigma_ = 1.0, rho_ = 1.0;
     cudaGraph_t graph_ = nullptr;

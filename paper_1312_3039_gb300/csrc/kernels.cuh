@@ -14,14 +14,22 @@
 //   u+     = Pi_C(u_bar - v),  v+ = v - u_bar + u+
 //
 // Arrangement on the device (2 + 2K sparse products per iteration for K CG
-// steps, the count of Table 5):
-//   K1  SpMV A   : y_acc = r_y + A z_prev                    (r_y formed per row)
+// steps, the count of Table 5, on every kAzEvery-th iteration; 1 + 2K on the
+// others):
+//   K1  SpMV A   : y_acc = r_y + A z_prev, az = A z_prev     (r_y formed per row)
+//                  on iterations k = 0 mod kAzEvery; on the others
+//   K1' elementwise: y_acc = r_y + az, where az = A z_prev is carried from the
+//                  previous iteration (K5 adds alpha q to it whenever z moves
+//                  by alpha p, so az = A z holds in exact arithmetic; the
+//                  product every kAzEvery iterations bounds the drift of the
+//                  carried sum to a few rounding errors)
 //   K2  SpMV A^T : r0 = r_x - z_prev - A^T y_acc  (= t - (I + A^T A) z_prev),
 //                  p0 = r0 / diag, CG dots, CG tolerance zeta^k
 //   CG step (while not converged):
 //   K3  SpMV A   : q = A p,  alpha = r.s / (p.p + q.q)   (p^T (I + A^T A) p)
 //   K4  SpMV A^T : z += alpha p,  r -= alpha (p + A^T q),  new r.s, ||r||
-//   K5  update   : y_acc += alpha q (keeps y_acc = r_y + A z),  p = s + beta p
+//   K5  update   : y_acc += alpha q (keeps y_acc = r_y + A z), az += alpha q,
+//                  p = s + beta p
 //   K6  SMW      : gamma = (c^.z_x + b^.y_acc) / (1 + h^T p)
 //   KP  relax + project + dual update of the PSD blocks (one CTA per block,
 //       Jacobi eigensolver; psd.cuh), when the cone has PSD blocks
@@ -58,28 +66,55 @@ struct CondHandle {
     }
 };
 
+// iterations whose K1 recomputes A z_prev by the sparse product
+constexpr int kAzEvery = 20;
+__device__ __forceinline__ bool az_product(const Scalars *S) { return S->k % kAzEvery == 0; }
+
 // ---------------------------------------------------------------------------
-// K1: rows of A.  y_acc_i = (u_y + v_s - w_tau b^)_i + (A^ z)_i
+// K1: rows of A.  y_acc_i = (u_y + v_s - w_tau b^)_i + (A^ z)_i, az_i = (A^ z)_i
 // ---------------------------------------------------------------------------
 template <typename T>
 struct EpiAInit {
     static constexpr int NV = 1;
     static constexpr int kSite = kSiteAInit;
     const T *u, *v, *b;
-    T *yacc;
+    T *yacc, *az;
     Scalars *S;
     int n, N;
     double wtau;
     struct In { T w, b; };
-    __device__ bool skip() const { return false; }
+    __device__ bool skip() const { return !az_product(S); }
     __device__ void begin() { wtau = static_cast<double>(u[N - 1]) + static_cast<double>(v[N - 1]); }
     __device__ In load(int i) const { return In{u[n + i] + v[n + i], b[i]}; }
     __device__ void row(int i, T s, const In &in, T (&red)[NV]) {
         yacc[i] = in.w - static_cast<T>(wtau) * in.b + s;
+        az[i] = s;
         red[0] += in.w * in.w;
     }
     __device__ void finish(const double (&t)[NV]) { S->ww_y = t[0]; }
 };
+
+// ---------------------------------------------------------------------------
+// K1': the same y_acc from the carried az = A^ z (iterations k != 0 mod kAzEvery)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kBlock) yacc_init_kernel(int n, int m, int N, const T *__restrict__ u,
+                                                           const T *__restrict__ v, const T *__restrict__ b,
+                                                           const T *__restrict__ az, T *__restrict__ yacc,
+                                                           Scalars *S, ReduceBuf rb) {
+    if (az_product(S)) return;
+    const T wtau = static_cast<T>(static_cast<double>(u[N - 1]) + static_cast<double>(v[N - 1]));
+    T acc = 0;
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < m; i += gridDim.x * kBlock) {
+        const T w = u[n + i] + v[n + i];
+        yacc[i] = w - wtau * b[i] + az[i];
+        acc += w * w;
+    }
+    double red[1] = {static_cast<double>(acc)}, tot[1];
+    if (grid_sum<1>(red, rb, kSiteAz, tot)) {
+        if (threadIdx.x == 0) S->ww_y = tot[0];
+    }
+}
 
 // ---------------------------------------------------------------------------
 // K2: rows of A^T.  r0_j = (u_x - w_tau c^)_j - z_j - (A^T y_acc)_j
@@ -191,13 +226,14 @@ struct EpiAtCG {
 };
 
 // ---------------------------------------------------------------------------
-// K5: y_acc += alpha q;  p = r / diag + beta p
+// K5: y_acc += alpha q;  az += alpha q;  p = r / diag + beta p
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kBlock) cg_update_kernel(int n, int m, const T *__restrict__ q,
-                                                           T *__restrict__ yacc, const T *__restrict__ r,
-                                                           const T *__restrict__ diag, T *__restrict__ p,
-                                                           Scalars *S, CondHandle cond, ReduceBuf rb) {
+                                                           T *__restrict__ yacc, T *__restrict__ az,
+                                                           const T *__restrict__ r, const T *__restrict__ diag,
+                                                           T *__restrict__ p, Scalars *S, CondHandle cond,
+                                                           ReduceBuf rb) {
     if (!S->active) return;
     const T alpha = static_cast<T>(S->alpha);
     const T beta = static_cast<T>(S->beta);
@@ -205,7 +241,10 @@ __global__ void __launch_bounds__(kBlock) cg_update_kernel(int n, int m, const T
     T acc = 0;
     const int total = n > m ? n : m;
     for (int i = blockIdx.x * kBlock + threadIdx.x; i < total; i += gridDim.x * kBlock) {
-        if (i < m) yacc[i] = yacc[i] + alpha * q[i];
+        if (i < m) {
+            yacc[i] = yacc[i] + alpha * q[i];
+            az[i] = az[i] + alpha * q[i];
+        }
         if (i < n && !done) {
             const T pj = r[i] / diag[i] + beta * p[i];
             p[i] = pj;
