@@ -602,13 +602,14 @@ def run_batch(args):
         plain_s += time.perf_counter() - t1
         plain_status.append(int(r[0] == infos[i]["status"] and r[4]["iters"] == infos[i]["iters"]))
     plain_total = plain_s / len(pick) * count
-    # algorithmic bytes of the products: per program (2 + 2 CG) SpMVs per
-    # iteration, each streaming A^'s CSR (8 B per nonzero + 4 B per row) and
-    # gathering its input once
+    # algorithmic bytes of the products: per program, per iteration one A^T
+    # product and 2 per CG step, and the product A z on every 20th iteration
+    # (the first of the solve included); each streams A^'s CSR (8 B per
+    # nonzero + 4 B per row) and gathers its input once
     byt = 0.0
     for i, P in enumerate(progs):
-        per = 8.0 * P.A.nnz + 4.0 * (P.m + P.n) + 4.0 * (P.n + P.m)
-        byt += per * (2 * iters[i] + 2 * cg[i]) / 2.0
+        per = (8.0 * P.A.nnz + 4.0 * (P.m + P.n) + 4.0 * (P.n + P.m)) / 2.0
+        byt += per * (iters[i] + 2 * cg[i] + (iters[i] + 19) // 20)
     peak, peak_src = measured_hbm_peak()
     achieved = byt * args.steps / (ms / 1e3) / 1e9
     cpu = None

@@ -177,7 +177,7 @@ __device__ __forceinline__ void team_rownorm(const int32_t *__restrict__ rp, con
 template <typename T>
 __host__ __device__ inline size_t team_bytes(int n, int m) {
     const size_t N = (size_t)n + m + 1;
-    const size_t solve = sizeof(T) * (2 * N + 6 * (size_t)n + 4 * (size_t)m);
+    const size_t solve = sizeof(T) * (2 * N + 6 * (size_t)n + 5 * (size_t)m);
     const size_t setup = sizeof(double) * 2 * ((size_t)n + m) + sizeof(T) * (5 * (size_t)n + 3 * (size_t)m);
     size_t b = solve > setup ? solve : setup;
     return (b + 15) & ~size_t(15);
@@ -194,11 +194,12 @@ __device__ __forceinline__ int next_job(int *queue, int *slot) {
 // ---------------------------------------------------------------------------
 // one program's CG on (I + A^T A) z = r_x - A^T r_y, warm-started from z,
 // the subspace step of Sec. 4.1.  On entry ya = r_y + A z and r, p, rz, rr,
-// pp are those of the starting point; ya is kept equal to r_y + A z.
+// pp are those of the starting point; ya is kept equal to r_y + A z, and az
+// (when given) equal to A z.
 // ---------------------------------------------------------------------------
 template <typename T, int NT>
 __device__ __forceinline__ int team_cg(const Dev<T> &B, const Meta &M, Team<NT> &tm, T *z, T *r, T *p, T *q, T *ya,
-                                       const T *dg, double rz, double rr, double pp, double tol, int cg_max) {
+                                       T *az, const T *dg, double rz, double rr, double pp, double tol, int cg_max) {
     const int n = M.n, m = M.m;
     int it = 0;
     bool done = !(sqrt(rr) > tol) || cg_max <= 0;
@@ -221,6 +222,8 @@ __device__ __forceinline__ int team_cg(const Dev<T> &B, const Meta &M, Team<NT> 
             acc1 += rj * rj;
         });
         for (int i = threadIdx.x; i < m; i += NT) ya[i] += a * q[i];
+        if (az)
+            for (int i = threadIdx.x; i < m; i += NT) az[i] += a * q[i];
         r4[0] = static_cast<double>(acc0);
         r4[1] = static_cast<double>(acc1);
         tm.sum(r4);
@@ -410,7 +413,7 @@ __device__ __forceinline__ void setup_program(const Dev<T> &B, int id, unsigned 
     tm.sum(r2);
     const double tol = (sizeof(T) == 8 ? 1e-14 : 1e-7) * sqrt(r2[3]);
     const int cap = B.cg_max * 10 > 500 ? B.cg_max * 10 : 500;
-    team_cg<T, NT>(B, M, tm, tz, tr, tp, tq, tya, tdg, r2[0], r2[1], r2[2], tol, cap);
+    team_cg<T, NT>(B, M, tm, tz, tr, tp, tq, tya, nullptr, tdg, r2[0], r2[1], r2[2], tol, cap);
     double hp[1] = {0.0};
     for (int j = threadIdx.x; j < n; j += NT) {
         B.pM[M.xo + M.yo + j] = tz[j];
@@ -452,7 +455,7 @@ __device__ __forceinline__ void solve_program(const Dev<T> &B, int id, unsigned 
     const int n = M.n, m = M.m, N = n + m + 1;
     T *u = reinterpret_cast<T *>(smem);
     T *v = u + N, *z = v + N, *r = z + n, *p = r + n, *dg = p + n, *ch = dg + n, *px = ch + n;
-    T *q = px + n, *ya = q + m, *bh = ya + m, *py = bh + m;
+    T *q = px + n, *ya = q + m, *bh = ya + m, *py = bh + m, *az = py + m;
     const T *pMg = B.pM + M.xo + M.yo;
     // state
     const bool cold = mode == 0 && !B.warm[id];
@@ -485,15 +488,26 @@ __device__ __forceinline__ void solve_program(const Dev<T> &B, int id, unsigned 
     __syncthreads();
     const int cap = mode == 1 ? iters : B.max_iters;
     while (it < cap) {
-        // ---- K1: ya = r_y + A^ z  (r_y = u_y + v_s - w_tau b^)
+        // ---- K1: ya = r_y + A^ z  (r_y = u_y + v_s - w_tau b^); the product
+        //      A^ z on the first iteration of the call and every kAzEvery-th,
+        //      the carried az = A^ z on the others
         const double wtau = static_cast<double>(u[N - 1]) + static_cast<double>(v[N - 1]);
         const T wt = static_cast<T>(wtau);
         T acc_wy = T(0);
-        team_spmv<NT, T>(B.a_rp, B.a_rid, B.a_col, B.a_val, M.a_row0, m, M.a_nlong, z, [&](int i, T s) {
-            const T w = u[n + i] + v[n + i];
-            ya[i] = w - wt * bh[i] + s;
-            acc_wy += w * w;
-        });
+        if (it % kAzEvery == 0) {
+            team_spmv<NT, T>(B.a_rp, B.a_rid, B.a_col, B.a_val, M.a_row0, m, M.a_nlong, z, [&](int i, T s) {
+                const T w = u[n + i] + v[n + i];
+                ya[i] = w - wt * bh[i] + s;
+                az[i] = s;
+                acc_wy += w * w;
+            });
+        } else {
+            for (int i = threadIdx.x; i < m; i += NT) {
+                const T w = u[n + i] + v[n + i];
+                ya[i] = w - wt * bh[i] + az[i];
+                acc_wy += w * w;
+            }
+        }
         __syncthreads();
         // ---- K2: r = r_x - z - A^T ya, p = r / diag
         T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
@@ -517,7 +531,7 @@ __device__ __forceinline__ void solve_program(const Dev<T> &B, int id, unsigned 
         if (B.cg_adapt > 0.0) tol = fmin(tol, B.cg_adapt * dstep);
         if (!isfinite(tol)) tol = 0.0;
         tol = fmax(tol, B.cg_tol_rel * sqrt(ww));
-        cg_total += team_cg<T, NT>(B, M, tm, z, r, p, q, ya, dg, r2[0], r2[1], r2[2], tol, B.cg_max);
+        cg_total += team_cg<T, NT>(B, M, tm, z, r, p, q, ya, az, dg, r2[0], r2[1], r2[2], tol, B.cg_max);
         // ---- K6: gamma = h^T z / (1 + h^T p)
         T ag = T(0);
         for (int j = threadIdx.x; j < n; j += NT) ag += ch[j] * z[j];

@@ -111,6 +111,11 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NV], ReduceBuf rb, int site
     return true;
 }
 
+// The warm-start product A^ z_prev of the CG runs on every kAzEvery-th ADMM
+// iteration; the iterations between carry A^ z_x forward from the CG's own
+// A^ p products (kernels.cuh header).
+constexpr int kAzEvery = 20;
+
 // grid-sum call sites (each has its own arrival counter)
 enum Site : int {
     kSiteAInit = 0, kSiteAtInit, kSiteACG, kSiteAtCG, kSiteCGUpd, kSiteSmw,

@@ -67,7 +67,6 @@ struct CondHandle {
 };
 
 // iterations whose K1 recomputes A z_prev by the sparse product
-constexpr int kAzEvery = 20;
 __device__ __forceinline__ bool az_product(const Scalars *S) { return S->k % kAzEvery == 0; }
 
 // ---------------------------------------------------------------------------
