@@ -111,9 +111,12 @@ typedef struct {
     int32_t status;
     int32_t iters;                        /* ADMM iterations done                        */
     int32_t cg_iters;                     /* CG steps over the solve                     */
-    int32_t matvecs;                      /* 2 * iters + 2 * cg_iters: one A and one A^T
-                                             product per iteration outside CG, two per
-                                             CG step (Table 5's count)                  */
+    int32_t matvecs;                      /* iters + ceil(iters / 20) + 2 * cg_iters: one
+                                             A^T product per iteration outside CG, the A
+                                             product of the CG's warm start on every 20th
+                                             iteration (A z is carried in between), two
+                                             per CG step (Table 5 counts 2 per iteration
+                                             outside CG)                                */
     double pobj, dobj;                    /* c^T x and -b^T y of the returned point      */
     double res_pri, res_dual, gap;        /* unscaled ||Ax+s-b||, ||A^T y+c||, |c^T x+b^T y| */
     double tau, kappa;

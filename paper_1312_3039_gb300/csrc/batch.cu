@@ -489,12 +489,13 @@ __device__ __forceinline__ void solve_program(const Dev<T> &B, int id, unsigned 
     const int cap = mode == 1 ? iters : B.max_iters;
     while (it < cap) {
         // ---- K1: ya = r_y + A^ z  (r_y = u_y + v_s - w_tau b^); the product
-        //      A^ z on the first iteration of the call and every kAzEvery-th,
-        //      the carried az = A^ z on the others
+        //      A^ z on iterations k = 0 mod kAzEvery and on the first of the
+        //      call (az is not kept between calls), the carried az = A^ z on
+        //      the others
         const double wtau = static_cast<double>(u[N - 1]) + static_cast<double>(v[N - 1]);
         const T wt = static_cast<T>(wtau);
         T acc_wy = T(0);
-        if (it % kAzEvery == 0) {
+        if (it == 0 || k % kAzEvery == 0) {
             team_spmv<NT, T>(B.a_rp, B.a_rid, B.a_col, B.a_val, M.a_row0, m, M.a_nlong, z, [&](int i, T s) {
                 const T w = u[n + i] + v[n + i];
                 ya[i] = w - wt * bh[i] + s;
@@ -710,7 +711,7 @@ __device__ __forceinline__ void solve_program(const Dev<T> &B, int id, unsigned 
         f.status = status;
         f.iters = k;
         f.cg_iters = cg_total;
-        f.matvecs = 2 * k + 2 * cg_total;
+        f.matvecs = k + (k + kAzEvery - 1) / kAzEvery + 2 * cg_total;
         f.tau = last[6];
         f.kappa = last[7];
         f.res_pri = last[8];

@@ -224,7 +224,7 @@ class Engine : public EngineBase {
             info->status = status;
             info->iters = Sh_->k;
             info->cg_iters = static_cast<int32_t>(Sh_->cg_total);
-            info->matvecs = 2 * Sh_->k + 2 * static_cast<int32_t>(Sh_->cg_total);
+            info->matvecs = Sh_->k + (Sh_->k + kAzEvery - 1) / kAzEvery + 2 * static_cast<int32_t>(Sh_->cg_total);
             info->tau = Sh_->tau;
             info->kappa = Sh_->kappa;
             info->res_pri = Sh_->res_pri;
@@ -300,12 +300,15 @@ class Engine : public EngineBase {
         double *a_val64 = upload(LA.val);
         int32_t *at_rowptr = upload(LAt.rowptr), *at_col = upload(LAt.col), *at_rowid = upload(LAt.rowid);
         double *at_val64 = upload(LAt.val);
+        const int32_t *a_tiles = upload(LA.tile_row), *at_tiles = upload(LAt.tile_row);
         S_ = dalloc<Scalars>(1);
         SCS_CUDA(cudaMemsetAsync(S_, 0, sizeof(Scalars), stream_));
         auto mkcsr = [&](auto *vals, const int32_t *rp, const int32_t *cl, const int32_t *rid,
                          const SpmvLayout<double> &lay, int rows) {
             using V = std::remove_cv_t<std::remove_pointer_t<decltype(vals)>>;
-            return Csr<V>{rp, cl, vals, rid, rows, lay.reg};
+            const bool tiled = !lay.tile_row.empty();
+            return Csr<V>{rp, cl, vals, rid, rows, lay.reg, tiled ? (&lay == &LA ? a_tiles : at_tiles) : nullptr,
+                          tiled ? static_cast<int32_t>(lay.tile_row.size()) - 1 : 0};
         };
         SCS_CUDA(cudaStreamSynchronize(stream_));     // host layouts are released below
 

@@ -10,14 +10,20 @@
 // Layout (setup, host): rows are stored grouped by length class (1, 2, 3-4,
 // 5-8, ...; original order kept inside a class; `rowid` maps a stored row
 // back to its matrix row, which is where the epilogue writes).  Each run of
-// classes forms a region whose rows get groups of L lanes: L = 1 up to 4
-// nonzeros, 2 up to 8, 4 up to 16, 8 up to 32, a warp up to kWarpRow and a
-// whole CTA beyond, so every lane holds a few nonzeros of one row and the
-// group's loads of a row are contiguous.  One launch covers all regions
-// (grid-stride loops whose trip counts are uniform per warp; region grids
-// sized by their nonzeros).  Every thread accumulates the epilogue's
-// reduction values over all its rows; each CTA joins one grid_sum at the
-// end, whose last CTA runs the epilogue's finisher.
+// classes forms a region:
+//   rows of up to 8 nonzeros: groups of L lanes per row (L = 1 up to 4
+//     nonzeros, 2 up to 8), every lane holding a few nonzeros of one row;
+//   rows of 9..256 nonzeros: tiles of whole rows with at most kTileNnz
+//     nonzeros; a CTA gathers a tile's products into shared memory with
+//     coalesced index loads (kTileNnz / kBlock independent gathers per
+//     thread, one dependent chain per tile), then one thread per row sums
+//     its products in order;
+//   longer rows: a warp per row up to kWarpRow nonzeros, a CTA beyond.
+// One launch covers all regions (grid-stride loops whose trip counts are
+// uniform per warp or per CTA; region grids sized by their work).  Every
+// thread accumulates the epilogue's reduction values over all its rows;
+// each CTA joins one grid_sum at the end, whose last CTA runs the
+// epilogue's finisher.
 #pragma once
 
 #include <stdint.h>
@@ -34,10 +40,15 @@ constexpr int kMaxRegions = 10;
 constexpr int kWarpLoop = 33;        // region tag: one warp per row, looping over the row
 constexpr int kCtaLanes = kBlock;    // region tag: one CTA per row
 constexpr int kRowsPerLane = 2;      // rows a lane of a small group serves per step
+constexpr int kTileLanes = 64;       // region tag: tiles of whole rows
+constexpr int kTileNnz = 2048;       // nonzeros of a tile (at most)
+constexpr int kTileMinRow = 9, kTileMaxRow = 256;   // row lengths served by tiles
 
 // lanes per row for a row length: groups of 1..32 lanes give every lane at
-// most 4 nonzeros; longer rows loop with a warp, the longest with a CTA
+// most 4 nonzeros; rows of 9..256 nonzeros go to tiles; longer rows loop with
+// a warp, the longest with a CTA
 inline int lanes_for(int32_t len) {
+    if (len >= kTileMinRow && len <= kTileMaxRow) return kTileLanes;
     if (len <= 4) return 1;
     if (len <= 8) return 2;
     if (len <= 16) return 4;
@@ -64,6 +75,8 @@ struct Csr {
     const int32_t *rowid;    // rows: matrix row of each stored row
     int32_t rows;
     SpmvRegions reg;
+    const int32_t *tile_row; // ntiles + 1: first stored row of each tile
+    int32_t ntiles;
     int32_t grid() const { return reg.cta0[reg.n]; }
 };
 
@@ -155,8 +168,56 @@ __device__ __forceinline__ void spmv_warp_rows(const Csr<TA> &A, const TX *__res
     }
 }
 
+// tiles of whole rows (each of at most kTileNnz nonzeros, rows of at most
+// kTileMaxRow): phase 1 gathers the tile's products into shared memory,
+// phase 2 sums each row's products in order (one thread per row); the first
+// row of each thread has its pointers and epilogue inputs loaded before the
+// gathers
+template <typename TA, typename TX, typename Acc, typename Epi>
+__device__ __forceinline__ void spmv_tiles(const Csr<TA> &A, const TX *__restrict__ x, Epi &epi,
+                                           Acc (&red)[Epi::NV], Acc *prod, int cta, int nctas) {
+    const int32_t *__restrict__ rowptr = A.rowptr;
+    const int32_t *__restrict__ col = A.col;
+    const TA *__restrict__ val = A.val;
+    const int tid = threadIdx.x;
+    for (int t = cta; t < A.ntiles; t += nctas) {
+        const int r0 = A.tile_row[t], r1 = A.tile_row[t + 1];
+        const int nz0 = rowptr[r0], nz1 = rowptr[r1];
+        const int rf = r0 + tid;
+        int fa = 0, fb = 0, fid = 0;
+        typename Epi::In fin{};
+        if (rf < r1) {
+            fa = rowptr[rf];
+            fb = rowptr[rf + 1];
+            fid = A.rowid[rf];
+            fin = epi.load(fid);
+        }
+#pragma unroll
+        for (int j = 0; j < kTileNnz / kBlock; ++j) {
+            const int k = nz0 + tid + j * kBlock;
+            if (k < nz1) prod[k - nz0] = fmul<Acc>(__ldcs(val + k), __ldg(x + __ldcs(col + k)));
+        }
+        __syncthreads();
+        for (int r = rf; r < r1; r += kBlock) {
+            int a = fa, b = fb, id = fid;
+            typename Epi::In in = fin;
+            if (r != rf) {
+                a = rowptr[r];
+                b = rowptr[r + 1];
+                id = A.rowid[r];
+                in = epi.load(id);
+            }
+            Acc sacc = 0;
+            for (int k = a - nz0; k < b - nz0; ++k) sacc += prod[k];
+            epi.row(id, sacc, in, red);
+        }
+        __syncthreads();
+    }
+}
+
 template <typename TA, typename TX, typename Acc, typename Epi>
 __global__ void __launch_bounds__(kBlock) spmv_kernel(Csr<TA> A, const TX *__restrict__ x, Epi epi, ReduceBuf rb) {
+    __shared__ Acc tile_prod[kTileNnz];
     constexpr int NV = Epi::NV;
     static_assert(NV >= 1 && NV <= kMaxRed, "epilogue reduction width");
     if (epi.skip()) return;
@@ -177,6 +238,7 @@ __global__ void __launch_bounds__(kBlock) spmv_kernel(Csr<TA> A, const TX *__res
         case 16: spmv_small_groups<16, TA, TX, Acc>(A, x, epi, red, r0, r1, cta, nctas); break;
         case 32: spmv_small_groups<32, TA, TX, Acc>(A, x, epi, red, r0, r1, cta, nctas); break;
         case kWarpLoop: spmv_warp_rows<TA, TX, Acc>(A, x, epi, red, r0, r1, cta, nctas); break;
+        case kTileLanes: spmv_tiles<TA, TX, Acc>(A, x, epi, red, tile_prod, cta, nctas); break;
         default: {
             // one CTA per row
             const int tid = threadIdx.x;
@@ -220,6 +282,7 @@ struct SpmvLayout {
     std::vector<int32_t> rowptr, col, rowid;
     std::vector<V> val;
     SpmvRegions reg{};
+    std::vector<int32_t> tile_row;   // tiles of the kTileLanes region (ntiles + 1 entries, or empty)
 };
 
 template <typename V>
@@ -265,7 +328,22 @@ inline SpmvLayout<V> spmv_layout(const std::vector<int32_t> &rp, const std::vect
         // small groups serve 32 / lanes * kRowsPerLane rows per step, a
         // looping warp 128 nonzeros per step, a CTA 1024 per step of 8 warps
         int64_t steps = 0;
-        if (lanes <= 32) {
+        if (lanes == kTileLanes) {
+            // tiles: whole rows, at most kTileNnz nonzeros each; a tile costs
+            // about as many warp steps as its nonzeros take in a looping warp
+            L.tile_row.assign(1, i);
+            int64_t acc = 0;
+            for (int32_t r = i; r < e; ++r) {
+                const int64_t len = L.rowptr[r + 1] - L.rowptr[r];
+                if (acc + len > kTileNnz) {
+                    L.tile_row.push_back(r);
+                    acc = 0;
+                }
+                acc += len;
+            }
+            L.tile_row.push_back(e);
+            steps = (int64_t)(L.tile_row.size() - 1) * (kTileNnz / 128);
+        } else if (lanes <= 32) {
             steps = (e - i + (32 / lanes) * kRowsPerLane - 1) / ((32 / lanes) * kRowsPerLane);
         } else if (lanes == kWarpLoop) {
             for (int32_t r = i; r < e; ++r) steps += (L.rowptr[r + 1] - L.rowptr[r] + 127) / 128;
@@ -291,7 +369,8 @@ inline SpmvLayout<V> spmv_layout(const std::vector<int32_t> &rp, const std::vect
     for (int k = 0; k < R.n; ++k) {
         const int64_t nrows = R.row1[k] - R.row0[k];
         const int64_t rows_per_cta = R.lanes[k] == kCtaLanes ? 1 : R.lanes[k] == kWarpLoop ? kWarps : (int64_t)kBlock / R.lanes[k] * kRowsPerLane;
-        const int64_t useful = std::max<int64_t>(1, (nrows + rows_per_cta - 1) / rows_per_cta);
+        const int64_t useful = R.lanes[k] == kTileLanes ? std::max<int64_t>(1, (int64_t)L.tile_row.size() - 1)
+                                                        : std::max<int64_t>(1, (nrows + rows_per_cta - 1) / rows_per_cta);
         int64_t g = total > 0 ? (int64_t)((double)ctas * work[k] / total) : 1;
         g = std::max<int64_t>(1, std::min(g, useful));
         R.cta0[k + 1] = R.cta0[k] + (int32_t)g;

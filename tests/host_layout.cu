@@ -21,3 +21,16 @@ extern "C" int host_spmv_layout(int rows, const int32_t *rowptr, const int32_t *
     }
     return 0;
 }
+
+// tile table of the layout above (first stored row of each tile, ntiles + 1
+// entries; 0 entries when no row length calls for tiles); returns the count
+extern "C" int host_spmv_tiles(int rows, const int32_t *rowptr, const int32_t *col, int ctas, int32_t *out,
+                               int cap) {
+    std::vector<int32_t> rp(rowptr, rowptr + rows + 1), cl(col, col + rowptr[rows]);
+    std::vector<double> vl(cl.size(), 1.0);
+    scs::SpmvLayout<double> L = scs::spmv_layout(rp, cl, vl, ctas);
+    const int n = static_cast<int>(L.tile_row.size());
+    if (n > cap) return -1;
+    if (n) std::memcpy(out, L.tile_row.data(), sizeof(int32_t) * n);
+    return n;
+}

@@ -142,7 +142,9 @@ def test_lp_solve(scs, precision, seed):
     assert st == scs.SOLVED, info
     check_solution(P, x, y, s, cone_tol=1e-5 if precision else 1e-7)
     assert abs(info["pobj"] - ref.pobj) <= 1e-3 * (1 + abs(ref.pobj))
-    assert info["matvecs"] == 2 * info["iters"] + 2 * info["cg_iters"]
+    # one A^T product per iteration, the warm-start A product every 20th
+    # iteration (A z carried in between), two per CG step
+    assert info["matvecs"] == info["iters"] + (info["iters"] + 19) // 20 + 2 * info["cg_iters"]
     assert info["iters"] % 20 == 0
 
 

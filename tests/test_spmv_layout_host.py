@@ -2,9 +2,9 @@
 satisfies what the kernel relies on: the stored rows are a permutation of the
 matrix rows carrying the same columns; the regions tile the stored rows in
 order, every row of a region gets the lane count its length calls for (1 up
-to 4 nonzeros, 2 up to 8, 4 up to 16, 8 up to 32, 16 up to 64, 32 up to 128,
-a looping warp up to 4096, a CTA beyond), and every region gets at least one
-CTA."""
+to 4 nonzeros, 2 up to 8, tiles of whole rows for 9 to 256, a looping warp up
+to 4096, a CTA beyond), every region gets at least one CTA, and the tiles
+cover their region in order with whole rows and at most 2048 nonzeros each."""
 import ctypes
 import os
 import shutil
@@ -43,12 +43,17 @@ def layout(lib, A, ctas):
     assert lib.host_spmv_layout(rows, P(rp), P(cl), ctas, P(o_rp), P(o_cl), P(o_id), P(info)) == 0
     n = int(info[0])
     regs = [tuple(int(v) for v in info[1 + 4 * k:5 + 4 * k]) for k in range(n)]
-    return dict(rp=o_rp, cl=o_cl, rowid=o_id[:rows], regs=regs)
+    tiles = np.zeros(rows + 2, np.int32)
+    nt = lib.host_spmv_tiles(rows, P(rp), P(cl), ctas, P(tiles), rows + 2)
+    assert nt >= 0
+    return dict(rp=o_rp, cl=o_cl, rowid=o_id[:rows], regs=regs, tiles=tiles[:nt])
+
+
+TILE = 64           # region tag of the tiles
 
 
 def lanes_for(n):
-    return (1 if n <= 4 else 2 if n <= 8 else 4 if n <= 16 else 8 if n <= 32 else 16 if n <= 64 else 32 if n <= 128
-            else 33 if n <= 4096 else 256)
+    return (1 if n <= 4 else 2 if n <= 8 else TILE if n <= 256 else 33 if n <= 4096 else 256)
 
 
 def check(A, L):
@@ -63,11 +68,25 @@ def check(A, L):
         r = rid[i]
         np.testing.assert_array_equal(L["cl"][L["rp"][i]:L["rp"][i + 1]], A.indices[A.indptr[r]:A.indptr[r + 1]])
     pos = 0
+    tiled = [(r0, r1, ctas) for r0, r1, lanes, ctas in L["regs"] if lanes == TILE]
     for r0, r1, lanes, ctas in L["regs"]:
         assert r0 == pos and r1 >= r0 and ctas >= 1
         assert all(lanes_for(int(v)) == lanes for v in slen[r0:r1])
         pos = r1
     assert pos == rows
+    t = L["tiles"]
+    assert len(tiled) <= 1
+    if not tiled:
+        assert len(t) == 0
+        return
+    r0, r1, ctas = tiled[0]
+    assert t[0] == r0 and t[-1] == r1 and np.all(np.diff(t) >= 1)
+    nz = L["rp"][t[1:]] - L["rp"][t[:-1]]
+    assert np.all(nz <= 2048)
+    # greedy: a tile ends only where its next row would not fit
+    nxt = slen[t[1:-1]]
+    assert np.all(nz[:-1] + nxt > 2048)
+    assert ctas <= len(t) - 1
 
 
 @pytest.mark.parametrize("case", ["powerlaw", "uniform", "tiny", "dense_rows", "empty_rows"])
