@@ -168,24 +168,33 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_nt_kernel(const __nv_bfloat
 }
 
 // ---------------------------------------------------------------------------
-// The same product on the 5th-generation tensor cores (tcgen05): one thread
-// issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) on 128 x 64 tiles whose
-// accumulator lives in tensor memory (64 or 128 columns), operands staged in
-// shared memory by cp.async in the K-major layout with the 128-byte swizzle
-// (8-row atoms of 128-byte rows, 1024 bytes apart).  Six stages; each stage's
-// MMAs signal an mbarrier (tcgen05.commit) that the loader waits on before
-// refilling the stage.  The epilogue reads the accumulator with
-// tcgen05.ld (each warp its 32 TMEM lanes = 32 rows).  Every mbarrier wait is
-// bounded: on time-out the kernel sets *err, waits (bounded) for its own MMAs,
-// frees its tensor memory and returns.
+// The same product on the 5th-generation tensor cores (tcgen05), warp
+// specialised: warps 0-3 copy A and B tiles into shared memory with
+// cp.async (K-major, 128-byte swizzle: 8-row atoms of 128-byte rows, 1024
+// bytes apart) and then run the epilogue; one thread of warp 4 issues
+// tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) into a 128 x BNt accumulator
+// in tensor memory (BNt = 64, 128 or 256 columns).  A ring of stages links
+// the two roles by mbarriers: `full[s]` completes when every loader has
+// fenced its copies of stage s for the tensor cores (fence.proxy.async)
+// and arrived, `empty[s]` when the MMAs that read stage s have completed
+// (tcgen05.commit), so neither role waits on a CTA-wide barrier.  The
+// epilogue reads the accumulator with tcgen05.ld (each warp its 32 TMEM
+// lanes = 32 rows) after a last commit.  Every mbarrier wait is bounded: on
+// time-out the kernel sets *err, lets every issued MMA and copy complete
+// (bounded), frees its tensor memory and returns.
 // ---------------------------------------------------------------------------
-constexpr int TBM = 128, TBN = 64, TBK = 64, kTcThreads = 128;   // TBN: the narrowest tile
-constexpr int kTcStages = 6, kTcAhead = kTcStages - 2;               // prefetch distance 4
-constexpr int kTcStageA = TBM * TBK * 2;                              // bytes
+constexpr int TBM = 128, TBN = 64, TBK = 64;             // TBN: the narrowest tile
+constexpr int kTcLoaders = 128;                          // warps 0-3
+constexpr int kTcThreads = kTcLoaders + 32;              // + warp 4, the MMA issuer
+constexpr int kTcStageA = TBM * TBK * 2;                 // bytes
+constexpr int kTcPipe = 196608;                          // shared-memory bytes of the stage ring
+constexpr int kTcLag = 2;                                // cp.async groups a loader keeps in flight
 template <int BNt>
 __host__ __device__ constexpr int tc_stage_b() { return BNt * TBK * 2; }
 template <int BNt>
-__host__ __device__ constexpr int tc_smem() { return kTcStages * (kTcStageA + tc_stage_b<BNt>()) + 1024 + 128; }
+__host__ __device__ constexpr int tc_stages() { return kTcPipe / (kTcStageA + tc_stage_b<BNt>()); }
+template <int BNt>
+__host__ __device__ constexpr int tc_smem() { return tc_stages<BNt>() * (kTcStageA + tc_stage_b<BNt>()) + 1024 + 256; }
 constexpr uint32_t kTcSpin = 1u << 20;
 
 __device__ __forceinline__ uint64_t tc_smem_desc(uint32_t addr) {
@@ -216,29 +225,33 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
     return false;
 }
 
-// C tile 128 x BNt per CTA; kTcStages shared-memory stages, loads kTcAhead
-// k-blocks ahead: the stage of k-block kt + kTcAhead is refilled once the
-// MMAs of k-block kt - 2 (its previous user) have completed, so those of
-// kt - 1 are still queued while kt issues.
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(mbar) : "memory");
+}
+
+// C tile 128 x BNt per CTA over K / 64 k-blocks through tc_stages<BNt>() stages
 template <typename Epi, int BNt>
 __global__ void __launch_bounds__(kTcThreads, 1) gemm_nt_tc_kernel(const __nv_bfloat16 *__restrict__ A, int lda,
                                                                    const __nv_bfloat16 *__restrict__ B, int ldb, int K,
                                                                    Epi epi, int *err) {
+    constexpr int S = tc_stages<BNt>();
     constexpr int kStageB = tc_stage_b<BNt>();
+    static_assert(S > kTcLag, "the ring must hold more stages than a loader keeps in flight");
     extern __shared__ __align__(16) unsigned char tc_raw[];
     const uint32_t raw = smem_u32(tc_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char *gbase = tc_raw + (base - raw);
-    unsigned char *misc = gbase + kTcStages * (kTcStageA + kStageB);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(misc);                  // [kTcStages]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(misc + 8 * kTcStages);
+    unsigned char *misc = gbase + S * (kTcStageA + kStageB);
+    uint64_t *full = reinterpret_cast<uint64_t *>(misc);     // [S]
+    uint64_t *empty = full + S;                               // [S]
+    uint64_t *done = empty + S;                               // every MMA of the tile completed
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int bm = blockIdx.y * TBM, bn = blockIdx.x * BNt;
     auto sA = [&](int st) { return base + st * kTcStageA; };
-    auto sB = [&](int st) { return base + kTcStages * kTcStageA + st * kStageB; };
+    auto sB = [&](int st) { return base + S * kTcStageA + st * kStageB; };
     auto gA = [&](int st) { return gbase + st * kTcStageA; };
-    auto gB = [&](int st) { return gbase + kTcStages * kTcStageA + st * kStageB; };
-    auto barS = [&](int st) { return smem_u32(&bar[st]); };
+    auto gB = [&](int st) { return gbase + S * kTcStageA + st * kStageB; };
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
@@ -246,52 +259,65 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_nt_tc_kernel(const __nv_bf
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     if (tid == 0) {
-        for (int st = 0; st < kTcStages; ++st) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(barS(st)));
+        for (int st = 0; st < S; ++st) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&full[st])), "n"(kTcLoaders));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[st])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(done)));
         asm volatile("fence.mbarrier_init.release.cluster;\n");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n");
     const uint32_t tmem = *tmem_slot;
-
-    auto load = [&](int stage, int k0) {
-        // A: 128 rows x 8 chunks of 16 bytes; B: BNt rows x 8 chunks; each row
-        // of 64 BF16 is 128 bytes, chunks placed by the 128-byte swizzle
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int ch = tid + i * kTcThreads, r = ch >> 3, kc = ch & 7;
-            cp_async16(gA(stage) + tc_sw128(r, kc), A + (size_t)(bm + r) * lda + k0 + kc * 8);
-        }
-#pragma unroll
-        for (int i = 0; i < BNt / 16; ++i) {
-            const int ch = tid + i * kTcThreads, r = ch >> 3, kc = ch & 7;
-            cp_async16(gB(stage) + tc_sw128(r, kc), B + (size_t)(bn + r) * ldb + k0 + kc * 8);
-        }
-    };
     const int KT = K / TBK;
     bool ok = true;
-    int issued = 0;
+
+    if (warp < 4) {
+        // loaders: A is 128 rows x 8 chunks of 16 bytes, B BNt rows x 8
+        // chunks; each row of 64 BF16 is 128 bytes, chunks placed by the
+        // 128-byte swizzle
+        int loaded = 0, arrived = 0;
+        for (int kt = 0; kt < KT; ++kt) {
+            const int s = kt % S, k0 = kt * TBK;
+            // the stage's previous MMAs (k-block kt - S) must have completed
+            if (kt >= S && !tc_wait(smem_u32(&empty[s]), ((kt / S) - 1) & 1)) {
+                ok = false;
+                break;
+            }
 #pragma unroll
-    for (int j = 0; j < kTcAhead; ++j) {
-        if (j < KT) load(j, j * TBK);
-        cp_commit();
-    }
-    for (int kt = 0; kt < KT; ++kt) {
-        const int s = kt % kTcStages;
-        const int nk = kt + kTcAhead;
-        if (nk < KT) {
-            // stage nk mod S was last read by the MMAs of k-block kt - 2
-            if (kt >= 2) ok = __syncthreads_and(tc_wait(barS((kt - 2) % kTcStages), ((kt - 2) / kTcStages) & 1)) != 0;
-            if (!ok) break;
-            load(nk % kTcStages, nk * TBK);
+            for (int i = 0; i < 8; ++i) {
+                const int ch = tid + i * kTcLoaders, r = ch >> 3, kc = ch & 7;
+                cp_async16(gA(s) + tc_sw128(r, kc), A + (size_t)(bm + r) * lda + k0 + kc * 8);
+            }
+#pragma unroll
+            for (int i = 0; i < BNt / 16; ++i) {
+                const int ch = tid + i * kTcLoaders, r = ch >> 3, kc = ch & 7;
+                cp_async16(gB(s) + tc_sw128(r, kc), B + (size_t)(bn + r) * ldb + k0 + kc * 8);
+            }
+            cp_commit();
+            loaded = kt + 1;
+            if (loaded - arrived > kTcLag) {
+                // the oldest group in flight has landed: hand its stage over
+                cp_wait<kTcLag>();
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                mbar_arrive(smem_u32(&full[arrived % S]));
+                ++arrived;
+            }
         }
-        cp_commit();
-        cp_wait<kTcAhead>();
+        cp_wait<0>();            // no copy of ours left in flight
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+        for (; arrived < loaded; ++arrived) mbar_arrive(smem_u32(&full[arrived % S]));
+    } else if (lane == 0) {
+        // MMA issuer
+        const uint32_t idesc = tc_idesc(TBM, BNt);
+        for (int kt = 0; kt < KT; ++kt) {
+            const int s = kt % S;
+            if (!tc_wait(smem_u32(&full[s]), (kt / S) & 1)) {
+                ok = false;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;\n");
-            const uint32_t idesc = tc_idesc(TBM, BNt);
 #pragma unroll
             for (int k = 0; k < TBK / 16; ++k) {
                 const uint64_t ad = tc_smem_desc(sA(s) + k * 32), bd = tc_smem_desc(sB(s) + k * 32);
@@ -302,38 +328,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_nt_tc_kernel(const __nv_bf
                     "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                barS(s)));
+                smem_u32(&empty[s])));
         }
-        issued = kt + 1;
+        // completes once every MMA issued above has (at once if none was)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+            smem_u32(done)));
     }
-    cp_wait<0>();            // no copy of ours left in flight
-    // the last commit covers every MMA issued before it (bounded wait, also
-    // after a time-out: the tensor memory is freed only after it)
-    if (issued > 0) {
-        const int last = issued - 1;
-        const bool done = __syncthreads_and(tc_wait(barS(last % kTcStages), (last / kTcStages) & 1)) != 0;
-        ok = ok && done;
-    }
-    if (!ok && tid == 0) atomicExch(err, 1);
-    asm volatile("tcgen05.fence::after_thread_sync;\n");
-    if (ok) {
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-        const int r = bm + warp * 32 + lane;
+    if (warp < 4) {
+        // epilogue: the accumulator once every MMA has completed
+        const bool fin = tc_wait(smem_u32(done), 0);
+        ok = __all_sync(0xffffffffu, ok && fin);
+        if (ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+            const int r = bm + warp * 32 + lane;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BNt; c0 += 16) {
+                uint32_t v[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                    "%13, %14, %15}, [%16];\n"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(tmem + lane_base + (uint32_t)c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-        for (int c0 = 0; c0 < BNt; c0 += 16) {
-            uint32_t v[16];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-                "%14, %15}, [%16];\n"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15])
-                : "r"(tmem + lane_base + (uint32_t)c0));
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-            for (int j = 0; j < 16; j += 2) epi(r, bn + c0 + j, __uint_as_float(v[j]), __uint_as_float(v[j + 1]));
+                for (int j = 0; j < 16; j += 2) epi(r, bn + c0 + j, __uint_as_float(v[j]), __uint_as_float(v[j + 1]));
+            }
         }
     }
+    if (!ok) atomicExch(err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;\n");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(BNt));
@@ -450,6 +475,19 @@ static __global__ void weights_bf16_kernel(const float *__restrict__ W, int out_
 
 inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
+template <typename Epi, int BNt>
+void launch_tc(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, int M, int N, int K, Epi epi, int *err,
+               cudaStream_t stream) {
+    static bool attr = false;
+    if (!attr) {
+        SCS_CUDA(cudaFuncSetAttribute(gemm_nt_tc_kernel<Epi, BNt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      tc_smem<BNt>()));
+        attr = true;
+    }
+    gemm_nt_tc_kernel<Epi, BNt><<<dim3(N / BNt, M / TBM), kTcThreads, tc_smem<BNt>(), stream>>>(A, lda, B, ldb, K, epi,
+                                                                                                 err);
+}
+
 // C = A B^T through either kernel; the shape must meet the kernel's tiling
 template <typename Epi>
 void launch_gemm(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, int M, int N, int K, Epi epi,
@@ -459,25 +497,12 @@ void launch_gemm(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ld
     if (tc) {
         if (M % TBM || N % TBN || K % TBK)
             throw CudaError("GEMM shape outside the tcgen05 kernel's tiling", SCS_INVALID_INPUT);
-        if (N % 128 == 0) {
-            static bool attr = false;
-            if (!attr) {
-                SCS_CUDA(cudaFuncSetAttribute(gemm_nt_tc_kernel<Epi, 128>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<128>()));
-                attr = true;
-            }
-            gemm_nt_tc_kernel<Epi, 128><<<dim3(N / 128, M / TBM), kTcThreads, tc_smem<128>(), stream>>>(
-                A, lda, B, ldb, K, epi, err);
-        } else {
-            static bool attr = false;
-            if (!attr) {
-                SCS_CUDA(cudaFuncSetAttribute(gemm_nt_tc_kernel<Epi, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              tc_smem<64>()));
-                attr = true;
-            }
-            gemm_nt_tc_kernel<Epi, 64><<<dim3(N / 64, M / TBM), kTcThreads, tc_smem<64>(), stream>>>(
-                A, lda, B, ldb, K, epi, err);
-        }
+        if (N % 256 == 0)
+            launch_tc<Epi, 256>(A, lda, B, ldb, M, N, K, epi, err, stream);
+        else if (N % 128 == 0)
+            launch_tc<Epi, 128>(A, lda, B, ldb, M, N, K, epi, err, stream);
+        else
+            launch_tc<Epi, 64>(A, lda, B, ldb, M, N, K, epi, err, stream);
     } else {
         if (M % BM || N % BN || K % BK) throw CudaError("GEMM shape outside the kernel's tiling", SCS_INVALID_INPUT);
         gemm_nt_kernel<Epi><<<dim3(N / BN, M / BM), kGemmThreads, 0, stream>>>(A, lda, B, ldb, K, epi);

@@ -1,8 +1,9 @@
-"""The network's product on tcgen05 (tensor-memory accumulators, one
-issuing thread, mbarrier-tracked completion) against the mma.sync kernel and
-an FP64 reference of the same BF16 operands, on one tile, a K loop of many
-stages, several tiles in M and N and the network's widest K; then the whole
-network's gradients on the tcgen05 path against the FP64 oracle."""
+"""The network's product on tcgen05 (tensor-memory accumulators; loader
+warps and an MMA-issuing thread linked by mbarriers) against the mma.sync
+kernel and an FP64 reference of the same BF16 operands, on one tile, K loops
+that wrap the stage ring, several tiles in M and N, each tile width, and the
+network's widest K; then the whole network's gradients on the tcgen05 path
+against the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -19,7 +20,10 @@ def env():
     return torch, scs
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 64, 64), (128, 64, 512), (384, 192, 256), (256, 512, 4480)])
+# tiles of 64 (N = 64, 192), 128 (N = 384) and 256 columns (N = 512, 768); K from
+# one k-block to 70 (the stage ring wraps many times)
+@pytest.mark.parametrize("M,N,K", [(128, 64, 64), (128, 64, 512), (384, 192, 256), (128, 384, 1024),
+                                   (256, 512, 4480), (384, 768, 192)])
 def test_tcgen05_product(env, M, N, K):
     torch, scs = env
     rng = np.random.default_rng(M + N + K)
