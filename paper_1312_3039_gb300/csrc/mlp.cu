@@ -15,8 +15,10 @@
 // Shapes are padded so that every launch meets the kernel's tiling exactly
 // (M % 128, N % 64, K % 32, rows 16-byte aligned); padding rows and columns
 // of the weights are zero and stay zero (their gradients are zero).
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cmath>
 #include <cstdint>
@@ -168,27 +170,31 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_nt_kernel(const __nv_bfloat
 }
 
 // ---------------------------------------------------------------------------
-// The same product on the 5th-generation tensor cores (tcgen05), warp
-// specialised: warps 0-3 copy A and B tiles into shared memory with
-// cp.async (K-major, 128-byte swizzle: 8-row atoms of 128-byte rows, 1024
-// bytes apart) and then run the epilogue; one thread of warp 4 issues
-// tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) into a 128 x BNt accumulator
-// in tensor memory (BNt = 64, 128 or 256 columns).  A ring of stages links
-// the two roles by mbarriers: `full[s]` completes when every loader has
-// fenced its copies of stage s for the tensor cores (fence.proxy.async)
-// and arrived, `empty[s]` when the MMAs that read stage s have completed
-// (tcgen05.commit), so neither role waits on a CTA-wide barrier.  The
-// epilogue reads the accumulator with tcgen05.ld (each warp its 32 TMEM
-// lanes = 32 rows) after a last commit.  Every mbarrier wait is bounded: on
-// time-out the kernel sets *err, lets every issued MMA and copy complete
-// (bounded), frees its tensor memory and returns.
+// The same product on the 5th-generation tensor cores (tcgen05): a
+// persistent, warp-specialised kernel.  Each CTA walks C tiles of 128 x BNt
+// (BNt = 64, 128 or 256; N tiles fastest, so the CTAs of a wave share A rows
+// and B stays in L2):
+//   warp 0, one thread: TMA copies (cp.async.bulk.tensor, 128-byte swizzle)
+//     of the A and B k-blocks into a ring of shared-memory stages; each copy
+//     completes on the stage's `full` mbarrier by its byte count;
+//   warp 1, one thread: tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) into one
+//     of two accumulators in tensor memory (2 x BNt columns); tcgen05.commit
+//     frees a stage (`empty`) once its MMAs completed, and hands a finished
+//     accumulator to the epilogue (`acc_full`);
+//   warps 2-5: the epilogue, tcgen05.ld of the accumulator (a warp reads the
+//     32 TMEM lanes of its quarter: rows 32 (warp % 4) ..) into the fused
+//     epilogue, then `acc_empty`, so that the MMAs of the next tile run while
+//     this one is written out.
+// The operand layout in shared memory is K-major with the 128-byte swizzle
+// (8-row atoms of 128-byte rows, 1024 bytes apart), the layout the TMA writes
+// for a 64-element-wide box.  Every mbarrier wait is bounded: on time-out the
+// kernel sets *err, waits (bounded) for its copies and MMAs in flight, frees
+// its tensor memory and returns.
 // ---------------------------------------------------------------------------
 constexpr int TBM = 128, TBN = 64, TBK = 64;             // TBN: the narrowest tile
-constexpr int kTcLoaders = 128;                          // warps 0-3
-constexpr int kTcThreads = kTcLoaders + 32;              // + warp 4, the MMA issuer
+constexpr int kTcThreads = 192;                          // 6 warps: TMA, MMA, 4 epilogue
 constexpr int kTcStageA = TBM * TBK * 2;                 // bytes
 constexpr int kTcPipe = 196608;                          // shared-memory bytes of the stage ring
-constexpr int kTcLag = 2;                                // cp.async groups a loader keeps in flight
 template <int BNt>
 __host__ __device__ constexpr int tc_stage_b() { return BNt * TBK * 2; }
 template <int BNt>
@@ -228,120 +234,140 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
     asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(mbar) : "memory");
 }
+__device__ __forceinline__ void mbar_expect(uint32_t mbar, uint32_t bytes) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(mbar),
+                 "r"(bytes)
+                 : "memory");
+}
+// 2-D tiled TMA load of the box at (x = k offset, y = row) into shared memory
+__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::
+            "r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
 
-// C tile 128 x BNt per CTA over K / 64 k-blocks through tc_stages<BNt>() stages
+// C = A B^T, A M x K and B N x K (K-contiguous, described by tmA and tmB)
 template <typename Epi, int BNt>
-__global__ void __launch_bounds__(kTcThreads, 1) gemm_nt_tc_kernel(const __nv_bfloat16 *__restrict__ A, int lda,
-                                                                   const __nv_bfloat16 *__restrict__ B, int ldb, int K,
-                                                                   Epi epi, int *err) {
+__global__ void __launch_bounds__(kTcThreads, 1) gemm_nt_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                   const __grid_constant__ CUtensorMap tmB, int M,
+                                                                   int N, int K, Epi epi, int *err) {
     constexpr int S = tc_stages<BNt>();
     constexpr int kStageB = tc_stage_b<BNt>();
-    static_assert(S > kTcLag, "the ring must hold more stages than a loader keeps in flight");
+    constexpr uint32_t kStageBytes = kTcStageA + kStageB;
     extern __shared__ __align__(16) unsigned char tc_raw[];
     const uint32_t raw = smem_u32(tc_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
-    unsigned char *gbase = tc_raw + (base - raw);
-    unsigned char *misc = gbase + S * (kTcStageA + kStageB);
-    uint64_t *full = reinterpret_cast<uint64_t *>(misc);     // [S]
-    uint64_t *empty = full + S;                               // [S]
-    uint64_t *done = empty + S;                               // every MMA of the tile completed
+    unsigned char *misc = tc_raw + (base - raw) + S * (kTcStageA + kStageB);
+    uint64_t *full = reinterpret_cast<uint64_t *>(misc);     // [S] the stage's copies landed
+    uint64_t *empty = full + S;                               // [S] the stage's MMAs completed
+    uint64_t *acc_full = empty + S;                           // [2] an accumulator is ready
+    uint64_t *acc_empty = acc_full + 2;                       // [2] an accumulator was read out
+    uint64_t *done = acc_empty + 2;                           // every MMA of the CTA completed
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int bm = blockIdx.y * TBM, bn = blockIdx.x * BNt;
+    const int mt = M / TBM, nt = N / BNt, ntiles = mt * nt, KT = K / TBK;
     auto sA = [&](int st) { return base + st * kTcStageA; };
     auto sB = [&](int st) { return base + S * kTcStageA + st * kStageB; };
-    auto gA = [&](int st) { return gbase + st * kTcStageA; };
-    auto gB = [&](int st) { return gbase + S * kTcStageA + st * kStageB; };
+    auto bar = [](uint64_t *b) { return smem_u32(b); };
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
-                     "n"(BNt));
+                     "n"(2 * BNt));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     if (tid == 0) {
         for (int st = 0; st < S; ++st) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&full[st])), "n"(kTcLoaders));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[st])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar(&full[st])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar(&empty[st])));
         }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(done)));
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar(&acc_full[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;\n" ::"r"(bar(&acc_empty[b])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar(done)));
         asm volatile("fence.mbarrier_init.release.cluster;\n");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n");
     const uint32_t tmem = *tmem_slot;
-    const int KT = K / TBK;
     bool ok = true;
 
-    if (warp < 4) {
-        // loaders: A is 128 rows x 8 chunks of 16 bytes, B BNt rows x 8
-        // chunks; each row of 64 BF16 is 128 bytes, chunks placed by the
-        // 128-byte swizzle
-        int loaded = 0, arrived = 0;
-        for (int kt = 0; kt < KT; ++kt) {
-            const int s = kt % S, k0 = kt * TBK;
-            // the stage's previous MMAs (k-block kt - S) must have completed
-            if (kt >= S && !tc_wait(smem_u32(&empty[s]), ((kt / S) - 1) & 1)) {
-                ok = false;
-                break;
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int ch = tid + i * kTcLoaders, r = ch >> 3, kc = ch & 7;
-                cp_async16(gA(s) + tc_sw128(r, kc), A + (size_t)(bm + r) * lda + k0 + kc * 8);
-            }
-#pragma unroll
-            for (int i = 0; i < BNt / 16; ++i) {
-                const int ch = tid + i * kTcLoaders, r = ch >> 3, kc = ch & 7;
-                cp_async16(gB(s) + tc_sw128(r, kc), B + (size_t)(bn + r) * ldb + k0 + kc * 8);
-            }
-            cp_commit();
-            loaded = kt + 1;
-            if (loaded - arrived > kTcLag) {
-                // the oldest group in flight has landed: hand its stage over
-                cp_wait<kTcLag>();
-                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                mbar_arrive(smem_u32(&full[arrived % S]));
-                ++arrived;
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        int it = 0;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int tm = t / nt, tn = t % nt;
+            for (int kt = 0; kt < KT; ++kt, ++it) {
+                const int s = it % S;
+                if (it >= S && !tc_wait(bar(&empty[s]), ((it / S) - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                mbar_expect(bar(&full[s]), kStageBytes);
+                tma_load(sA(s), &tmA, kt * TBK, tm * TBM, bar(&full[s]));
+                tma_load(sB(s), &tmB, kt * TBK, tn * BNt, bar(&full[s]));
             }
         }
-        cp_wait<0>();            // no copy of ours left in flight
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        for (; arrived < loaded; ++arrived) mbar_arrive(smem_u32(&full[arrived % S]));
-    } else if (lane == 0) {
+        // the copies of the last uses of each stage have landed (bounded)
+        for (int j = (it > S ? it - S : 0); j < it; ++j) ok = tc_wait(bar(&full[j % S]), (j / S) & 1) && ok;
+    } else if (warp == 1 && lane == 0) {
         // MMA issuer
         const uint32_t idesc = tc_idesc(TBM, BNt);
-        for (int kt = 0; kt < KT; ++kt) {
-            const int s = kt % S;
-            if (!tc_wait(smem_u32(&full[s]), (kt / S) & 1)) {
+        int it = 0, tl = 0;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
+            const int b = tl & 1;
+            if (tl >= 2 && !tc_wait(bar(&acc_empty[b]), ((tl >> 1) - 1) & 1)) {
                 ok = false;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n");
+            const uint32_t acc_tm = tmem + (uint32_t)(b * BNt);
+            for (int kt = 0; kt < KT; ++kt, ++it) {
+                const int s = it % S;
+                if (!tc_wait(bar(&full[s]), (it / S) & 1)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n");
 #pragma unroll
-            for (int k = 0; k < TBK / 16; ++k) {
-                const uint64_t ad = tc_smem_desc(sA(s) + k * 32), bd = tc_smem_desc(sB(s) + k * 32);
-                const uint32_t acc = (kt > 0 || k > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                for (int k = 0; k < TBK / 16; ++k) {
+                    const uint64_t ad = tc_smem_desc(sA(s) + k * 32), bd = tc_smem_desc(sB(s) + k * 32);
+                    const uint32_t acc = (kt > 0 || k > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_tm),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                    bar(&empty[s])));
             }
+            // the accumulator is handed over even after a time-out, so that
+            // the epilogue does not wait in vain
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                smem_u32(&empty[s])));
+                bar(&acc_full[b])));
         }
-        // completes once every MMA issued above has (at once if none was)
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-            smem_u32(done)));
-    }
-    if (warp < 4) {
-        // epilogue: the accumulator once every MMA has completed
-        const bool fin = tc_wait(smem_u32(done), 0);
-        ok = __all_sync(0xffffffffu, ok && fin);
-        if (ok) {
+        // every MMA issued above has completed before the memory is freed
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar(done)));
+        ok = tc_wait(bar(done), 0) && ok;
+    } else if (warp >= 2) {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = the tile's rows
+        const int q = warp & 3;
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        int tl = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
+            const int b = tl & 1, tm = t / nt, tn = t % nt;
+            const bool ready = __all_sync(0xffffffffu, tc_wait(bar(&acc_full[b]), (tl >> 1) & 1));
+            if (!ready) {
+                ok = false;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;\n");
-            const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-            const int r = bm + warp * 32 + lane;
+            const int r = tm * TBM + q * 32 + lane;
 #pragma unroll 1
             for (int c0 = 0; c0 < BNt; c0 += 16) {
                 uint32_t v[16];
@@ -351,17 +377,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_nt_tc_kernel(const __nv_bf
                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
                       "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
                       "=r"(v[15])
-                    : "r"(tmem + lane_base + (uint32_t)c0));
+                    : "r"(tmem + lane_base + (uint32_t)(b * BNt + c0)));
                 asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-                for (int j = 0; j < 16; j += 2) epi(r, bn + c0 + j, __uint_as_float(v[j]), __uint_as_float(v[j + 1]));
+                for (int j = 0; j < 16; j += 2)
+                    epi(r, tn * BNt + c0 + j, __uint_as_float(v[j]), __uint_as_float(v[j + 1]));
             }
+            asm volatile("tcgen05.fence::before_thread_sync;\n");
+            mbar_arrive(bar(&acc_empty[b]));
         }
     }
     if (!ok) atomicExch(err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;\n");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(BNt));
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(2 * BNt));
 }
 
 // dst[c][r] = src[r][c] for r < rows, c < cols (BF16; 32 x 32 tiles)
@@ -475,17 +505,45 @@ static __global__ void weights_bf16_kernel(const float *__restrict__ W, int out_
 
 inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
+// tensor map of a row-major BF16 matrix (rows x cols, leading dimension ld
+// elements) read in boxes of box_rows x 64 with the 128-byte swizzle
+inline CUtensorMap tc_map(const __nv_bfloat16 *p, int rows, int cols, int ld, int box_rows) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        SCS_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !fn) throw CudaError("cuTensorMapEncodeTiled unavailable", SCS_DEVICE_ERROR);
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    CUtensorMap m;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)TBK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(p), dims, strides,
+                              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw CudaError("tensor map encoding failed", SCS_INVALID_INPUT);
+    return m;
+}
+
 template <typename Epi, int BNt>
 void launch_tc(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, int M, int N, int K, Epi epi, int *err,
                cudaStream_t stream) {
     static bool attr = false;
+    static int sms = 0;
     if (!attr) {
         SCS_CUDA(cudaFuncSetAttribute(gemm_nt_tc_kernel<Epi, BNt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       tc_smem<BNt>()));
+        int dev = 0;
+        SCS_CUDA(cudaGetDevice(&dev));
+        SCS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         attr = true;
     }
-    gemm_nt_tc_kernel<Epi, BNt><<<dim3(N / BNt, M / TBM), kTcThreads, tc_smem<BNt>(), stream>>>(A, lda, B, ldb, K, epi,
-                                                                                                 err);
+    const CUtensorMap ma = tc_map(A, M, K, lda, TBM), mb = tc_map(B, N, K, ldb, BNt);
+    const int tiles = (M / TBM) * (N / BNt);
+    gemm_nt_tc_kernel<Epi, BNt><<<std::min(tiles, sms), kTcThreads, tc_smem<BNt>(), stream>>>(ma, mb, M, N, K, epi, err);
 }
 
 // C = A B^T through either kernel; the shape must meet the kernel's tiling
