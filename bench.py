@@ -811,13 +811,19 @@ def run_mlp_train(args):
         C = torch.empty(M, N, dtype=torch.float32, device="cuda")
         for _ in range(3):
             scs.lib().scs_bf16_gemm(A.data_ptr(), K, B.data_ptr(), K, M, N, K, C.data_ptr(), N, tc, stream.cuda_stream)
+        # back-to-back launches (enqueue only), CUDA events on their stream
+        err = torch.zeros(1, dtype=torch.int32, device="cuda")
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
         g0.record(stream)
         R = 10
         for _ in range(R):
-            scs.lib().scs_bf16_gemm(A.data_ptr(), K, B.data_ptr(), K, M, N, K, C.data_ptr(), N, tc, stream.cuda_stream)
+            rc = scs.lib().scs_bf16_gemm_async(A.data_ptr(), K, B.data_ptr(), K, M, N, K, C.data_ptr(), N, tc,
+                                               err.data_ptr(), stream.cuda_stream)
+            assert rc == 0, rc
         g1.record(stream)
         stream.synchronize()
+        assert int(err.item()) == 0
         gms = g0.elapsed_time(g1) / R
         res[tc] = {"step_ms": ms, "step_tflops": flop_step / (ms / 1e3) / 1e12,
                    "gemm_ms": gms, "gemm_tflops": 2.0 * M * N * K / (gms / 1e3) / 1e12}

@@ -368,6 +368,13 @@ void scs_mlp_destroy(scs_mlp *w);
  * status word; synchronises `stream`. */
 int32_t scs_bf16_gemm(const void *A, int32_t lda, const void *B, int32_t ldb, int32_t M, int32_t N, int32_t K,
                       float *C, int32_t ldc, int32_t tcgen05, void *stream);
+/* The same product enqueued on `stream` only (no allocation, no
+ * synchronisation), so that back-to-back launches can be timed: err is a
+ * device int32 the caller zeroes beforehand; a tcgen05 launch sets it to 1
+ * if a bounded wait timed out.  Shapes are checked on the host
+ * (SCS_INVALID_INPUT); returns 0 once the launch is enqueued. */
+int32_t scs_bf16_gemm_async(const void *A, int32_t lda, const void *B, int32_t ldb, int32_t M, int32_t N, int32_t K,
+                            float *C, int32_t ldc, int32_t tcgen05, int32_t *err, void *stream);
 
 /* Device helpers of the warm-start pipeline (FP32 row-major data):
  * per-column mean and standard deviation; in-place standardisation

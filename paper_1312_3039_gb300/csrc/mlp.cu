@@ -941,6 +941,17 @@ int32_t scs_mlp_error(scs_mlp *w) {
     return h ? SCS_DEVICE_ERROR : 0;
 }
 
+int32_t scs_bf16_gemm_async(const void *A, int32_t lda, const void *B, int32_t ldb, int32_t M, int32_t N, int32_t K,
+                            float *C, int32_t ldc, int32_t tcgen05, int32_t *err, void *stream) {
+    if (!A || !B || !C || !err || M <= 0 || N <= 0 || K <= 0 || ldc < N || ldc % 2) return SCS_INVALID_INPUT;
+    return mlp_guarded([&]() -> int32_t {
+        scs::mlp::launch_gemm(static_cast<const __nv_bfloat16 *>(A), lda, static_cast<const __nv_bfloat16 *>(B), ldb,
+                              M, N, K, scs::mlp::EpiPlain{C, ldc}, tcgen05 != 0, reinterpret_cast<int *>(err),
+                              static_cast<cudaStream_t>(stream));
+        return 0;
+    });
+}
+
 int32_t scs_bf16_gemm(const void *A, int32_t lda, const void *B, int32_t ldb, int32_t M, int32_t N, int32_t K,
                       float *C, int32_t ldc, int32_t tcgen05, void *stream) {
     if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0 || ldc < N || ldc % 2) return SCS_INVALID_INPUT;

@@ -163,6 +163,8 @@ def lib():
         L.scs_mlp_error.restype = I32
         L.scs_bf16_gemm.argtypes = [V, I32, V, I32, I32, I32, I32, V, I32, I32, V]
         L.scs_bf16_gemm.restype = I32
+        L.scs_bf16_gemm_async.argtypes = [V, I32, V, I32, I32, I32, I32, V, I32, I32, V, V]
+        L.scs_bf16_gemm_async.restype = I32
         L.scs_column_stats.argtypes = [V, C.c_int64, I32, V, V, V]
         L.scs_column_stats.restype = I32
         L.scs_standardize.argtypes = [V, C.c_int64, I32, V, V, V]

@@ -63,3 +63,27 @@ def test_network_gradients_on_tcgen05(env):
     for li, ((gW, gb), (rW, rb)) in enumerate(zip(scs.unpack_params(g.astype(np.float64), sizes), g_ref)):
         e = np.linalg.norm(gW - rW) / np.linalg.norm(rW)
         assert e < 5e-2, (li, e)
+
+
+def test_enqueue_only_product(env):
+    """scs_bf16_gemm_async (enqueue only, caller's status word) gives the
+    synchronising call's result, bit for bit, and leaves the status at 0."""
+    torch, scs = env
+    rng = np.random.default_rng(11)
+    M, N, K = 256, 512, 1024
+    A = torch.tensor(rng.standard_normal((M, K)), dtype=torch.bfloat16, device="cuda")
+    B = torch.tensor(rng.standard_normal((N, K)), dtype=torch.bfloat16, device="cuda")
+    C1 = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    C2 = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    assert scs.lib().scs_bf16_gemm(A.data_ptr(), K, B.data_ptr(), K, M, N, K, C1.data_ptr(), N, 1, None) == 0
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream()
+    for _ in range(3):
+        assert scs.lib().scs_bf16_gemm_async(A.data_ptr(), K, B.data_ptr(), K, M, N, K, C2.data_ptr(), N, 1,
+                                             err.data_ptr(), s.cuda_stream) == 0
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    assert torch.equal(C1, C2)
+    # shapes outside the tiling are refused on the host
+    assert scs.lib().scs_bf16_gemm_async(A.data_ptr(), K, B.data_ptr(), K, M, N - 8, K, C2.data_ptr(), N, 1,
+                                         err.data_ptr(), s.cuda_stream) == scs.INVALID_INPUT
