@@ -4,11 +4,16 @@
 
 #include "../paper_1312_3039_gb300/csrc/spmv.cuh"
 
-extern "C" int host_spmv_layout(int rows, const int32_t *rowptr, const int32_t *col, int ctas, int32_t *out_rowptr,
-                                int32_t *out_col, int32_t *out_rowid, int32_t *info) {
+// threads: host threads of the copy (0: the solver's choice); the values of
+// the layout are the source positions of the entries (out_val, may be null)
+extern "C" int host_spmv_layout_t(int rows, const int32_t *rowptr, const int32_t *col, int ctas, int threads,
+                                  int32_t *out_rowptr, int32_t *out_col, int32_t *out_rowid, int32_t *info,
+                                  double *out_val) {
     std::vector<int32_t> rp(rowptr, rowptr + rows + 1), cl(col, col + rowptr[rows]);
-    std::vector<double> vl(cl.size(), 1.0);
-    scs::SpmvLayout<double> L = scs::spmv_layout(rp, cl, vl, ctas);
+    std::vector<double> vl(cl.size());
+    for (size_t t = 0; t < vl.size(); ++t) vl[t] = (double)t;
+    scs::SpmvLayout<double> L = scs::spmv_layout(rp, cl, vl, ctas, threads);
+    if (out_val) std::memcpy(out_val, L.val.data(), sizeof(double) * L.val.size());
     std::memcpy(out_rowptr, L.rowptr.data(), sizeof(int32_t) * L.rowptr.size());
     std::memcpy(out_col, L.col.data(), sizeof(int32_t) * L.col.size());
     std::memcpy(out_rowid, L.rowid.data(), sizeof(int32_t) * L.rowid.size());
@@ -20,6 +25,11 @@ extern "C" int host_spmv_layout(int rows, const int32_t *rowptr, const int32_t *
         info[4 + 4 * k] = L.reg.cta0[k + 1] - L.reg.cta0[k];
     }
     return 0;
+}
+
+extern "C" int host_spmv_layout(int rows, const int32_t *rowptr, const int32_t *col, int ctas, int32_t *out_rowptr,
+                                int32_t *out_col, int32_t *out_rowid, int32_t *info) {
+    return host_spmv_layout_t(rows, rowptr, col, ctas, 0, out_rowptr, out_col, out_rowid, info, nullptr);
 }
 
 // tile table of the layout above (first stored row of each tile, ntiles + 1

@@ -113,3 +113,34 @@ def test_layout_of_transpose_of_mixed(lib):
     P = synth.mixed_small(0, scale=200)
     for M in (P.A, P.A.T):
         check(M, layout(lib, M, 1216))
+
+
+def test_threaded_copy_is_identical(lib):
+    """The copy into stored order split over host threads gives the same
+    layout as one thread, and every stored value is the entry of its own
+    row and column (values carry their source positions)."""
+    rng = np.random.default_rng(5)
+    A = sp.csr_matrix(synth.powerlaw_rows(rng, 30000, 9000, 300000, max_len=5000))
+    rows, nnz = A.shape[0], A.nnz
+    rp = np.ascontiguousarray(A.indptr, dtype=np.int32)
+    cl = np.ascontiguousarray(A.indices, dtype=np.int32)
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    outs = []
+    for threads in (1, 3, 8):
+        o_rp = np.zeros(rows + 1, np.int32)
+        o_cl = np.zeros(nnz, np.int32)
+        o_id = np.zeros(rows, np.int32)
+        o_v = np.zeros(nnz, np.float64)
+        info = np.zeros(1 + 4 * 10, np.int32)
+        assert lib.host_spmv_layout_t(rows, P(rp), P(cl), 1216, threads, P(o_rp), P(o_cl), P(o_id), P(info),
+                                      P(o_v)) == 0
+        outs.append((o_rp, o_cl, o_id, o_v, info))
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            np.testing.assert_array_equal(a, b)
+    o_rp, o_cl, o_id, o_v, _ = outs[0]
+    src = o_v.astype(np.int64)
+    np.testing.assert_array_equal(cl[src], o_cl)
+    rows_of_src = np.repeat(np.arange(rows), np.diff(A.indptr))
+    rows_of_stored = np.repeat(o_id, np.diff(o_rp))
+    np.testing.assert_array_equal(rows_of_src[src], rows_of_stored)
