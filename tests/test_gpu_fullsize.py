@@ -1,0 +1,78 @@
+"""Parity at the full size of the large mixed-cone program (n = 1e6, m = 2e6,
+nnz = 2e7; power-law rows up to 10^4 nonzeros; zero, nonnegative, SOC and
+exponential cones), the workload bench.py times:
+
+* Sec. 5 equilibration: the GPU's D, E, sigma, rho equal the oracle's to
+  1e-12 (both FP64);
+* the FP64 engine with a tight CG follows the oracle's first two iterations
+  (Eq. "e-SCS" with relaxation, indirect subspace step of Sec. 4.1) to 1e-9
+  relative: every SpMV region (lane groups, shared-memory row tiles, warp and
+  CTA rows), the CG, the SMW step, every cone projection and tau at full
+  size, the second iteration on the carried A z;
+* in the launch configuration bench.py times (FP32 engine, default settings)
+  the solve reaches the Sec. 3.5 tests at 1e-4, and its point passes them
+  recomputed on the host in FP64, is within FP32 rounding of K and K*
+  (distance to the cone over the vector's size), and its objective lies in
+  the weak-duality band around the generator's optimum — properties that
+  hold at any size.
+"""
+import numpy as np
+import pytest
+
+from oracle import admm, cones
+from paper_1312_3039_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def scs():
+    from paper_1312_3039_gb300 import build, scs as _scs
+    build.build()
+    return _scs
+
+
+@pytest.fixture(scope="module")
+def prob():
+    return synth.mixed(0)
+
+
+def test_fullsize_scaling_and_first_iterations(scs, prob):
+    P = prob
+    st = admm.Settings(linsys="indirect", cg_rate=0.0, cg_adapt=0.0, cg_tol_rel=1e-14, cg_max_iters=5000)
+    orc = admm.HSDSolver(P.A, P.b, P.c, P.cone, st)
+    with scs.Solver(P.A, P.b, P.c, P.cone, precision=0, cg_rate=0.0, cg_adapt=0.0, cg_tol_rel=1e-13,
+                    cg_max_iters=5000) as g:
+        D, E, sigma, rho = g.scaling()
+        np.testing.assert_allclose(D, orc.D, rtol=1e-12)
+        np.testing.assert_allclose(E, orc.E, rtol=1e-12)
+        assert abs(sigma - orc.sigma) <= 1e-12 * orc.sigma
+        assert abs(rho - orc.rho) <= 1e-12 * orc.rho
+        for k in range(2):
+            g.iterate(1)
+            orc.step()
+            u, v = g.iterates()
+            eu = np.linalg.norm(u - orc.u) / np.linalg.norm(orc.u)
+            ev = np.linalg.norm(v - orc.v) / max(np.linalg.norm(orc.v), 1e-300)
+            assert eu <= 1e-9 and ev <= 1e-9, (k + 1, eu, ev)
+
+
+def test_fullsize_fp32_solve(scs, prob):
+    P = prob
+    st, x, y, s, info = scs.solve(P.A, P.b, P.c, P.cone, precision=1, max_iters=100000, time_limit_s=300)
+    assert st == scs.SOLVED, info
+    eps, slack = 1e-4, 1.001
+    nb, nc = np.linalg.norm(P.b), np.linalg.norm(P.c)
+    rp = np.linalg.norm(P.A @ x + s - P.b)
+    rd = np.linalg.norm(P.A.T @ y + P.c)
+    cx, by = P.c @ x, P.b @ y
+    assert rp <= eps * (1 + nb) * slack
+    assert rd <= eps * (1 + nc) * slack
+    assert abs(cx + by) <= eps * (1 + abs(cx) + abs(by)) * slack
+    # s in K and y in K* up to FP32 rounding of the iterates
+    assert np.linalg.norm(s - cones.proj_K(s, P.cone)) <= 1e-5 * (1 + np.linalg.norm(s))
+    assert np.linalg.norm(y - cones.proj_Kdual(y, P.cone)) <= 1e-5 * (1 + np.linalg.norm(y))
+    # weak duality around the generator's optimum
+    band = 1e-9 * (1 + abs(P.p_star))
+    assert P.p_star - cx <= np.linalg.norm(P.y_star) * rp + band
+    assert cx - P.p_star <= abs(cx + by) + np.linalg.norm(P.x_star) * rd + band
