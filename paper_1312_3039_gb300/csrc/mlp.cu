@@ -20,8 +20,10 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -508,7 +510,9 @@ inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
 // tensor map of a row-major BF16 matrix (rows x cols, leading dimension ld
 // elements) read in boxes of box_rows x 64 with the 128-byte swizzle
 inline CUtensorMap tc_map(const __nv_bfloat16 *p, int rows, int cols, int ld, int box_rows) {
+    static std::mutex mu;
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    std::lock_guard<std::mutex> lock(mu);
     if (!encode) {
         cudaDriverEntryPointQueryResult q;
         void *fn = nullptr;
@@ -531,19 +535,26 @@ inline CUtensorMap tc_map(const __nv_bfloat16 *p, int rows, int cols, int ld, in
 template <typename Epi, int BNt>
 void launch_tc(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, int M, int N, int K, Epi epi, int *err,
                cudaStream_t stream) {
-    static bool attr = false;
-    static int sms = 0;
-    if (!attr) {
-        SCS_CUDA(cudaFuncSetAttribute(gemm_nt_tc_kernel<Epi, BNt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      tc_smem<BNt>()));
-        int dev = 0;
-        SCS_CUDA(cudaGetDevice(&dev));
-        SCS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        attr = true;
+    // per device: the kernel's shared-memory attribute set once, its SM count
+    constexpr int kDevs = 64;
+    static std::mutex mu;
+    static int sms[kDevs] = {};
+    int dev = 0;
+    SCS_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kDevs) throw CudaError("device index beyond the product's table", SCS_INVALID_INPUT);
+    int nsm = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!sms[dev]) {
+            SCS_CUDA(cudaFuncSetAttribute(gemm_nt_tc_kernel<Epi, BNt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          tc_smem<BNt>()));
+            SCS_CUDA(cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev));
+        }
+        nsm = sms[dev];
     }
     const CUtensorMap ma = tc_map(A, M, K, lda, TBM), mb = tc_map(B, N, K, ldb, BNt);
     const int tiles = (M / TBM) * (N / BNt);
-    gemm_nt_tc_kernel<Epi, BNt><<<std::min(tiles, sms), kTcThreads, tc_smem<BNt>(), stream>>>(ma, mb, M, N, K, epi, err);
+    gemm_nt_tc_kernel<Epi, BNt><<<std::min(tiles, nsm), kTcThreads, tc_smem<BNt>(), stream>>>(ma, mb, M, N, K, epi, err);
 }
 
 // C = A B^T through either kernel; the shape must meet the kernel's tiling
