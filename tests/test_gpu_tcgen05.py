@@ -20,10 +20,12 @@ def env():
     return torch, scs
 
 
-# tiles of 64 (N = 64, 192), 128 (N = 384) and 256 columns (N = 512, 768); K from
-# one k-block to 70 (the stage ring wraps many times)
+# tiles of 64 (N = 64, 192, 4416), 128 (N = 384) and 256 columns (N = 512, 768,
+# 2048); K from one k-block to 70 (the stage ring wraps many times); the last
+# two shapes have more tiles than SMs, so CTAs walk several tiles and
+# alternate their two tensor-memory accumulators
 @pytest.mark.parametrize("M,N,K", [(128, 64, 64), (128, 64, 512), (384, 192, 256), (128, 384, 1024),
-                                   (256, 512, 4480), (384, 768, 192)])
+                                   (256, 512, 4480), (384, 768, 192), (6144, 2048, 128), (2560, 4416, 64)])
 def test_tcgen05_product(env, M, N, K):
     torch, scs = env
     rng = np.random.default_rng(M + N + K)
