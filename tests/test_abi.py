@@ -55,7 +55,8 @@ def test_default_settings(L):
     assert s.precision == 1 and s.normalize == 1
 
 
-@pytest.mark.parametrize("case", ["cone_rows", "row_index", "nonfinite", "alpha", "colptr"])
+@pytest.mark.parametrize("case", ["cone_rows", "row_index", "nonfinite", "alpha", "colptr", "psd_cond", "precision",
+                                  "block_scale", "check_interval", "soc_size", "cg_tol"])
 def test_invalid_input_rejected_on_host(L, case):
     from paper_1312_3039_gb300 import scs, synth
     P = synth.lp(0, n=6, m=10, n_zero=2, density=0.5)
@@ -73,6 +74,30 @@ def test_invalid_input_rejected_on_host(L, case):
     elif case == "colptr":
         A = sp.csc_matrix(A)
         A.indptr[2] = A.indptr[3] + 1
+    elif case == "psd_cond":
+        kw["psd_fp64_cond"] = 0.5
+    elif case == "precision":
+        kw["precision"] = 2
+    elif case == "block_scale":
+        kw["block_scale"] = 3
+    elif case == "check_interval":
+        kw["check_interval"] = 0
+    elif case == "soc_size":
+        cone = synth.Cone(z=2, l=8, q=(0,))
+    elif case == "cg_tol":
+        kw["cg_tol_rel"] = -1.0
     with pytest.raises(scs.ScsError) as ei:
         scs.Solver(A, b, c, cone, **kw)
     assert ei.value.code == scs.INVALID_INPUT
+
+
+def test_psd_order_beyond_the_kernel_is_unsupported(L):
+    """A PSD block of order 1025 (above the kernel's 1024) is refused on the
+    host with SCS_UNSUPPORTED, before any device work."""
+    from paper_1312_3039_gb300 import scs, synth
+    k = 1025
+    m = k * (k + 1) // 2
+    A = sp.csc_matrix((np.ones(3), (np.array([0, 5, m - 1]), np.array([0, 1, 1]))), shape=(m, 2))
+    with pytest.raises(scs.ScsError) as ei:
+        scs.Solver(A, np.zeros(m), np.ones(2), synth.Cone(s=(k,)))
+    assert ei.value.code == scs.UNSUPPORTED
