@@ -101,3 +101,22 @@ def test_psd_order_beyond_the_kernel_is_unsupported(L):
     with pytest.raises(scs.ScsError) as ei:
         scs.Solver(A, np.zeros(m), np.ones(2), synth.Cone(s=(k,)))
     assert ei.value.code == scs.UNSUPPORTED
+
+
+def test_batch_inputs_refused_on_host(L):
+    """scs_batch_init checks every program on the host: a bad program is
+    refused with its index in the message; exponential cones are not taken
+    by the batched solver (SCS_UNSUPPORTED)."""
+    from paper_1312_3039_gb300 import scs, synth
+    good = synth.lp(0, n=6, m=10, n_zero=2, density=0.5)
+    bad = synth.lp(1, n=6, m=10, n_zero=2, density=0.5)
+    A = sp.csc_matrix(bad.A.copy())
+    A.indices[0] = 99
+    with pytest.raises(scs.ScsError) as ei:
+        scs.Batch([(good.A, good.b, good.c, good.cone), (A, bad.b, bad.c, bad.cone)])
+    assert ei.value.code == scs.INVALID_INPUT
+    assert "program 1" in str(ei.value)
+    P = synth.random_cone(3, n=12, cone=synth.Cone(l=6, ep=2))
+    with pytest.raises(scs.ScsError) as ei:
+        scs.Batch([(P.A, P.b, P.c, P.cone)])
+    assert ei.value.code == scs.UNSUPPORTED
