@@ -120,3 +120,35 @@ def test_batch_inputs_refused_on_host(L):
     with pytest.raises(scs.ScsError) as ei:
         scs.Batch([(P.A, P.b, P.c, P.cone)])
     assert ei.value.code == scs.UNSUPPORTED
+
+
+def test_family_and_network_inputs_refused_on_host(L):
+    """scs_family_init refuses cones other than zero / nonnegative / SOC and
+    bad data on the host; scs_mlp_create refuses a batch that is not a
+    positive multiple of 128 before allocating anything; the product entry
+    point refuses shapes outside its tiling and unaligned operands before
+    any launch."""
+    import ctypes
+    from paper_1312_3039_gb300 import scs, synth
+    P = synth.random_cone(3, n=12, cone=synth.Cone(l=6, ep=2))
+    with pytest.raises(scs.ScsError) as ei:
+        scs.Family(P.A, P.cone, P.b[None, :], P.c[None, :])
+    assert ei.value.code == scs.UNSUPPORTED
+    Q = synth.lp(0, n=6, m=10, n_zero=2, density=0.5)
+    bq = Q.b.copy()
+    bq[0] = np.inf
+    with pytest.raises(scs.ScsError) as ei:
+        scs.Family(Q.A, Q.cone, bq[None, :], Q.c[None, :])
+    assert ei.value.code == scs.INVALID_INPUT
+    err = ctypes.c_int32(0)
+    fake_stream = ctypes.c_void_p(1)          # never used: the sizes are refused first
+    assert not L.scs_mlp_create(64, 512, 3, 4406, 100, fake_stream, ctypes.byref(err))
+    assert err.value == scs.INVALID_INPUT
+    f = L.scs_bf16_gemm_async
+    # 16-byte aligned stand-in addresses: nothing is dereferenced before the checks fail
+    a = 1 << 20
+    assert f(a, 64, a, 64, 100, 64, 64, a, 64, 1, a, None) == scs.INVALID_INPUT      # M % 128
+    assert f(a, 64, a, 64, 128, 72, 64, a, 72, 1, a, None) == scs.INVALID_INPUT      # N % 64
+    assert f(a, 64, a, 64, 128, 64, 48, a, 64, 1, a, None) == scs.INVALID_INPUT      # K % 64 (tcgen05)
+    assert f(a + 8, 64, a, 64, 128, 64, 64, a, 64, 1, a, None) == scs.INVALID_INPUT  # unaligned A
+    assert f(a, 60, a, 64, 128, 64, 64, a, 64, 1, a, None) == scs.INVALID_INPUT      # lda % 8
