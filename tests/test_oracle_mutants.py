@@ -1,0 +1,134 @@
+"""The oracle's pins catch plausible mistakes: each case plants one mistake
+in the oracle (a flipped sign, a dropped term or factor, a swapped operand, a
+missing clip) and runs the pin that guards that step; the pin must fail.
+
+Planted only in the oracle, on the CPU (monkeypatch, undone after each case).
+"""
+import numpy as np
+import pytest
+
+from oracle import admm, cones
+
+import test_oracle_admm as pins_admm
+import test_oracle_cones as pins_cones
+
+
+# ---- subspace step (Sec. 4.1) ------------------------------------------------
+
+def iq_gamma_sign(self, w, k=None):
+    n, m = self.n, self.m
+    wxy, wt = w[:n + m], w[-1]
+    z = self._solve_M(wxy - wt * self.h, k)
+    ut_xy = z + self.p * (float(self.h @ z) / self.hp1)          # planted: + instead of -
+    ut_t = wt + float(self.c @ ut_xy[:n]) + float(self.b @ ut_xy[n:])
+    return np.concatenate([ut_xy, [ut_t]])
+
+
+def iq_tau_drops_b(self, w, k=None):
+    n, m = self.n, self.m
+    wxy, wt = w[:n + m], w[-1]
+    z = self._solve_M(wxy - wt * self.h, k)
+    ut_xy = z - self.p * (float(self.h @ z) / self.hp1)
+    ut_t = wt + float(self.c @ ut_xy[:n])                       # planted: b^T u~_y dropped
+    return np.concatenate([ut_xy, [ut_t]])
+
+
+_solve_M = admm.HSDSolver._solve_M
+
+
+def solve_M_zy_sign(self, r, k):
+    z = _solve_M(self, r, k).copy()
+    z[self.n:] = -z[self.n:]                                    # planted: sign of z_y
+    return z
+
+
+# ---- the iteration (Eq. "e-SCS" with relaxation) -------------------------------
+
+def step_relax_swapped(self):
+    self.k += 1
+    w = self.u + self.v
+    if self.st.linsys == "indirect":
+        self._wnorm = float(np.linalg.norm(w))
+    ut = self.solve_IQ(w, self.k)
+    a = self.st.alpha
+    ubar = (1.0 - a) * ut + a * self.u                          # planted: weights swapped
+    u_new = self.proj_C(ubar - self.v)
+    v_new = self.v - ubar + u_new
+    self.u, self.v = u_new, v_new
+
+
+def step_dual_sign(self):
+    self.k += 1
+    w = self.u + self.v
+    if self.st.linsys == "indirect":
+        self._wnorm = float(np.linalg.norm(w))
+    ut = self.solve_IQ(w, self.k)
+    a = self.st.alpha
+    ubar = a * ut + (1.0 - a) * self.u
+    u_new = self.proj_C(ubar - self.v)
+    v_new = self.v + ubar - u_new                               # planted: signs of the dual update
+    self.u, self.v = u_new, v_new
+
+
+def proj_C_tau_unclipped(self, x):
+    n, m = self.n, self.m
+    out = np.empty_like(x)
+    out[:n] = x[:n]
+    out[n:n + m] = cones.proj_Kdual(x[n:n + m], self.cone)
+    out[-1] = x[-1]                                             # planted: tau not kept >= 0
+    return out
+
+
+# ---- cone projections -------------------------------------------------------
+
+_proj_soc, _proj_exp = cones.proj_soc, cones.proj_exp
+
+
+def soc_half_dropped(v):
+    p = _proj_soc(v)
+    t, x = v[0], v[1:]
+    if abs(t) < np.linalg.norm(x):
+        return 2.0 * p                                          # planted: the 1/2 of (t + ||x||)/2 dropped
+    return p
+
+
+def psd_abs_eigenvalues(v, k):
+    lam, Q = np.linalg.eigh(cones.smat(v, k))
+    return cones.svec((Q * np.abs(lam)) @ Q.T)                  # planted: |lambda| instead of max(lambda, 0)
+
+
+def exp_dual_moreau_sign(v):
+    return np.asarray(v, dtype=float) - _proj_exp(-np.asarray(v, dtype=float))   # planted: w - Pi(-w)
+
+
+# ---- equilibration (Sec. 5) ---------------------------------------------------
+
+_equilibrate = admm.equilibrate
+
+
+def equilibrate_b_unscaled(*args, **kw):
+    Ah, bh, ch, D, E, sigma, rho = _equilibrate(*args, **kw)
+    return Ah, bh / D, ch, D, E, sigma, rho                     # planted: b^ misses the row scaling D
+
+
+MUTANTS = [
+    ("SMW correction sign", admm.HSDSolver, "solve_IQ", iq_gamma_sign, pins_admm.test_smw_equals_dense_solve),
+    ("tau drops b^T u_y", admm.HSDSolver, "solve_IQ", iq_tau_drops_b, pins_admm.test_smw_equals_dense_solve),
+    ("z_y sign", admm.HSDSolver, "_solve_M", solve_M_zy_sign, pins_admm.test_smw_equals_dense_solve),
+    ("relaxation weights swapped", admm.HSDSolver, "step", step_relax_swapped,
+     pins_admm.test_naive_equals_simplified),
+    ("dual update signs", admm.HSDSolver, "step", step_dual_sign, pins_admm.test_naive_equals_simplified),
+    ("tau not clipped", admm.HSDSolver, "proj_C", proj_C_tau_unclipped, pins_admm.test_infeasible_certificate),
+    ("SOC factor 1/2 dropped", cones, "proj_soc", soc_half_dropped, pins_cones.test_soc_kkt_random),
+    ("PSD keeps |lambda|", cones, "proj_psd", psd_abs_eigenvalues, pins_cones.test_psd_kkt_random),
+    ("exp dual Moreau sign", cones, "proj_exp_dual", exp_dual_moreau_sign, pins_cones.test_exp_dual_kkt_random),
+    ("b^ without D", admm, "equilibrate", equilibrate_b_unscaled, pins_admm.test_scaling_preserves_solution),
+]
+
+
+@pytest.mark.parametrize("name,target,attr,mutant,pin", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pin_catches_mutant(monkeypatch, name, target, attr, mutant, pin):
+    pin()                                   # the pin holds on the oracle as written
+    monkeypatch.setattr(target, attr, mutant)
+    with pytest.raises(AssertionError):
+        pin()
