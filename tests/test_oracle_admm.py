@@ -282,3 +282,26 @@ def test_sdp_solve_known_optimum():
     assert r.status == admm.SOLVED
     assert abs(r.pobj - P.p_star) <= 1e-5 * (1 + abs(P.p_star))
     assert cones.in_K(r.s, P.cone, 1e-7) and cones.in_Kdual(r.y, P.cone, 1e-7)
+
+
+@pytest.mark.parametrize("case", ["lp", "mixed", "soc_exp"])
+def test_returned_point_passes_tests_on_original_data(case):
+    """Sec. 3.5 / Sec. 5: the oracle tests its residuals in scaled coordinates
+    (D, E, sigma, rho); the point it returns must pass the same tests written
+    directly on the original data: ||A x + s - b|| <= eps (1 + ||b||),
+    ||A^T y + c|| <= eps (1 + ||c||), |c^T x + b^T y| <= eps (1 + |c^T x| + |b^T y|)."""
+    if case == "lp":
+        P = synth.lp(2)
+    elif case == "mixed":
+        P = synth.mixed_small(2, scale=500)
+    else:
+        P = synth.random_cone(13, n=30, cone=synth.Cone(z=4, l=20, q=(5, 3, 8), ep=4))
+    st = admm.Settings()
+    r = admm.solve(P.A, P.b, P.c, P.cone, st)
+    assert r.status == admm.SOLVED
+    nb, nc = np.linalg.norm(P.b), np.linalg.norm(P.c)
+    cx, by = P.c @ r.x, P.b @ r.y
+    tol = 1 + 1e-9
+    assert np.linalg.norm(P.A @ r.x + r.s - P.b) <= st.eps_pri * (1 + nb) * tol
+    assert np.linalg.norm(P.A.T @ r.y + P.c) <= st.eps_dual * (1 + nc) * tol
+    assert abs(cx + by) <= st.eps_gap * (1 + abs(cx) + abs(by)) * tol

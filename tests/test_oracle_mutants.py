@@ -1,6 +1,9 @@
 """The oracle's pins catch plausible mistakes: each case plants one mistake
-in the oracle (a flipped sign, a dropped term or factor, a swapped operand, a
-missing clip) and runs the pin that guards that step; the pin must fail.
+in the oracle (a flipped sign, a dropped term or factor, swapped weights, a
+missing clip or scaling) and runs the pin that guards that step; the pin must
+fail.  (Mistakes that only make the method stop later, such as an
+over-reported residual, do not change a correct result and are out of reach
+of result pins.)
 
 Planted only in the oracle, on the CPU (monkeypatch, undone after each case).
 """
@@ -8,9 +11,11 @@ import numpy as np
 import pytest
 
 from oracle import admm, cones
+from oracle import mlp as omlp
 
 import test_oracle_admm as pins_admm
 import test_oracle_cones as pins_cones
+import test_oracle_mlp as pins_mlp
 
 
 # ---- subspace step (Sec. 4.1) ------------------------------------------------
@@ -101,6 +106,31 @@ def exp_dual_moreau_sign(v):
     return np.asarray(v, dtype=float) - _proj_exp(-np.asarray(v, dtype=float))   # planted: w - Pi(-w)
 
 
+# ---- termination (Sec. 3.5, Sec. 5) -----------------------------------------------
+
+_residuals = admm.HSDSolver.residuals
+
+
+def residuals_pri_without_sigma(self):
+    out = _residuals(self)
+    n, m = self.n, self.m
+    tau = self.u[-1]
+    if tau > 0:
+        r = self.A @ self.u[:n] + self.v[n:n + m] - tau * self.b
+        out["pri"] = np.linalg.norm(r / self.D) / tau              # planted: 1/sigma dropped
+    return out
+
+
+def residuals_dual_without_rho(self):
+    out = _residuals(self)
+    n, m = self.n, self.m
+    tau = self.u[-1]
+    if tau > 0:
+        r = self.At @ self.u[n:n + m] + tau * self.c
+        out["dual"] = np.linalg.norm(r / self.E) / tau             # planted: 1/rho dropped
+    return out
+
+
 # ---- equilibration (Sec. 5) ---------------------------------------------------
 
 _equilibrate = admm.equilibrate
@@ -109,6 +139,38 @@ _equilibrate = admm.equilibrate
 def equilibrate_b_unscaled(*args, **kw):
     Ah, bh, ch, D, E, sigma, rho = _equilibrate(*args, **kw)
     return Ah, bh / D, ch, D, E, sigma, rho                     # planted: b^ misses the row scaling D
+
+
+# ---- warm-start network ---------------------------------------------------------
+
+_gelu_grad = omlp.gelu_grad
+
+
+def gelu_grad_drops_density_term(z):
+    return 0.5 * (1.0 + omlp.erf(z / omlp.SQRT2))                # planted: z phi(z) dropped
+
+
+_adam = omlp.adam
+
+
+def adam_without_bias_correction(params, grads, state, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    # planted: the moments used as they are (no division by 1 - beta^t)
+    if not state:
+        state["t"] = 0
+        state["m"] = [[np.zeros_like(W), np.zeros_like(b)] for W, b in params]
+        state["v"] = [[np.zeros_like(W), np.zeros_like(b)] for W, b in params]
+    state["t"] += 1
+    new = []
+    for li, (layer, grad) in enumerate(zip(params, grads)):
+        pair = []
+        for k in range(2):
+            g = grad[k]
+            m = beta1 * state["m"][li][k] + (1.0 - beta1) * g
+            v = beta2 * state["v"][li][k] + (1.0 - beta2) * g * g
+            state["m"][li][k], state["v"][li][k] = m, v
+            pair.append(layer[k] - lr * m / (np.sqrt(v) + eps))
+        new.append(tuple(pair))
+    return new
 
 
 MUTANTS = [
@@ -123,6 +185,13 @@ MUTANTS = [
     ("PSD keeps |lambda|", cones, "proj_psd", psd_abs_eigenvalues, pins_cones.test_psd_kkt_random),
     ("exp dual Moreau sign", cones, "proj_exp_dual", exp_dual_moreau_sign, pins_cones.test_exp_dual_kkt_random),
     ("b^ without D", admm, "equilibrate", equilibrate_b_unscaled, pins_admm.test_scaling_preserves_solution),
+    ("primal residual without 1/sigma", admm.HSDSolver, "residuals", residuals_pri_without_sigma,
+     lambda: pins_admm.test_returned_point_passes_tests_on_original_data("mixed")),
+    ("dual residual without 1/rho", admm.HSDSolver, "residuals", residuals_dual_without_rho,
+     lambda: pins_admm.test_returned_point_passes_tests_on_original_data("lp")),
+    ("GELU derivative without z phi(z)", omlp, "gelu_grad", gelu_grad_drops_density_term,
+     pins_mlp.test_backward_matches_finite_differences),
+    ("Adam without bias correction", omlp, "adam", adam_without_bias_correction, pins_mlp.test_adam_scalar_quadratic),
 ]
 
 
