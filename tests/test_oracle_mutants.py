@@ -47,6 +47,29 @@ def solve_M_zy_sign(self, r, k):
     return z
 
 
+def pcg_residual_sign(self, t, x0, tol, max_iters):
+    x = x0.copy()
+    r = t - self._G(x)
+    if np.linalg.norm(r) <= tol:
+        return x
+    zr = r / self.pre
+    p = zr.copy()
+    rz = float(r @ zr)
+    for _ in range(max_iters):
+        Gp = self._G(p)
+        a = rz / float(p @ Gp)
+        x += a * p
+        r += a * Gp                                             # planted: residual updated with + a G p
+        self.cg_iters += 1
+        if np.linalg.norm(r) <= tol:
+            break
+        zr = r / self.pre
+        rz_new = float(r @ zr)
+        p = zr + (rz_new / rz) * p
+        rz = rz_new
+    return x
+
+
 # ---- the iteration (Eq. "e-SCS" with relaxation) -------------------------------
 
 def step_relax_swapped(self):
@@ -87,6 +110,14 @@ def proj_C_tau_unclipped(self, x):
 # ---- cone projections -------------------------------------------------------
 
 _proj_soc, _proj_exp = cones.proj_soc, cones.proj_exp
+
+
+def exp_curve_mu_sign(rho, r0, s0, t0):
+    den = rho * rho - rho + 1.0
+    y = ((rho - 1.0) * r0 + s0) / den
+    mu = (r0 - rho * s0) / den
+    with np.errstate(over="ignore", invalid="ignore"):
+        return y * np.exp(rho) + mu * np.exp(-rho) - t0, y       # planted: + mu e^-rho
 
 
 def soc_half_dropped(v):
@@ -189,6 +220,9 @@ MUTANTS = [
      lambda: pins_admm.test_returned_point_passes_tests_on_original_data("mixed")),
     ("dual residual without 1/rho", admm.HSDSolver, "residuals", residuals_dual_without_rho,
      lambda: pins_admm.test_returned_point_passes_tests_on_original_data("lp")),
+    ("exp curve: sign of mu e^-rho", cones, "_exp_h", exp_curve_mu_sign, pins_cones.test_exp_kkt_random),
+    ("CG residual update sign", admm.HSDSolver, "_pcg", pcg_residual_sign,
+     pins_admm.test_direct_and_tight_indirect_agree),
     ("GELU derivative without z phi(z)", omlp, "gelu_grad", gelu_grad_drops_density_term,
      pins_mlp.test_backward_matches_finite_differences),
     ("Adam without bias correction", omlp, "adam", adam_without_bias_correction, pins_mlp.test_adam_scalar_quadratic),
