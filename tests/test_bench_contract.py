@@ -42,3 +42,29 @@ def test_reference_line():
 def test_reference_other_ranks_are_silent():
     lines = run({"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"})
     assert lines == []
+
+
+def test_roofline_models():
+    """The algorithmic-byte and flop models bench.py divides by: the CG
+    products of the large mixed program move 8 nnz + 4(m+1) + 4n + 4m bytes
+    (q = A p) and 8 nnz + 4(n+1) + 4m + 24n bytes (A^T q with its CG update),
+    179.9 MB and 195.9 MB; the FP32 ALU peak is 152 SMs x 128 lanes x 2 flops
+    a clock."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class P:
+        m, n = 2_000_000, 1_000_000
+
+        class A:
+            nnz = 19_986_983          # synth.mixed(0): 2e7 drawn entries, duplicates merged
+
+    b = bench.spmv_bytes(P, 5, 7)
+    k3 = 8 * P.A.nnz + 4 * (P.m + 1) + 4 * P.n + 4 * P.m
+    k4 = 8 * P.A.nnz + 4 * (P.n + 1) + 4 * P.m + 24 * P.n
+    assert b["per_launch"]["A_cg"] == k3 and b["per_launch"]["At_cg"] == k4
+    assert b[0] == 7 * k3                      # only the CG products q = A p are timed as kind 0
+    k2 = 8 * P.A.nnz + 4 * (P.n + 1) + 4 * P.m + (8 + 8 + 4 + 4) * P.n + 8 * P.n
+    assert b[1] == 5 * k2 + 7 * k4
+    assert (k3, k4) == (179_895_868, 195_895_868)
+    assert abs(bench.fp32_alu_peak_tflops(2070.0) - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
