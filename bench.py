@@ -334,7 +334,10 @@ def run_gb300(args):
     # would replace by a private stream that torch's events do not see)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    common = dict(precision=1, device=local, cuda_stream=stream.cuda_stream)
+    # the small LP runs in FP64 throughout (its parity configuration); the
+    # other programs in the mixed-precision engine
+    prec = 0 if args.workload == "lp" else 1
+    common = dict(precision=prec, device=local, cuda_stream=stream.cuda_stream)
 
     def barrier():
         if world > 1:
@@ -387,7 +390,7 @@ def run_gb300(args):
     # counters include the profiled iterations: take CG steps of those 5 from
     # the launch counts (kind 0 = the CG launches of q = A p)
     cg_prof = prof[0][1]
-    byt = spmv_bytes(P, 5, cg_prof)
+    byt = spmv_bytes(P, 5, cg_prof, elt=8 if prec == 0 else 4)
     kind = 0 if prof[0][0] >= prof[1][0] else 1
     achieved = byt[kind] / (prof[kind][0] / 1e3) / 1e9
     peak, peak_src = measured_hbm_peak()
@@ -471,10 +474,14 @@ def run_gb300(args):
         line = {
             "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32",
             "data": "synthetic (Sec. 6.6 generator, seed %d)" % args.seed,
-            "config": {"workload": desc, "precision": "fp32 A/CG, fp64 iterates and checks",
-                       "l2": "inputs larger than L2 (A and A^T in CSR: %.0f MB)" % (2 * 8 * P.A.nnz / 1e6),
+            "config": {"workload": desc,
+                       "precision": "fp64 throughout" if prec == 0 else
+                       "fp32 A, CG and working iterates; fp64 scaling, tau, tests and outputs",
+                       "l2": ("inputs larger than L2 (A and A^T in CSR: %.0f MB)" % (2 * (4 + 4 * (2 - prec)) * P.A.nnz / 1e6)
+                              if 2 * (4 + 4 * (2 - prec)) * P.A.nnz > 129e6 else
+                              "inputs fit in L2 (a parity-size program: no flush, not a headline line)"),
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "cg_steps_per_iter": cg_steps / max(it1 - it0, 1)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
