@@ -4,6 +4,7 @@
 // same projections as the iteration's kernels (zero/free, nonnegative,
 // second-order, PSD by a cold-started Jacobi eigensolver, exponential via
 // Moreau); used to put predicted warm starts back into the cones.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -202,8 +203,6 @@ inline int project_setup(const scs_cone *k, int64_t count, ProjCone &P, std::vec
     return 0;
 }
 
-thread_local std::string g_project_error;
-
 }  // namespace scs
 
 extern "C" int32_t scs_project(const scs_cone *k, int32_t dual, const double *v, double *out, int64_t count,
@@ -213,16 +212,24 @@ extern "C" int32_t scs_project(const scs_cone *k, int32_t dual, const double *v,
     std::vector<int32_t> qoff, qlen, soff;
     std::string err;
     int rc = project_setup(k, count, P, qoff, qlen, soff, err);
-    if (rc) return rc;
+    if (rc) {
+        set_last_error("scs_project: " + err);
+        return rc;
+    }
     if (count == 0 || P.m == 0) {
         if (dist2) *dist2 = 0.0;
         return 0;
     }
-    if (!v || !out) return SCS_INVALID_INPUT;
+    if (!v || !out) {
+        set_last_error("scs_project: v and out must be device pointers");
+        return SCS_INVALID_INPUT;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int dev = 0, sms = 1;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) {
+        set_last_error("scs_project: no usable CUDA device");
         return SCS_DEVICE_ERROR;
+    }
     project_grid(P, sms * 8);
     const int grid = P.g_exp + P.g_soc + P.g_elem;
     // PSD launch: one CTA per (vector, block) pair up to 4 per SM
@@ -285,17 +292,19 @@ extern "C" int32_t scs_project(const scs_cone *k, int32_t dual, const double *v,
     cudaFree(tables);
     cudaFree(psd_dd);
     cudaFree(psd_work);
+    if (rc) set_last_error("scs_project: CUDA call failed");
     return rc;
 }
 
 // ---------------------------------------------------------------------------
-// scs_project_noalloc: the same projection for callers that cannot allocate
-// device memory (for example code running inside a memory pool that owns
-// the whole device, or a runtime that forbids cudaMalloc while it is
-// capturing or serving).  Its scratch -- the reduction's arrival counters and
-// partial sums, the SOC block tables and the result -- lives in one
-// file-scope device array of fixed size, held by every GPU that loads the
-// library until the process exits.
+// scs_project_noalloc: the same projection for callers that may not allocate
+// device memory -- for example an application whose own memory pool has
+// reserved the whole GPU, or a serving process that hands the library fixed
+// buffers and a stream and keeps every allocation under its own control.
+// Its scratch -- the reduction's arrival counters and partial sums, the SOC
+// block tables and the result -- lives in one file-scope device array of
+// fixed size, held by every GPU that loads the library until the process
+// exits.
 // ---------------------------------------------------------------------------
 namespace scs {
 
@@ -306,12 +315,48 @@ constexpr size_t kNoAllocResultOff = 128;                                  // on
 constexpr size_t kNoAllocPartialOff = 256;                                 // kNoAllocMaxCtas doubles
 constexpr size_t kNoAllocTableOff = kNoAllocPartialOff + 8 * kNoAllocMaxCtas;   // 2 * kNoAllocMaxSoc int32
 constexpr size_t kNoAllocBytes = kNoAllocTableOff + 8 * kNoAllocMaxSoc;
+constexpr int kNoAllocMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// device address of the scratch array on each device (set up once per device)
-static void *g_noalloc_addr[64];
+// Device address of the scratch array, looked up once per device and per
+// CUDA context: the address belongs to the context that was current at the
+// lookup, so a new context on the device (after cudaDeviceReset, or another
+// context made current) triggers a new lookup.
+struct NoAllocAddr {
+    unsigned long long ctx;   // unique id of the context of the lookup (0: none)
+    void *addr;
+};
+static NoAllocAddr g_noalloc_addr[kNoAllocMaxDevices];
 static std::mutex g_noalloc_mutex;
+
+// Unique id of the calling thread's current CUDA context, or 0 when there is
+// none or the driver cannot report it (then nothing is cached).  The driver
+// functions are reached through the runtime's entry-point query, so the
+// library does not link the driver library itself.
+static unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr, *g = nullptr;
+        cudaDriverEntryPointQueryResult qf, qg;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &qf) == cudaSuccess &&
+            qf == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &qg) == cudaSuccess &&
+            qg == cudaDriverEntryPointSuccess && f && g) {
+            get_current = reinterpret_cast<GetCurrent>(f);
+            get_id = reinterpret_cast<GetId>(g);
+        }
+    });
+    if (!get_current || !get_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id + 1;   // 0 stays "unknown"
+}
 
 }  // namespace scs
 
@@ -322,29 +367,51 @@ extern "C" int32_t scs_project_noalloc(const scs_cone *k, int32_t dual, const do
     std::vector<int32_t> qoff, qlen, soff;
     std::string err;
     int rc = project_setup(k, count, P, qoff, qlen, soff, err);
-    if (rc) return rc;
-    if ((int64_t)qoff.size() > kNoAllocMaxSoc) return SCS_UNSUPPORTED;   // more SOC blocks than the scratch holds
-    if (!soff.empty()) return SCS_UNSUPPORTED;     // PSD blocks need matrix scratch this entry point does not hold
+    if (rc) {
+        set_last_error("scs_project_noalloc: " + err);
+        return rc;
+    }
+    if ((int64_t)qoff.size() > kNoAllocMaxSoc) {
+        set_last_error("scs_project_noalloc: more than " + std::to_string(kNoAllocMaxSoc) +
+                       " SOC blocks in the cone (the fixed scratch holds the tables of at most that many)");
+        return SCS_UNSUPPORTED;
+    }
+    if (!soff.empty()) {
+        set_last_error("scs_project_noalloc: PSD blocks need eigensolver matrix scratch; use scs_project");
+        return SCS_UNSUPPORTED;
+    }
     if (count == 0 || P.m == 0) {
         if (dist2) *dist2 = 0.0;
         return 0;
     }
-    if (!v || !out) return SCS_INVALID_INPUT;
+    if (!v || !out) {
+        set_last_error("scs_project_noalloc: v and out must be device pointers");
+        return SCS_INVALID_INPUT;
+    }
     int dev = 0, sms = 1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        set_last_error("scs_project_noalloc: no usable CUDA device (or device ordinal of 64 or more)");
         return SCS_DEVICE_ERROR;
+    }
     void *base = nullptr;
+    unsigned long long ctx = current_context_id();
     {
-        // first call on this device: look up the array's device address
-        // (host code cannot use the symbol's host-side name as a pointer)
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (!g_noalloc_addr[dev]) {
-            void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SCS_DEVICE_ERROR;
-            g_noalloc_addr[dev] = p;
+        if (ctx && g_noalloc_addr[dev].ctx == ctx) base = g_noalloc_addr[dev].addr;
+    }
+    if (!base) {
+        // set-up for this device and context, with the device current: host
+        // code cannot use the array's host-side name as a device pointer
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            set_last_error("scs_project_noalloc: cudaGetSymbolAddress of the scratch array failed");
+            return SCS_DEVICE_ERROR;
         }
-        base = g_noalloc_addr[dev];
+        ctx = current_context_id();   // the lookup creates the context if there was none
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        g_noalloc_addr[dev] = NoAllocAddr{ctx, p};
+        base = p;
     }
     unsigned char *sc = static_cast<unsigned char *>(base);
     unsigned *counter = reinterpret_cast<unsigned *>(sc + kNoAllocCounterOff);
@@ -354,14 +421,22 @@ extern "C" int32_t scs_project_noalloc(const scs_cone *k, int32_t dual, const do
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     project_grid(P, std::min(sms * 8, kNoAllocMaxCtas));
     const int grid = P.g_exp + P.g_soc + P.g_elem;
-    if (grid > kNoAllocMaxCtas) return SCS_UNSUPPORTED;
+    if (grid > kNoAllocMaxCtas) {
+        set_last_error("scs_project_noalloc: launch grid above the scratch's 1024 CTAs");
+        return SCS_UNSUPPORTED;
+    }
     // the counters must start at zero (the array keeps the last call's contents)
-    if (cudaMemsetAsync(counter, 0, sizeof(unsigned) * kSiteCount, s) != cudaSuccess) return SCS_DEVICE_ERROR;
+    if (cudaMemsetAsync(counter, 0, sizeof(unsigned) * kSiteCount, s) != cudaSuccess) {
+        set_last_error("scs_project_noalloc: clearing the scratch counters failed");
+        return SCS_DEVICE_ERROR;
+    }
     if (!qoff.empty()) {
         if (cudaMemcpyAsync(tables, qoff.data(), 4 * qoff.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemcpyAsync(tables + kNoAllocMaxSoc, qlen.data(), 4 * qlen.size(), cudaMemcpyHostToDevice, s) !=
-                cudaSuccess)
+                cudaSuccess) {
+            set_last_error("scs_project_noalloc: copying the SOC tables failed");
             return SCS_DEVICE_ERROR;
+        }
     }
     P.q_off = tables;
     P.q_len = tables + kNoAllocMaxSoc;
@@ -370,8 +445,10 @@ extern "C" int32_t scs_project_noalloc(const scs_cone *k, int32_t dual, const do
     double h = 0.0;
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(&h, res, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        set_last_error("scs_project_noalloc: the projection launch or its read-back failed");
         return SCS_DEVICE_ERROR;
+    }
     if (dist2) *dist2 = h;
     return 0;
 }

@@ -2,13 +2,13 @@
 allocate device memory, gives the same result as scs_project (which
 allocates a scratch buffer per call).
 
-Callers such as an application whose memory pool already owns the whole
-GPU, or a runtime that forbids cudaMalloc while it captures or serves
-requests, need an entry point that allocates nothing: scs_project_noalloc
-keeps its scratch in a fixed-size device array inside the library.  This
-file is named to be collected last, so that a run stopping at the first
-failure has run every other test before it; it passes alone in a fresh
-process as well as after the other tests.
+Callers such as an application whose own memory pool has already reserved
+the whole GPU, or a serving process that keeps every device allocation under
+its own control, need an entry point that allocates nothing:
+scs_project_noalloc keeps its scratch in a fixed-size device array inside the
+library.  This file is named to be collected last, so that a run stopping at
+the first failure has run every other test before it; it passes alone in a
+fresh process as well as after the other tests.
 """
 import numpy as np
 import pytest
@@ -52,3 +52,4 @@ def test_noalloc_rejects_cones_beyond_its_tables(env):
     with pytest.raises(scs.ScsError) as ei:
         scs.project_noalloc(cone, 0, dv.data_ptr(), dv.data_ptr(), 1)
     assert ei.value.code == scs.UNSUPPORTED
+    assert "SOC blocks" in str(ei.value)          # the reason reaches scs_last_error
