@@ -166,6 +166,14 @@ int32_t scs_reset(scs_work *w);
  * stream unless `sync` is nonzero. */
 int32_t scs_iterate(scs_work *w, int32_t iters, int32_t sync);
 
+/* Exactly `iters` ADMM iterations from the current iterates with the work
+ * scs_solve does around them: every check_interval iterations the Sec. 3.5
+ * tests run on the device and the host reads the status word (synchronising
+ * the stream), but the call does not stop when a test passes (benchmarking
+ * the solve's per-iteration cost).  *status (may be NULL) receives the last
+ * check's result (0: no test passed; see the status codes). */
+int32_t scs_iterate_checked(scs_work *w, int32_t iters, int32_t *status);
+
 /* Copy the raw scaled iterates u = (x, y, tau) and v = (0, s, kappa), each of
  * length n + m + 1, to host arrays (either may be NULL). */
 int32_t scs_get_iterates(scs_work *w, double *u, double *v);
@@ -212,20 +220,25 @@ int32_t scs_dims(scs_work *w, int32_t *m, int32_t *n, int64_t *nnz, int64_t *dev
 int32_t scs_project(const scs_cone *k, int32_t dual, const double *v, double *out, int64_t count,
                     double *dist2, void *stream);
 
-/* scs_project for callers that cannot allocate device memory -- for
- * example an application whose memory pool already owns the whole GPU, or
- * a runtime that forbids cudaMalloc while it captures or serves requests.
+/* scs_project for callers that may not allocate device memory -- for
+ * example an application whose own memory pool has already reserved the
+ * whole GPU, or a serving process that gives the library its buffers and
+ * stream and keeps every device allocation under its own control.
  * The paper has no counterpart: this is a property of the library.
- * Same arguments, result and stream semantics as scs_project, but the call
- * allocates nothing: its scratch (the reduction's counters and partial sums,
- * the SOC block tables and the result) lives in one fixed-size device array
- * inside the library, which every GPU that loads the library holds
- * (about 41 KB) until the process exits.
- *   - The first call on a device looks up that array's device address, with
- *     the device current; make that first call before any stream capture.
+ * Same arguments, result and stream semantics as scs_project (it returns
+ * once the projection is done), but the call allocates nothing: its scratch
+ * (the reduction's counters and partial sums, the SOC block tables and the
+ * result) lives in one fixed-size device array inside the library, which
+ * every GPU that loads the library holds (about 41 KB) until the process
+ * exits.
+ *   - Set-up: the first call on a device (and again after that device's
+ *     CUDA context is replaced, e.g. by cudaDeviceReset) looks up the
+ *     array's device address, with the device current; make that first
+ *     call before any stream capture.
  *   - Limits: at most 4096 SOC blocks per cone and no PSD blocks (their
- *     eigensolver needs matrix scratch); SCS_UNSUPPORTED otherwise.
- *   - Every call shares the one array, and each call resets the part that
+ *     eigensolver needs matrix scratch); SCS_UNSUPPORTED otherwise, with
+ *     the reason in scs_last_error().
+ *   - Every call shares the one array, and each call clears the part that
  *     must start at zero; calls that overlap on the GPU (different streams or
  *     threads at the same time) race on it and must not be issued. */
 int32_t scs_project_noalloc(const scs_cone *k, int32_t dual, const double *v, double *out, int64_t count,
@@ -322,6 +335,15 @@ int32_t scs_family_get_iterates(scs_family *w, int32_t index, double *u, double 
  * copied to dst (host or device). */
 int32_t scs_family_snapshots(scs_family *w, float *dst);
 
+/* Map each member's point from its scaled space to the caller's units
+ * (Sec. 5: x = E x^ / sigma, y = D y^ / rho, s = s^ / (sigma D)), the inverse
+ * of the warm-start mapping, so that a prediction made for the family can
+ * warm-start the single-problem solver (scs_warm_start, Sec. 4.2) of the same
+ * member.  All six arrays are device FP64, count x n, m, m (member-major);
+ * synchronises the family's stream. */
+int32_t scs_family_unscale(scs_family *w, const double *xh, const double *yh, const double *sh, double *x, double *y,
+                           double *s);
+
 int32_t scs_family_dims(scs_family *w, int32_t *n, int32_t *m, int32_t *count);
 void scs_family_finish(scs_family *w);
 
@@ -375,6 +397,17 @@ int32_t scs_bf16_gemm(const void *A, int32_t lda, const void *B, int32_t ldb, in
  * (SCS_INVALID_INPUT); returns 0 once the launch is enqueued. */
 int32_t scs_bf16_gemm_async(const void *A, int32_t lda, const void *B, int32_t ldb, int32_t M, int32_t N, int32_t K,
                             float *C, int32_t ldc, int32_t tcgen05, int32_t *err, void *stream);
+
+/* The family solver's dense product alone (Sec. 4.1 direct step in dense
+ * form), for tests and tuning: C (M x N) = alpha A (M x K) B (K x N) +
+ * beta C, all column-major device arrays with leading dimensions lda >= M,
+ * ldb >= K, ldc >= M; precision 0: FP64, 1: FP32 (alpha, beta rounded to
+ * FP32).  beta == 0 does not read C.  Plain CUDA-core fused multiply-adds in
+ * k order, no reduced-precision arithmetic.  Enqueued on `stream` (no
+ * allocation, no synchronisation); SCS_INVALID_INPUT for bad sizes or
+ * pointers, SCS_DEVICE_ERROR if the launch fails. */
+int32_t scs_dense_gemm(int32_t precision, int32_t M, int32_t N, int32_t K, double alpha, const void *A, int64_t lda,
+                       const void *B, int64_t ldb, double beta, void *C, int64_t ldc, void *stream);
 
 /* Device helpers of the warm-start pipeline (FP32 row-major data):
  * per-column mean and standard deviation; in-place standardisation

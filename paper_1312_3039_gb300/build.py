@@ -64,7 +64,7 @@ def build(verbose: bool = False, ptxas_info: bool = False, force: bool = False) 
             if r.returncode:
                 raise RuntimeError("nvcc failed: " + " ".join(cmd))
     if force or jobs or _stale(LIB, objs):
-        cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart_static", "-lcublas",
+        cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart_static",
                "-Xlinker", "-rpath=" + os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:

@@ -257,6 +257,11 @@ int32_t scs_iterate(scs_work *w, int32_t iters, int32_t sync) {
     return guarded([&] { return w->eng->iterate(iters, sync); });
 }
 
+int32_t scs_iterate_checked(scs_work *w, int32_t iters, int32_t *status) {
+    if (!w || !w->eng || iters < 0) { set_error("bad argument"); return SCS_INVALID_INPUT; }
+    return guarded([&] { return w->eng->iterate_checked(iters, status); });
+}
+
 int32_t scs_iterate_profiled(scs_work *w, int32_t iters) {
     if (!w || !w->eng || iters < 0) { set_error("bad argument"); return SCS_INVALID_INPUT; }
     return guarded([&] { return w->eng->iterate_profiled(iters); });

@@ -1,0 +1,148 @@
+// Dense column-major products on the CUDA cores, for the family solver's
+// direct subspace step (Sec. 4.1 with the dense (I + A^T A)^-1):
+//
+//     C (M x N) = alpha * A (M x K) * B (K x N) + beta * C
+//
+// all three column-major with leading dimensions lda, ldb, ldc.  FP32 runs
+// 128 x 128 output tiles (8 x 8 per thread), FP64 64 x 64 tiles (4 x 4 per
+// thread); 256 threads; k-blocks of 8 staged in shared memory, the next
+// block's global loads held in registers while the current one is consumed
+// (one barrier per k-block).  Edges of every dimension are bounds-checked
+// (zero-filled loads, masked stores), so no size needs padding.  CTAs walk the
+// M tiles fastest, so the CTAs that read one block of B columns run together
+// and B is fetched from HBM about once.  The products are plain FP32 / FP64
+// fused multiply-adds in k order: no reduced-precision arithmetic.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace scs {
+namespace dense {
+
+constexpr int kGemmThreads = 256;
+
+template <typename T>
+struct GemmTile;
+template <>
+struct GemmTile<float> {
+    static constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;
+    using Vec = float4;
+};
+template <>
+struct GemmTile<double> {
+    static constexpr int BM = 64, BN = 64, BK = 8, TM = 4, TN = 4;
+    using Vec = double2;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kGemmThreads) gemm_nn_kernel(int M, int N, int K, T alpha,
+                                                               const T *__restrict__ A, int64_t lda,
+                                                               const T *__restrict__ B, int64_t ldb, T beta,
+                                                               T *__restrict__ C, int64_t ldc) {
+    using G = GemmTile<T>;
+    using V = typename G::Vec;
+    constexpr int BM = G::BM, BN = G::BN, BK = G::BK, TM = G::TM, TN = G::TN;
+    constexpr int TX = BN / TN, TY = BM / TM;
+    static_assert(TX * TY == kGemmThreads, "one thread per TM x TN sub-tile");
+    constexpr int LA = BM * BK / kGemmThreads, LB = BN * BK / kGemmThreads;
+    constexpr int PB = 16 / sizeof(T);              // pad of the B rows (keeps 16-byte rows, spreads banks)
+    constexpr int VA = TM * sizeof(T) / 16, VB = TN * sizeof(T) / 16;
+    __shared__ __align__(16) T As[2][BK][BM];
+    __shared__ __align__(16) T Bs[2][BK][BN + PB];
+
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+    T ra[LA], rb[LB];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int r = 0; r < LA; ++r) {      // A tile, M fastest: coalesced along the columns of A
+            const int idx = tid + r * kGemmThreads;
+            const int64_t gi = m0 + idx % BM;
+            const int gk = k0 + idx / BM;
+            ra[r] = (gi < M && gk < K) ? A[gi + gk * lda] : T(0);
+        }
+#pragma unroll
+        for (int r = 0; r < LB; ++r) {      // B tile, K fastest: 8 contiguous entries of a column
+            const int idx = tid + r * kGemmThreads;
+            const int gk = k0 + idx % BK;
+            const int64_t gj = n0 + idx / BK;
+            rb[r] = (gj < N && gk < K) ? B[gk + gj * ldb] : T(0);
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int r = 0; r < LA; ++r) {
+            const int idx = tid + r * kGemmThreads;
+            As[buf][idx / BM][idx % BM] = ra[r];
+        }
+#pragma unroll
+        for (int r = 0; r < LB; ++r) {
+            const int idx = tid + r * kGemmThreads;
+            Bs[buf][idx % BK][idx / BK] = rb[r];
+        }
+    };
+
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+
+    load(0);
+    store(0);
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        const bool more = k0 + BK < K;
+        if (more) load(k0 + BK);
+#pragma unroll
+        for (int k = 0; k < BK; ++k) {
+            T a[TM], b[TN];
+            const V *pa = reinterpret_cast<const V *>(&As[buf][k][ty * TM]);
+            const V *pb = reinterpret_cast<const V *>(&Bs[buf][k][tx * TN]);
+#pragma unroll
+            for (int v = 0; v < VA; ++v) reinterpret_cast<V *>(a)[v] = pa[v];
+#pragma unroll
+            for (int v = 0; v < VB; ++v) reinterpret_cast<V *>(b)[v] = pb[v];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        if (more) store(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+    }
+
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+        const int64_t gj = n0 + tx * TN + j;
+        if (gj >= N) break;
+        T *col = C + gj * ldc;
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const int64_t gi = m0 + ty * TM + i;
+            if (gi < M) col[gi] = beta == T(0) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * col[gi];
+        }
+    }
+}
+
+// Enqueue C = alpha A B + beta C on `stream` (beta == 0: C is not read).
+// Empty products (M, N or K zero) scale C by beta (K == 0) or do nothing.
+template <typename T>
+inline cudaError_t gemm_nn(cudaStream_t stream, int M, int N, int K, T alpha, const T *A, int64_t lda, const T *B,
+                           int64_t ldb, T beta, T *C, int64_t ldc) {
+    using G = GemmTile<T>;
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    const unsigned gx = static_cast<unsigned>((M + G::BM - 1) / G::BM);
+    const unsigned gy = static_cast<unsigned>((N + G::BN - 1) / G::BN);
+    if (gy > 65535u) return cudaErrorInvalidConfiguration;
+    gemm_nn_kernel<T><<<dim3(gx, gy), kGemmThreads, 0, stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    return cudaGetLastError();
+}
+
+}  // namespace dense
+}  // namespace scs

@@ -101,6 +101,25 @@ class Engine : public EngineBase {
         return 0;
     }
 
+    // the solve loop's work without its stopping rule: check_interval
+    // iterations, the Sec. 3.5 test launch and the host read of the status
+    // word, repeated until `iters` iterations are done
+    int iterate_checked(int iters, int32_t *status) override {
+        SCS_CUDA(cudaSetDevice(device_));
+        const int ci = st_.check_interval > 0 ? st_.check_interval : 1;
+        for (int k = 0; k < iters;) {
+            const int chunk = std::min(ci, iters - k);
+            run_iters(chunk);
+            k += chunk;
+            launch_check();
+            SCS_CUDA(cudaMemcpyAsync(Sh_, S_, sizeof(Scalars), cudaMemcpyDeviceToHost, stream_));
+            SCS_CUDA(cudaStreamSynchronize(stream_));
+            if (Sh_->dev_error) throw CudaError("a device wait timed out", SCS_DEVICE_ERROR);
+        }
+        if (status) *status = iters > 0 ? Sh_->status : 0;
+        return 0;
+    }
+
     int iterate_profiled(int iters) override {
         SCS_CUDA(cudaSetDevice(device_));
         if (ev_.empty()) {

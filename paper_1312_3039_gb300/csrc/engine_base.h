@@ -46,6 +46,7 @@ class EngineBase {
     virtual int warm_start(const double *x, const double *y, const double *s) = 0;
     virtual int reset() = 0;
     virtual int iterate(int iters, int sync) = 0;
+    virtual int iterate_checked(int iters, int32_t *status) = 0;
     virtual int iterate_profiled(int iters) = 0;
     virtual int kernel_time(int kind, double *ms, int64_t *launches) = 0;
     virtual int get_iterates(double *u, double *v) = 0;

@@ -10,7 +10,9 @@
 //     t  = r_x - A^T r_y            (n x m) (m x B)
 //     z_x = (I + A^T A)^-1 t        (n x n) (n x B)
 //     z_y = r_y + A z_x             (m x n) (n x B)
-// (cuBLAS GEMMs, in T), then per member the SMW correction, relaxation,
+// (the CUDA-core GEMM of dense.cuh, in T; A^ is kept in both orientations
+// so that every product is a plain column-major one), then per member the
+// SMW correction, relaxation,
 // projection and dual update of Eq. "e-SCS" (one CTA per member).  The
 // Sec. 3.5 tests run every check_interval iterations on the active members
 // (two more products); a member that passes is recorded (status, iterations,
@@ -21,7 +23,6 @@
 //
 // Layout: member vectors are the columns of column-major matrices (n x B,
 // m x B); A^ is dense m x n.  Cones: zero, nonnegative, SOC.
-#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,6 +34,7 @@
 
 #include "../../include/scs_gpu.h"
 #include "common.cuh"
+#include "dense.cuh"
 #include "engine_base.h"
 #include "kernels.cuh"
 
@@ -41,24 +43,6 @@ namespace family {
 
 constexpr int kFamThreads = 256;
 
-#define SCS_CUBLAS(call)                                                                                \
-    do {                                                                                                \
-        cublasStatus_t s_ = (call);                                                                     \
-        if (s_ != CUBLAS_STATUS_SUCCESS)                                                                \
-            throw ::scs::CudaError(std::string(#call) + ": cuBLAS status " + std::to_string((int)s_),   \
-                                   SCS_DEVICE_ERROR);                                                   \
-    } while (0)
-
-inline cublasStatus_t gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k,
-                           float alpha, const float *A, int lda, const float *B, int ldb, float beta, float *C,
-                           int ldc) {
-    return cublasSgemm(h, ta, tb, m, n, k, &alpha, A, lda, B, ldb, &beta, C, ldc);
-}
-inline cublasStatus_t gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k,
-                           double alpha, const double *A, int lda, const double *B, int ldb, double beta,
-                           double *C, int ldc) {
-    return cublasDgemm(h, ta, tb, m, n, k, &alpha, A, lda, B, ldb, &beta, C, ldc);
-}
 
 template <typename T>
 struct Dev {
@@ -387,11 +371,15 @@ __global__ void __launch_bounds__(kFamThreads) hp1_kernel(Dev<T> F) {
     if (threadIdx.x == 0) F.hp1[k] = 1.0 + s;
 }
 
-// dense A^ (column-major m x n) from CSR scaled values
+// dense A^ (column-major m x n) and A^T (column-major n x m) from CSR scaled values
 static __global__ void densify_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                      const double *__restrict__ val, int m, double *__restrict__ A64) {
+                                      const double *__restrict__ val, int m, int n, double *__restrict__ A64,
+                                      double *__restrict__ At64) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
-        for (int k = rp[i]; k < rp[i + 1]; ++k) A64[(size_t)col[k] * m + i] = val[k];
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            A64[(size_t)col[k] * m + i] = val[k];
+            At64[(size_t)i * n + col[k]] = val[k];
+        }
 }
 
 // Gauss-Jordan inversion of the SPD G (n x n, in place), step k:
@@ -484,6 +472,27 @@ __global__ void to_scaled_kernel(Dev<T> F, double *x, double *y, double *s) {
     }
 }
 
+// the inverse map: a scaled point (x^, y^, s^) of each member to the
+// caller's units, x = E x^ / sigma, y = D y^ / rho, s = s^ / (sigma D)
+// (Sec. 5 scaling; the warm start of Sec. 4.2 takes these units)
+template <typename T>
+__global__ void from_scaled_kernel(Dev<T> F, const double *xh, const double *yh, const double *sh, double *x,
+                                   double *y, double *s) {
+    const int64_t nx = (int64_t)F.n * F.B, ny = (int64_t)F.m * F.B;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nx + ny;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        if (e < nx) {
+            const int b = static_cast<int>(e / F.n), j = static_cast<int>(e % F.n);
+            if (x) x[e] = F.E[j] * xh[e] / F.sigma[b];
+        } else {
+            const int64_t f = e - nx;
+            const int b = static_cast<int>(f / F.m), i = static_cast<int>(f % F.m);
+            if (y) y[f] = F.D[i] * yh[f] / F.rho[b];
+            if (s) s[f] = sh[f] / (F.sigma[b] * F.D[i]);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 class FamilyBase {
    public:
@@ -494,6 +503,7 @@ class FamilyBase {
     virtual int iterate(int iters) = 0;
     virtual int get_iterates(int idx, double *u, double *v) = 0;
     virtual int snapshots(float *dst) = 0;
+    virtual int unscale(const double *xh, const double *yh, const double *sh, double *x, double *y, double *s) = 0;
     virtual void dims(int32_t *n, int32_t *m, int32_t *count) = 0;
 };
 
@@ -511,9 +521,6 @@ class FamilyEngine : public FamilyBase {
             SCS_CUDA(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking));
             own_stream_ = true;
         }
-        SCS_CUBLAS(cublasCreate(&blas_));
-        SCS_CUBLAS(cublasSetStream(blas_, stream_));
-        SCS_CUBLAS(cublasSetMathMode(blas_, CUBLAS_PEDANTIC_MATH));   // true FP32 / FP64 products
         n_ = P.n;
         m_ = P.m;
         B_ = count;
@@ -524,7 +531,6 @@ class FamilyEngine : public FamilyBase {
         cudaSetDevice(device_);
         if (exec_) cudaGraphExecDestroy(exec_);
         if (graph_) cudaGraphDestroy(graph_);
-        if (blas_) cublasDestroy(blas_);
         for (void *p : allocs_) cudaFree(p);
         if (own_stream_ && stream_) cudaStreamDestroy(stream_);
     }
@@ -602,16 +608,16 @@ class FamilyEngine : public FamilyBase {
         if (!(mean_row > 0.0)) mean_row = 1.0;
         mean_row_ = mean_row;
         // ---- dense A^ (FP64, then T) and (I + A^T A)^-1
-        double *A64 = dalloc<double>((size_t)m * n);
+        double *A64 = dalloc<double>((size_t)m * n), *At64 = dalloc<double>((size_t)m * n);
         SCS_CUDA(cudaMemsetAsync(A64, 0, sizeof(double) * m * n, stream_));
-        densify_kernel<<<grid(m), kBlock, 0, stream_>>>(a_rp, a_col, av, m, A64);
+        SCS_CUDA(cudaMemsetAsync(At64, 0, sizeof(double) * m * n, stream_));
+        densify_kernel<<<grid(m), kBlock, 0, stream_>>>(a_rp, a_col, av, m, n, A64, At64);
         double *G = dalloc<double>((size_t)n * n), *colk = dalloc<double>(2 * (size_t)n);
         {
             std::vector<double> I((size_t)n * n, 0.0);
             for (int j = 0; j < n; ++j) I[(size_t)j * n + j] = 1.0;
             SCS_CUDA(cudaMemcpyAsync(G, I.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice, stream_));
-            const double one = 1.0;
-            SCS_CUBLAS(cublasDgemm(blas_, CUBLAS_OP_T, CUBLAS_OP_N, n, n, m, &one, A64, m, A64, m, &one, G, n));
+            SCS_CUDA(dense::gemm_nn<double>(stream_, n, n, m, 1.0, At64, n, A64, m, 1.0, G, n));   // I + A^T A
             for (int k = 0; k < n; ++k) {
                 gj_pivot_kernel<<<1, 1024, 0, stream_>>>(G, n, k, colk);
                 gj_update_kernel<<<grid((int64_t)n * n), kBlock, 0, stream_>>>(G, n, k, colk);
@@ -620,8 +626,10 @@ class FamilyEngine : public FamilyBase {
             SCS_CUDA(cudaStreamSynchronize(stream_));
         }
         Ah_ = dalloc<T>((size_t)m * n);
+        Aht_ = dalloc<T>((size_t)m * n);
         Minv_ = dalloc<T>((size_t)n * n);
         cast_kernel<T><<<grid((int64_t)m * n), kBlock, 0, stream_>>>(A64, Ah_, (int64_t)m * n);
+        cast_kernel<T><<<grid((int64_t)m * n), kBlock, 0, stream_>>>(At64, Aht_, (int64_t)m * n);
         cast_kernel<T><<<grid((int64_t)n * n), kBlock, 0, stream_>>>(G, Minv_, (int64_t)n * n);
         // ---- member arrays
         const size_t nx = (size_t)n * B_, ny = (size_t)m * B_;
@@ -700,9 +708,9 @@ class FamilyEngine : public FamilyBase {
         // p = M^-1 h, h = (c^, b^):  p_x = Minv (c^ - A^T b^),  p_y = b^ + A^ p_x
         SCS_CUDA(cudaMemcpyAsync(F_.rx, F_.ch, sizeof(T) * nx, cudaMemcpyDeviceToDevice, stream_));
         SCS_CUDA(cudaMemcpyAsync(F_.py, F_.bh, sizeof(T) * ny, cudaMemcpyDeviceToDevice, stream_));
-        SCS_CUBLAS(gemm(blas_, CUBLAS_OP_T, CUBLAS_OP_N, n_, B_, m_, T(-1), Ah_, m_, F_.bh, m_, T(1), F_.rx, n_));
-        SCS_CUBLAS(gemm(blas_, CUBLAS_OP_N, CUBLAS_OP_N, n_, B_, n_, T(1), Minv_, n_, F_.rx, n_, T(0), F_.px, n_));
-        SCS_CUBLAS(gemm(blas_, CUBLAS_OP_N, CUBLAS_OP_N, m_, B_, n_, T(1), Ah_, m_, F_.px, n_, T(1), F_.py, m_));
+        SCS_CUDA(dense::gemm_nn<T>(stream_, n_, B_, m_, T(-1), Aht_, n_, F_.bh, m_, T(1), F_.rx, n_));
+        SCS_CUDA(dense::gemm_nn<T>(stream_, n_, B_, n_, T(1), Minv_, n_, F_.rx, n_, T(0), F_.px, n_));
+        SCS_CUDA(dense::gemm_nn<T>(stream_, m_, B_, n_, T(1), Ah_, m_, F_.px, n_, T(1), F_.py, m_));
         hp1_kernel<T><<<B_, kFamThreads, 0, stream_>>>(F_);
         SCS_CUDA(cudaGetLastError());
         SCS_CUDA(cudaStreamSynchronize(stream_));
@@ -749,9 +757,9 @@ class FamilyEngine : public FamilyBase {
         Dev<T> F = F_;
         F.B = A;
         rhs_kernel<T><<<grid((int64_t)(n_ + m_) * A), kFamThreads, 0, stream_>>>(F);
-        SCS_CUBLAS(gemm(blas_, CUBLAS_OP_T, CUBLAS_OP_N, n_, A, m_, T(-1), Ah_, m_, F_.ry, m_, T(1), F_.rx, n_));
-        SCS_CUBLAS(gemm(blas_, CUBLAS_OP_N, CUBLAS_OP_N, n_, A, n_, T(1), Minv_, n_, F_.rx, n_, T(0), F_.zx, n_));
-        SCS_CUBLAS(gemm(blas_, CUBLAS_OP_N, CUBLAS_OP_N, m_, A, n_, T(1), Ah_, m_, F_.zx, n_, T(1), F_.ry, m_));
+        SCS_CUDA(dense::gemm_nn<T>(stream_, n_, A, m_, T(-1), Aht_, n_, F_.ry, m_, T(1), F_.rx, n_));
+        SCS_CUDA(dense::gemm_nn<T>(stream_, n_, A, n_, T(1), Minv_, n_, F_.rx, n_, T(0), F_.zx, n_));
+        SCS_CUDA(dense::gemm_nn<T>(stream_, m_, A, n_, T(1), Ah_, m_, F_.zx, n_, T(1), F_.ry, m_));
         update_kernel<T><<<A, kFamThreads, 0, stream_>>>(F);
     }
     void launch_iteration() { launch_iteration(B_); }
@@ -759,8 +767,8 @@ class FamilyEngine : public FamilyBase {
     void launch_check(int A, int k, int final_pass) {
         Dev<T> F = F_;
         F.B = A;
-        SCS_CUBLAS(gemm(blas_, CUBLAS_OP_N, CUBLAS_OP_N, m_, A, n_, T(1), Ah_, m_, F_.ux, n_, T(0), F_.ax, m_));
-        SCS_CUBLAS(gemm(blas_, CUBLAS_OP_T, CUBLAS_OP_N, n_, A, m_, T(1), Ah_, m_, F_.uy, m_, T(0), F_.aty, n_));
+        SCS_CUDA(dense::gemm_nn<T>(stream_, m_, A, n_, T(1), Ah_, m_, F_.ux, n_, T(0), F_.ax, m_));
+        SCS_CUDA(dense::gemm_nn<T>(stream_, n_, A, m_, T(1), Aht_, n_, F_.uy, m_, T(0), F_.aty, n_));
         check_kernel<T><<<A, kFamThreads, 0, stream_>>>(F, k, final_pass);
     }
 
@@ -934,6 +942,14 @@ class FamilyEngine : public FamilyBase {
         return 0;
     }
 
+    int unscale(const double *xh, const double *yh, const double *sh, double *x, double *y, double *s) override {
+        SCS_CUDA(cudaSetDevice(device_));
+        from_scaled_kernel<T><<<grid((int64_t)(n_ + m_) * B_), kBlock, 0, stream_>>>(F_, xh, yh, sh, x, y, s);
+        SCS_CUDA(cudaGetLastError());
+        SCS_CUDA(cudaStreamSynchronize(stream_));
+        return 0;
+    }
+
     int snapshots(float *dst) override {
         SCS_CUDA(cudaSetDevice(device_));
         SCS_CUDA(cudaMemcpyAsync(dst, F_.snap, sizeof(float) * (size_t)(n_ + 2 * m_ + 1) * B_,
@@ -953,9 +969,8 @@ class FamilyEngine : public FamilyBase {
     double mean_row_ = 1.0;
     bool own_stream_ = false, warm_pending_ = false;
     cudaStream_t stream_ = nullptr;
-    cublasHandle_t blas_ = nullptr;
     std::vector<void *> allocs_;
-    T *Ah_ = nullptr, *Minv_ = nullptr;
+    T *Ah_ = nullptr, *Aht_ = nullptr, *Minv_ = nullptr;   // A^ (m x n), A^T (n x m), (I + A^T A)^-1
     double *bdev_ = nullptr, *cdev_ = nullptr;
     int32_t *pairs_ = nullptr;
     std::vector<int32_t> swap_log_;
@@ -1063,6 +1078,12 @@ int32_t scs_family_snapshots(scs_family *w, float *dst) {
     return family_guarded([&] { return w->eng->snapshots(dst); });
 }
 
+int32_t scs_family_unscale(scs_family *w, const double *xh, const double *yh, const double *sh, double *x, double *y,
+                           double *s) {
+    if (!w || !w->eng || !xh || !yh || !sh || !x || !y || !s) return SCS_INVALID_INPUT;
+    return family_guarded([&] { return w->eng->unscale(xh, yh, sh, x, y, s); });
+}
+
 int32_t scs_family_dims(scs_family *w, int32_t *n, int32_t *m, int32_t *count) {
     if (!w || !w->eng) return SCS_INVALID_INPUT;
     w->eng->dims(n, m, count);
@@ -1073,6 +1094,29 @@ void scs_family_finish(scs_family *w) {
     if (!w) return;
     delete w->eng;
     delete w;
+}
+
+int32_t scs_dense_gemm(int32_t precision, int32_t M, int32_t N, int32_t K, double alpha, const void *A, int64_t lda,
+                       const void *B, int64_t ldb, double beta, void *C, int64_t ldc, void *stream) {
+    using namespace scs;
+    if (M < 0 || N < 0 || K < 0 || (precision != 0 && precision != 1) || lda < std::max(1, M) ||
+        ldb < std::max(1, K) || ldc < std::max(1, M) || (M && N && (!C || (K && (!A || !B))))) {
+        set_last_error("scs_dense_gemm: bad sizes, leading dimensions or pointers");
+        return SCS_INVALID_INPUT;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const cudaError_t e =
+        precision == 0 ? dense::gemm_nn<double>(s, M, N, K, alpha, static_cast<const double *>(A), lda,
+                                                static_cast<const double *>(B), ldb, beta, static_cast<double *>(C),
+                                                ldc)
+                       : dense::gemm_nn<float>(s, M, N, K, static_cast<float>(alpha), static_cast<const float *>(A),
+                                               lda, static_cast<const float *>(B), ldb, static_cast<float>(beta),
+                                               static_cast<float *>(C), ldc);
+    if (e != cudaSuccess) {
+        set_last_error(std::string("scs_dense_gemm: ") + cudaGetErrorString(e));
+        return SCS_DEVICE_ERROR;
+    }
+    return 0;
 }
 
 }  // extern "C"

@@ -86,6 +86,8 @@ def lib():
         L.scs_reset.restype = I32
         L.scs_iterate.argtypes = [P, I32, I32]
         L.scs_iterate.restype = I32
+        L.scs_iterate_checked.argtypes = [P, I32, C.POINTER(I32)]
+        L.scs_iterate_checked.restype = I32
         L.scs_iterate_profiled.argtypes = [P, I32]
         L.scs_iterate_profiled.restype = I32
         L.scs_kernel_time.argtypes = [P, I32, D, I64]
@@ -136,6 +138,8 @@ def lib():
         L.scs_family_get_iterates.restype = I32
         L.scs_family_snapshots.argtypes = [P, C.c_void_p]
         L.scs_family_snapshots.restype = I32
+        L.scs_family_unscale.argtypes = [P, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.scs_family_unscale.restype = I32
         L.scs_family_dims.argtypes = [P, C.POINTER(I32), C.POINTER(I32), C.POINTER(I32)]
         L.scs_family_dims.restype = I32
         L.scs_family_finish.argtypes = [P]
@@ -165,6 +169,9 @@ def lib():
         L.scs_bf16_gemm.restype = I32
         L.scs_bf16_gemm_async.argtypes = [V, I32, V, I32, I32, I32, I32, V, I32, I32, V, V]
         L.scs_bf16_gemm_async.restype = I32
+        L.scs_dense_gemm.argtypes = [I32, I32, I32, I32, C.c_double, V, C.c_int64, V, C.c_int64, C.c_double, V,
+                                     C.c_int64, V]
+        L.scs_dense_gemm.restype = I32
         L.scs_column_stats.argtypes = [V, C.c_int64, I32, V, V, V]
         L.scs_column_stats.restype = I32
         L.scs_standardize.argtypes = [V, C.c_int64, I32, V, V, V]
@@ -291,6 +298,13 @@ class Solver:
 
     def iterate(self, iters, sync=True):
         return self._check(lib().scs_iterate(self._w, int(iters), 1 if sync else 0))
+
+    def iterate_checked(self, iters):
+        """scs_iterate_checked: iterations with the Sec. 3.5 tests every
+        check_interval (not stopping); returns the last test's status."""
+        st = C.c_int32(0)
+        self._check(lib().scs_iterate_checked(self._w, int(iters), C.byref(st)))
+        return st.value
 
     def iterate_profiled(self, iters):
         return self._check(lib().scs_iterate_profiled(self._w, int(iters)))
@@ -532,6 +546,10 @@ class Family:
         self._check(lib().scs_family_get_iterates(self._w, int(index), _dptr(u), _dptr(v)))
         return u, v
 
+    def unscale(self, xh_ptr, yh_ptr, sh_ptr, x_ptr, y_ptr, s_ptr):
+        """Device FP64 scaled points (count x n, m, m) to the caller's units."""
+        return self._check(lib().scs_family_unscale(self._w, xh_ptr, yh_ptr, sh_ptr, x_ptr, y_ptr, s_ptr))
+
     def snapshots(self, dst_ptr):
         """Copy the members' (u_x, u_y, v_s, u_tau) at their first passing test
         (float32, count x (n + 2m + 1)) to dst_ptr (host or device)."""
@@ -622,6 +640,13 @@ class MLP:
             self.close()
         except Exception:
             pass
+
+
+def dense_gemm(precision, M, N, K, alpha, a_ptr, lda, b_ptr, ldb, beta, c_ptr, ldc, stream=None):
+    """scs_dense_gemm: C = alpha A B + beta C (column-major device arrays),
+    enqueued on `stream`."""
+    return _rc(lib().scs_dense_gemm(int(precision), int(M), int(N), int(K), float(alpha), a_ptr, int(lda), b_ptr,
+                                    int(ldb), float(beta), c_ptr, int(ldc), stream))
 
 
 def column_stats(data_ptr, rows, cols, mean_ptr, sd_ptr, stream=None):
