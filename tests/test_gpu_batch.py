@@ -18,7 +18,7 @@ import pytest
 from oracle import admm, cones
 from paper_1312_3039_gb300 import synth
 
-from test_gpu_parity import TIGHT, check_solution
+from test_gpu_parity import TIGHT, check_solution, same_settings, two_point_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -73,27 +73,58 @@ def test_batch_matches_single_solver_fp64(scs):
 
 def test_portfolio_batch_fp32(scs):
     """Every program ends as scs_solve ends it (same status and iteration
-    count: the batch runs the same iteration); the solved ones pass the
-    Sec. 3.5 tests on their own data and match the oracle's objective.  (A
-    few portfolio programs stall near a 1e-3 dual residual and stop at
-    max_iters in both solvers.)"""
+    count: the batch runs the same iteration); with max_iters 50000 every
+    program reaches the Sec. 3.5 tests on its own data, and the objectives
+    are within the two-point weak-duality bound of the FP64 oracle's (the
+    same method and settings)."""
     progs = synth.portfolio_batch(seed=1, count=96, lo=20, hi=200)
-    with scs.Batch(as_tuples(progs), precision=1) as bt:
+    with scs.Batch(as_tuples(progs), precision=1, max_iters=50000) as bt:
         xs, ys, ss, infos = bt.solve()
         cfg = bt.config()
     assert cfg["threads"] in (64, 128, 256, 512) and cfg["row_split"] in (4, 16, 64)
-    solved = [i for i in range(len(progs)) if infos[i]["status"] == 1]
-    assert len(solved) >= 0.9 * len(progs)
-    assert all(f["status"] in (1, 2) for f in infos)
-    for i in solved:
+    assert all(f["status"] == 1 for f in infos), [(i, f["status"]) for i, f in enumerate(infos) if f["status"] != 1]
+    for i in range(len(progs)):
         check_solution(progs[i], xs[i], ys[i], ss[i], cone_tol=1e-5)
     for i in range(0, len(progs), 8):
         P = progs[i]
-        st, x, y, s, info = scs.solve(P.A, P.b, P.c, P.cone, precision=1)
+        st, x, y, s, info = scs.solve(P.A, P.b, P.c, P.cone, precision=1, max_iters=50000)
         assert (infos[i]["status"], infos[i]["iters"]) == (st, info["iters"]), (i, infos[i], info)
-    for i in solved[::16]:
-        ref = admm.solve(progs[i].A, progs[i].b, progs[i].c, progs[i].cone, admm.Settings())
-        assert abs(infos[i]["pobj"] - ref.pobj) <= 1e-3 * (1 + abs(ref.pobj)), (i, infos[i]["pobj"], ref.pobj)
+    for i in range(0, len(progs), 16):
+        P = progs[i]
+        ref = admm.solve(P.A, P.b, P.c, P.cone, same_settings(max_iters=50000))
+        bound = two_point_bound(P, xs[i], ys[i], ss[i], ref.x, ref.y, ref.s)
+        assert abs(infos[i]["pobj"] - ref.pobj) <= 1.01 * bound + 1e-9, (i, infos[i]["pobj"], ref.pobj, bound)
+
+
+def test_slow_portfolio_programs_converge_past_10000_iterations(scs):
+    """Three of the 4096 portfolio programs that stop unfinished at 10000
+    iterations: the FP64 oracle (direct method) stops there too, with the
+    same dual residual, so this is the method's rate on these programs, not
+    the FP32 iterates; given 50000 iterations the FP32 batch, the FP64 batch
+    and the oracle all reach the Sec. 3.5 tests, and the objectives agree
+    within the two-point weak-duality bound."""
+    allp = synth.portfolio_batch(0, count=4096)
+    idx = (13, 25, 55)
+    progs = [allp[i] for i in idx]
+    with scs.Batch(as_tuples(progs), precision=1) as bt:
+        *_r, inf10 = bt.solve()
+    assert all(f["status"] == 2 and f["iters"] == 10000 for f in inf10), inf10
+    with scs.Batch(as_tuples(progs), precision=1, max_iters=50000) as bt:
+        xs, ys, ss, inf32 = bt.solve()
+    with scs.Batch(as_tuples(progs), precision=0, max_iters=50000) as bt:
+        *_r, inf64 = bt.solve()
+    for k, P in enumerate(progs):
+        assert inf32[k]["status"] == 1 and inf32[k]["iters"] > 10000, inf32[k]
+        assert inf64[k]["status"] == 1 and inf64[k]["iters"] > 10000, inf64[k]
+        check_solution(P, xs[k], ys[k], ss[k], cone_tol=1e-5)
+        r10 = admm.solve(P.A, P.b, P.c, P.cone, admm.Settings())
+        assert r10.status == 2 and r10.iters == 10000
+        # the stall is in the dual residual, in the oracle as on the GPU
+        assert abs(r10.res_dual - inf10[k]["res_dual"]) <= 0.05 * r10.res_dual, (r10.res_dual, inf10[k])
+        ref = admm.solve(P.A, P.b, P.c, P.cone, admm.Settings(max_iters=50000))
+        assert ref.status == 1 and ref.iters > 10000
+        bound = two_point_bound(P, xs[k], ys[k], ss[k], ref.x, ref.y, ref.s)
+        assert abs(inf32[k]["pobj"] - ref.pobj) <= 1.01 * bound + 1e-9
 
 
 @pytest.mark.parametrize("precision", [0, 1])

@@ -7,8 +7,16 @@
   cannot grow).
 * Full solves (FP64 and mixed FP32/FP64, the paper's CG schedule) reach the
   Sec. 3.5 tests; the returned point is checked on the CPU against the
-  original data, and its objective against the oracle's within 1e-4
-  relative (plus the generator's known optimum).
+  original data and against the oracle run with the same method and
+  settings (indirect CG, same schedule):
+    - FP64: the same iteration count and the objective within 1e-4
+      relative (the two follow one trajectory);
+    - FP32: the objective difference within the bound weak duality puts on
+      two points with their residuals (two_point_bound), which at eps = 1e-4
+      can exceed 1e-4 relative (the oracle's own 1e-4 point of the 1/500
+      mixed program lies 8e-4 from p*);
+    - both: at eps = 1e-6 the objective within 1e-4 relative of the
+      oracle's at the same eps.
 * Infeasible / unbounded problems return valid certificates (Sec. 2.2).
 """
 import math
@@ -31,6 +39,42 @@ def scs():
 
 
 TIGHT = dict(precision=0, cg_rate=0.0, cg_adapt=0.0, cg_tol_rel=1e-13, cg_max_iters=500)
+
+
+def same_settings(eps=1e-4, **kw):
+    """The oracle with the GPU's default method and settings: indirect CG,
+    zeta^k = (1/k)^1.5 capped at 0.3 x the last step, at most 50 CG steps."""
+    return admm.Settings(linsys="indirect", cg_max_iters=50, eps_pri=eps, eps_dual=eps, eps_gap=eps, **kw)
+
+
+def rel(a, b):
+    return abs(a - b) / (1 + abs(b))
+
+
+def two_point_bound(P, x1, y1, s1, x2, y2, s2):
+    """Weak duality (Sec. 2) bounds how far the objectives of two points can
+    be apart given their residuals: with r_p = A x + s - b, r_d = A^T y + c,
+    g = c^T x + b^T y, s1, s2 in K and y1, y2 in K*,
+        c^T x1 - c^T x2 in [-g2 - e12, g1 + e21],
+        e12 = ||y2|| ||r_p1|| + ||x1|| ||r_d2||
+    (c^T x1 + b^T y2 = y2^T s1 - y2^T r_p1 + x1^T r_d2 and y2^T s1 >= 0)."""
+    def parts(x, y, s):
+        return (np.linalg.norm(P.A @ x + s - P.b), np.linalg.norm(P.A.T @ y + P.c), P.c @ x + P.b @ y,
+                np.linalg.norm(x), np.linalg.norm(y))
+    rp1, rd1, g1, nx1, ny1 = parts(x1, y1, s1)
+    rp2, rd2, g2, nx2, ny2 = parts(x2, y2, s2)
+    return max(g2 + ny2 * rp1 + nx1 * rd2, g1 + ny1 * rp2 + nx2 * rd1)
+
+
+def assert_objective_parity(P, precision, info, x, y, s, ref):
+    """FP64: one trajectory with the oracle; FP32: within two_point_bound."""
+    d = abs(info["pobj"] - ref.pobj)
+    if precision == 0:
+        assert info["iters"] == ref.iters, (info["iters"], ref.iters)
+        assert d <= 1e-4 * (1 + abs(ref.pobj)), (info["pobj"], ref.pobj)
+    else:
+        bound = two_point_bound(P, x, y, s, ref.x, ref.y, ref.s)
+        assert d <= bound * 1.01 + 1e-9 * (1 + abs(ref.pobj)), (info["pobj"], ref.pobj, bound)
 
 
 def trajectory_parity(scs, P, iters=50, tol=1e-9, **gpu_kw):
@@ -137,11 +181,11 @@ def check_solution(P, x, y, s, eps=1e-4, cone_tol=1e-7, slack=1.0001):
 @pytest.mark.parametrize("seed", [0, 1])
 def test_lp_solve(scs, precision, seed):
     P = synth.lp(seed)
-    ref = admm.solve(P.A, P.b, P.c, P.cone, admm.Settings())
+    ref = admm.solve(P.A, P.b, P.c, P.cone, same_settings())
     st, x, y, s, info = scs.solve(P.A, P.b, P.c, P.cone, precision=precision)
     assert st == scs.SOLVED, info
     check_solution(P, x, y, s, cone_tol=1e-5 if precision else 1e-7)
-    assert abs(info["pobj"] - ref.pobj) <= 1e-3 * (1 + abs(ref.pobj))
+    assert_objective_parity(P, precision, info, x, y, s, ref)
     # one A^T product per iteration, the warm-start A product every 20th
     # iteration (A z carried in between), two per CG step
     assert info["matvecs"] == info["iters"] + (info["iters"] + 19) // 20 + 2 * info["cg_iters"]
@@ -154,6 +198,38 @@ def test_mixed_small_solve(scs, precision):
     st, x, y, s, info = scs.solve(P.A, P.b, P.c, P.cone, precision=precision)
     assert st == scs.SOLVED, info
     check_solution(P, x, y, s, cone_tol=1e-5 if precision else 1e-7)
+    ref = admm.solve(P.A, P.b, P.c, P.cone, same_settings())
+    assert_objective_parity(P, precision, info, x, y, s, ref)
+
+
+_TIGHT_REF = {}
+
+
+def tight_problems():
+    return {"lp0": synth.lp(0), "lp1": synth.lp(1),
+            "soc_exp": synth.random_cone(11, n=40, cone=synth.Cone(z=5, l=20, q=(3, 7, 1, 2, 40), ep=8)),
+            "all_cones": synth.random_cone(3, n=60),
+            "sdp": synth.sdp(seed=4, n=60, n_psd=3, order=6, n_nonneg=20, density=0.2, n_ill=1),
+            "mixed_500": synth.mixed_small(1, scale=500)}
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", ["lp0", "lp1", "soc_exp", "all_cones", "sdp", "mixed_500"])
+def test_objective_within_1e4_of_oracle_at_eps_1e6(scs, precision, name):
+    """At eps = 1e-6 the Sec. 3.5 tests leave the objective far less room
+    than 1e-4: both precisions land within 1e-4 relative of the FP64
+    oracle's objective at the same eps (and of the generator's p*)."""
+    P = tight_problems()[name]
+    st, x, y, s, info = scs.solve(P.A, P.b, P.c, P.cone, precision=precision, eps_pri=1e-6, eps_dual=1e-6,
+                                  eps_gap=1e-6, max_iters=100000)
+    assert st == scs.SOLVED, info
+    if name not in _TIGHT_REF:
+        _TIGHT_REF[name] = admm.solve(P.A, P.b, P.c, P.cone, same_settings(1e-6, max_iters=100000))
+    ref = _TIGHT_REF[name]
+    assert ref.status == 1
+    assert rel(info["pobj"], ref.pobj) <= 1e-4, (info["pobj"], ref.pobj)
+    assert rel(info["pobj"], P.p_star) <= 1e-4, (info["pobj"], P.p_star)
+    check_solution(P, x, y, s, eps=1e-6, cone_tol=1e-5 if precision else 1e-7, slack=1.01)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
