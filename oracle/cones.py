@@ -13,6 +13,10 @@ Conventions (the paper does not fix them):
     projection of the matrix.
   * Exponential triples are ordered (x, y, z) as in the definition of Kexp
     (Sec. 6.1).
+  * Power triples (x, y, z) with parameter a in (0, 1):
+    Kpow^a = {x^a y^(1-a) >= |z|, x >= 0, y >= 0} and its dual
+    (Kpow^a)* = {(u/a)^a (v/(1-a))^(1-a) >= |w|, u >= 0, v >= 0} (Sec. 6.1).
+    A cone may also hold Kexp* or (Kpow^a)* itself ("exp_dual", "pow_dual").
 """
 from __future__ import annotations
 
@@ -202,6 +206,102 @@ def proj_exp_dual(v):
     return v + proj_exp(-v)
 
 
+def _pow_dist(v1, v2, w, a, s1, s2):
+    """Upper bound on the distance from (v1, v2, w) to the cone
+    {(v1/s1)^a (v2/s2)^(1-a) >= |w|, v1 >= 0, v2 >= 0}: the smallest of three
+    moves onto it -- negative v1, v2 raised to 0 and |w| lowered to the
+    boundary value; or v1 raised (or v2 raised) until the boundary reaches
+    |w|, with the other entry raised to 0 if negative."""
+    p1, p2 = max(v1, 0.0), max(v2, 0.0)
+    aw = abs(w)
+    r = (p1 / s1) ** a * (p2 / s2) ** (1.0 - a)
+    best = math.sqrt((p1 - v1) ** 2 + (p2 - v2) ** 2 + max(aw - r, 0.0) ** 2)
+    try:
+        if p2 > 0.0:
+            need1 = s1 * (aw / (p2 / s2) ** (1.0 - a)) ** (1.0 / a)
+            best = min(best, math.sqrt(max(need1 - v1, 0.0) ** 2 + (p2 - v2) ** 2))
+        if p1 > 0.0:
+            need2 = s2 * (aw / (p1 / s1) ** a) ** (1.0 / (1.0 - a))
+            best = min(best, math.sqrt((p1 - v1) ** 2 + max(need2 - v2, 0.0) ** 2))
+    except OverflowError:
+        pass
+    return best
+
+
+def in_pow(v, a, tol=0.0):
+    """Membership in Kpow^a = {x^a y^(1-a) >= |z|, x >= 0, y >= 0} up to a
+    distance ``tol * max(1, ||v||)`` (accepted when one of the moves of
+    ``_pow_dist`` reaches the cone within it)."""
+    x, y, z = (float(t) for t in v)
+    slack = tol * max(1.0, math.sqrt(x * x + y * y + z * z))
+    return _pow_dist(x, y, z, a, 1.0, 1.0) <= slack
+
+
+def in_pow_dual(v, a, tol=0.0):
+    """Membership in (Kpow^a)* = {(u/a)^a (v/(1-a))^(1-a) >= |w|, u, v >= 0}
+    (Sec. 6.1), with the same distance test as ``in_pow``."""
+    u, vv, w = (float(t) for t in v)
+    slack = tol * max(1.0, math.sqrt(u * u + vv * vv + w * w))
+    return _pow_dist(u, vv, w, a, a, 1.0 - a) <= slack
+
+
+def _pow_branch(c0, k, r, r0):
+    """The positive root t of t^2 - c0 t - k r (r0 - r) = 0 (k r (r0 - r) >= 0),
+    written without cancellation for c0 < 0."""
+    q = k * r * (r0 - r)
+    d = math.sqrt(c0 * c0 + 4.0 * q)
+    return 0.5 * (c0 + d) if c0 >= 0.0 else 2.0 * q / (d - c0) if d - c0 > 0.0 else 0.0
+
+
+def proj_pow(v, a):
+    """Euclidean projection onto Kpow^a (Sec. 6.1 gives only the cone).
+
+    From the projection's optimality conditions: p = Pi(v) iff p in K,
+    p - v in K* and p.(p - v) = 0.  Cases: v in K; -v in K* (projection 0);
+    z0 = 0 (projection (x0+, y0+, 0)).  Otherwise p lies on the curved
+    boundary x^a y^(1-a) = |z| with z of the sign of z0.  With r = |z| and
+    the multiplier mu of the constraint g = x^a y^(1-a) - |z| >= 0, the
+    stationarity p - v = mu grad g reads
+        x - x0 = mu a r / x,   y - y0 = mu (1 - a) r / y,   r - |z0| = -mu,
+    so mu = |z0| - r and x, y are the positive roots of
+        x^2 - x0 x - a r (|z0| - r) = 0,   y^2 - y0 y - (1-a) r (|z0| - r) = 0;
+    r is the root in (0, |z0|) of phi(r) = x(r)^a y(r)^(1-a) - r, where phi
+    changes sign from >= 0 at r = 0 to < 0 at r = |z0| (v not in K), found
+    by bisection."""
+    x0, y0, z0 = (float(t) for t in v)
+    if in_pow((x0, y0, z0), a):
+        return np.array([x0, y0, z0])
+    if in_pow_dual((-x0, -y0, -z0), a):
+        return np.zeros(3)
+    if z0 == 0.0:
+        return np.array([max(x0, 0.0), max(y0, 0.0), 0.0])
+    r0 = abs(z0)
+
+    def phi(r):
+        x = _pow_branch(x0, a, r, r0)
+        y = _pow_branch(y0, 1.0 - a, r, r0)
+        return x ** a * y ** (1.0 - a) - r, x, y
+
+    lo, hi = 0.0, r0
+    for _ in range(300):
+        mid = 0.5 * (lo + hi)
+        if mid <= lo or mid >= hi:
+            break
+        if phi(mid)[0] > 0.0:
+            lo = mid
+        else:
+            hi = mid
+    r = 0.5 * (lo + hi)
+    _, x, y = phi(r)
+    return np.array([x, y, math.copysign(r, z0)])
+
+
+def proj_pow_dual(v, a):
+    """Moreau (Eq. "e-moreau" applied to K*): Pi_{K*}(w) = w + Pi_K(-w)."""
+    v = np.asarray(v, dtype=float)
+    return v + proj_pow(-v, a)
+
+
 # ---------------------------------------------------------------------------
 # whole-cone projections and membership
 # ---------------------------------------------------------------------------
@@ -222,12 +322,19 @@ def proj_K(v, cone):
             out[off:off + size] = proj_psd(seg, order)
         elif kind == "exp":
             out[off:off + size] = proj_exp(seg)
+        elif kind == "exp_dual":
+            out[off:off + size] = proj_exp_dual(seg)
+        elif kind == "pow":
+            out[off:off + size] = proj_pow(seg, order)
+        elif kind == "pow_dual":
+            out[off:off + size] = proj_pow_dual(seg, order)
     return out
 
 
 def proj_Kdual(v, cone):
     """Euclidean projection onto K*: the dual of {0} is R (free), the
-    nonnegative, second-order and PSD cones are self-dual, Kexp* via Moreau."""
+    nonnegative, second-order and PSD cones are self-dual, Kexp* and
+    (Kpow^a)* via Moreau; the dual of Kexp* is Kexp, of (Kpow^a)* Kpow^a."""
     v = np.asarray(v, dtype=float)
     out = np.empty_like(v)
     for kind, off, size, order in cone.blocks():
@@ -242,6 +349,12 @@ def proj_Kdual(v, cone):
             out[off:off + size] = proj_psd(seg, order)
         elif kind == "exp":
             out[off:off + size] = proj_exp_dual(seg)
+        elif kind == "exp_dual":
+            out[off:off + size] = proj_exp(seg)
+        elif kind == "pow":
+            out[off:off + size] = proj_pow_dual(seg, order)
+        elif kind == "pow_dual":
+            out[off:off + size] = proj_pow(seg, order)
     return out
 
 
@@ -267,6 +380,12 @@ def in_K(v, cone, tol=1e-9):
             return False
         if kind == "exp" and not in_exp(seg, tol):
             return False
+        if kind == "exp_dual" and not in_exp_dual(seg, tol):
+            return False
+        if kind == "pow" and not in_pow(seg, order, tol):
+            return False
+        if kind == "pow_dual" and not in_pow_dual(seg, order, tol):
+            return False
     return True
 
 
@@ -280,5 +399,11 @@ def in_Kdual(v, cone, tol=1e-9):
         if kind == "psd" and not _in_psd(seg, order, tol):
             return False
         if kind == "exp" and not in_exp_dual(seg, tol):
+            return False
+        if kind == "exp_dual" and not in_exp(seg, tol):
+            return False
+        if kind == "pow" and not in_pow_dual(seg, order, tol):
+            return False
+        if kind == "pow_dual" and not in_pow(seg, order, tol):
             return False
     return True

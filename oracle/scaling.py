@@ -51,7 +51,7 @@ def equilibrate(A, b, c, cone, passes=10, lo=1e-4, hi=1e4, block="rms"):
         rn = np.sqrt(np.asarray(sq.sum(axis=1)).ravel())
         cn = np.sqrt(np.asarray(sq.sum(axis=0)).ravel())
         for kind, off, size, _order in cone.blocks():
-            if kind in ("soc", "psd", "exp"):
+            if kind in ("soc", "psd", "exp", "exp_dual", "pow", "pow_dual"):
                 rn[off:off + size] = _block_value(rn[off:off + size], block)
         d = 1.0 / np.sqrt(_clamp(rn, lo, hi))
         e = 1.0 / np.sqrt(_clamp(cn, lo, hi))

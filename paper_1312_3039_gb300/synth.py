@@ -29,18 +29,23 @@ SQRT2 = math.sqrt(2.0)
 
 @dataclass(frozen=True)
 class Cone:
-    """Cone ``K = {0}^z x R+^l x SOC(q_1) x ... x PSD(s_1) x ... x Kexp^ep``."""
+    """Cone ``K = {0}^z x R+^l x SOC(q_1) x ... x PSD(s_1) x ... x Kexp^ep
+    x (Kexp*)^ed x Kpow(p_1) x ...`` (Sec. 6.1).  ``p`` holds one parameter
+    per power triple: a in (0, 1) is the power cone Kpow^a, -a the dual
+    power cone (Kpow^a)*."""
 
     z: int = 0
     l: int = 0
     q: tuple = ()
     s: tuple = ()
     ep: int = 0
+    ed: int = 0
+    p: tuple = ()
 
     @property
     def m(self) -> int:
         return (self.z + self.l + int(sum(self.q))
-                + int(sum(k * (k + 1) // 2 for k in self.s)) + 3 * self.ep)
+                + int(sum(k * (k + 1) // 2 for k in self.s)) + 3 * (self.ep + self.ed + len(self.p)))
 
     def blocks(self):
         """Yield ``(kind, start, size, order)`` for every block, in row order."""
@@ -60,6 +65,15 @@ class Cone:
             off += d
         for _ in range(self.ep):
             yield ("exp", off, 3, 0)
+            off += 3
+        for _ in range(self.ed):
+            yield ("exp_dual", off, 3, 0)
+            off += 3
+        for a in self.p:
+            if a > 0:
+                yield ("pow", off, 3, float(a))
+            else:
+                yield ("pow_dual", off, 3, float(-a))
             off += 3
 
 
@@ -148,6 +162,30 @@ def _pair_exp(rng):
     return s, y
 
 
+def _pair_pow(rng, a):
+    """Boundary of Kpow^a = {x^a y^(1-a) >= |z|, x, y >= 0} (Sec. 6.1):
+    s = (x, y, sigma x^a y^(1-a)); its complementary ray in the dual cone
+    (Kpow^a)* = {(u/a)^a (v/(1-a))^(1-a) >= |w|, u, v >= 0}:
+    y = mu (a r / x, (1 - a) r / y, -sigma) with r = x^a y^(1-a), which is
+    orthogonal to s (a r + (1 - a) r - r = 0) and on the dual boundary
+    ((r/x)^a (r/y)^(1-a) = 1).  Or one side strictly inside, the other 0."""
+    x, y = rng.uniform(0.3, 2.0, size=2)
+    sig = 1.0 if rng.random() < 0.5 else -1.0
+    r = x ** a * y ** (1.0 - a)
+    mu = rng.uniform(0.5, 1.5)
+    u = rng.random()
+    s = np.zeros(3)
+    d = np.zeros(3)
+    if u < 0.15:
+        s[:] = (x, y, sig * r * rng.uniform(0.0, 0.9))
+    elif u < 0.30:
+        d[:] = (mu * a * r / x, mu * (1.0 - a) * r / y, -sig * mu * rng.uniform(0.0, 0.9))
+    else:
+        s[:] = (x, y, sig * r)
+        d[:] = (mu * a * r / x, mu * (1.0 - a) * r / y, -sig * mu)
+    return s, d
+
+
 def _pair_psd(rng, k, ill=False):
     Q, _ = np.linalg.qr(rng.standard_normal((k, k)))
     if ill:
@@ -182,6 +220,12 @@ def complementary_pair(cone: Cone, rng, ill_psd_blocks: int = 0):
             n_psd += 1
         elif kind == "exp":
             s[off:off + 3], y[off:off + 3] = _pair_exp(rng)
+        elif kind == "exp_dual":        # K = Kexp*, K* = Kexp: the roles swap
+            y[off:off + 3], s[off:off + 3] = _pair_exp(rng)
+        elif kind == "pow":
+            s[off:off + 3], y[off:off + 3] = _pair_pow(rng, order)
+        elif kind == "pow_dual":        # K = (Kpow^a)*, K* = Kpow^a
+            y[off:off + 3], s[off:off + 3] = _pair_pow(rng, order)
     return s, y
 
 

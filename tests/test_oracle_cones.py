@@ -8,8 +8,11 @@
   s in K, y in K*, s.y = 0  =>  Pi_K(s - y) = s and Pi_K*(y - s) = y.
 * Closed forms: SOC(2) is the nonnegative orthant rotated by 45 degrees,
   PSD(1) is R+, a 2x2 PSD projection from its explicit eigen-pair formula.
-* Brute force: no point of the exponential cone's boundary is closer to v
-  than the computed projection.
+* Brute force: no point of the exponential (or power) cone's boundary is
+  closer to v than the computed projection.
+* Power cone (Sec. 6.1): the printed dual is the dual (y.s >= 0 over the two
+  sets, complementary boundary rays reach y.s = 0); projections of points in
+  K, in the polar cone and with z = 0 have their closed forms.
 """
 import math
 
@@ -172,10 +175,104 @@ def test_exp_brute_force():
         assert dist <= best + 1e-7, (v, dist, best)
 
 
+POW_A = (0.03, 0.2, 0.5, 0.71, 0.97)
+
+
+def _pow_points(rng, count, a):
+    pts = []
+    for _ in range(count):
+        u = rng.random()
+        if u < 0.6:
+            pts.append(rng.standard_normal(3) * rng.uniform(0.1, 5))
+        elif u < 0.7:      # inside K
+            x, y = rng.uniform(0.1, 3, size=2)
+            pts.append(np.array([x, y, rng.uniform(-1, 1) * x ** a * y ** (1 - a)]))
+        elif u < 0.8:      # inside the polar cone (-v in K*)
+            uu, vv = rng.uniform(0.1, 3, size=2)
+            r = (uu / a) ** a * (vv / (1 - a)) ** (1 - a)
+            pts.append(-np.array([uu, vv, rng.uniform(-1, 1) * r]))
+        elif u < 0.9:      # extreme scales
+            pts.append(rng.standard_normal(3) * 10.0 ** rng.uniform(-6, 6))
+        else:              # one of x, y negative
+            v = rng.standard_normal(3) * 2
+            v[int(rng.integers(0, 2))] = -abs(v[0]) - 0.1
+            pts.append(v)
+    return pts
+
+
+@pytest.mark.parametrize("a", POW_A)
+def test_pow_kkt_random(a):
+    rng = np.random.default_rng(int(a * 1000) + 11)
+    for v in _pow_points(rng, 600, a):
+        p = cones.proj_pow(v, a)
+        kkt_triple(p, v, lambda x, t: cones.in_pow(x, a, t), lambda x, t: cones.in_pow_dual(x, a, t), 1e-12)
+
+
+@pytest.mark.parametrize("a", POW_A)
+def test_pow_dual_kkt_random(a):
+    rng = np.random.default_rng(int(a * 1000) + 12)
+    for v in _pow_points(rng, 400, a):
+        p = cones.proj_pow_dual(v, a)
+        kkt_triple(p, v, lambda x, t: cones.in_pow_dual(x, a, t), lambda x, t: cones.in_pow(x, a, t), 1e-12)
+
+
+def test_pow_dual_reading():
+    """The dual printed in Sec. 6.1 is the dual of Kpow^a: (1) y.s >= 0 for
+    s on the boundary of Kpow^a and y on the printed dual's boundary (by the
+    weighted AM-GM inequality); (2) every boundary ray s = (x, y, sigma r),
+    r = x^a y^(1-a), has the printed-dual ray (a r/x, (1-a) r/y, -sigma)
+    with y.s = 0, so the printed set is not a strict subset of the dual."""
+    rng = np.random.default_rng(13)
+    for _ in range(4000):
+        a = rng.uniform(0.02, 0.98)
+        x, y = rng.uniform(0.01, 5, size=2)
+        sig = rng.choice([-1.0, 1.0])
+        s = np.array([x, y, sig * x ** a * y ** (1 - a)])
+        u, vv = rng.uniform(0.01, 5, size=2)
+        w = rng.choice([-1.0, 1.0]) * (u / a) ** a * (vv / (1 - a)) ** (1 - a)
+        d = np.array([u, vv, w])
+        assert cones.in_pow(s, a, 1e-12) and cones.in_pow_dual(d, a, 1e-12)
+        assert s @ d >= -1e-12 * np.linalg.norm(s) * np.linalg.norm(d)
+        r = x ** a * y ** (1 - a)
+        ray = np.array([a * r / x, (1 - a) * r / y, -sig])
+        assert cones.in_pow_dual(ray, a, 1e-12)
+        assert abs(ray @ s) <= 1e-12 * np.linalg.norm(ray) * np.linalg.norm(s)
+
+
+@pytest.mark.parametrize("a", (0.2, 0.5, 0.83))
+def test_pow_brute_force(a):
+    """No point of the curved boundary (x^a y^(1-a) = |z|, z of either sign)
+    nor of the face {x, y >= 0, z = 0} is closer to v than Pi(v)."""
+    rng = np.random.default_rng(int(a * 100) + 14)
+    for v in [rng.standard_normal(3) * 2 for _ in range(40)]:
+        p = cones.proj_pow(v, a)
+        dist = np.linalg.norm(p - v)
+        best = 0.0 if cones.in_pow(v, a) else np.linalg.norm(np.array([max(v[0], 0), max(v[1], 0), 0.0]) - v)
+        for sig in (-1.0, 1.0):
+            def f(t):
+                x, y = math.exp(t[0]), math.exp(t[1])
+                return np.linalg.norm(np.array([x, y, sig * x ** a * y ** (1 - a)]) - v)
+            for lx in (-3, -1, 0, 1):
+                for ly in (-3, -1, 0, 1):
+                    r = so.minimize(f, [lx, ly], method="Nelder-Mead",
+                                    options=dict(xatol=1e-12, fatol=1e-14, maxiter=4000))
+                    best = min(best, r.fun)
+        assert dist <= best + 1e-7, (v, dist, best)
+
+
+def test_pow_special_cases():
+    a = 0.3
+    v = np.array([2.0, 1.5, 0.7 * 2.0 ** a * 1.5 ** (1 - a)])        # in K: unchanged
+    np.testing.assert_array_equal(cones.proj_pow(v, a), v)
+    w = -np.array([1.0, 2.0, 0.5 * (1 / a) ** a * (2 / (1 - a)) ** (1 - a)])   # -w in K*: projection 0
+    np.testing.assert_array_equal(cones.proj_pow(w, a), np.zeros(3))
+    np.testing.assert_array_equal(cones.proj_pow(np.array([-1.0, 3.0, 0.0]), a), [0.0, 3.0, 0.0])
+
+
 @pytest.mark.parametrize("seed", range(5))
 def test_complementary_pairs_fix_projection(seed):
     rng = np.random.default_rng(100 + seed)
-    cone = synth.Cone(z=3, l=7, q=(3, 6, 2), s=(1, 3, 4), ep=6)
+    cone = synth.Cone(z=3, l=7, q=(3, 6, 2), s=(1, 3, 4), ep=6, ed=3, p=(0.3, -0.6, 0.5, -0.1))
     s, y = synth.complementary_pair(cone, rng, ill_psd_blocks=1)
     assert abs(s @ y) < 1e-10
     np.testing.assert_allclose(cones.proj_K(s - y, cone), s, atol=1e-9)
@@ -185,7 +282,7 @@ def test_complementary_pairs_fix_projection(seed):
 @pytest.mark.parametrize("seed", range(5))
 def test_moreau_mixed(seed):
     rng = np.random.default_rng(200 + seed)
-    cone = synth.Cone(z=3, l=7, q=(3, 6, 2), s=(1, 3, 4), ep=6)
+    cone = synth.Cone(z=3, l=7, q=(3, 6, 2), s=(1, 3, 4), ep=6, ed=3, p=(0.3, -0.6, 0.5, -0.1))
     v = rng.standard_normal(cone.m) * 2
     pk = cones.proj_K(v, cone)
     pd = cones.proj_Kdual(-v, cone)

@@ -172,6 +172,23 @@ def equilibrate_b_unscaled(*args, **kw):
     return Ah, bh / D, ch, D, E, sigma, rho                     # planted: b^ misses the row scaling D
 
 
+# ---- power cone (Sec. 6.1) -------------------------------------------------------
+
+def pow_branch_weights_swapped(v, a):
+    x0, y0, z0 = (float(t) for t in v)
+    return _proj_pow(np.array([x0, y0, z0]), 1.0 - a)              # planted: a and 1 - a swapped
+
+
+_proj_pow = cones.proj_pow
+
+
+def pow_sign_of_z(v, a):
+    p = _proj_pow(v, a).copy()
+    if not cones.in_pow(v, a):
+        p[2] = -p[2]                                               # planted: z takes the wrong sign
+    return p
+
+
 # ---- warm-start network ---------------------------------------------------------
 
 _gelu_grad = omlp.gelu_grad
@@ -221,6 +238,9 @@ MUTANTS = [
     ("dual residual without 1/rho", admm.HSDSolver, "residuals", residuals_dual_without_rho,
      lambda: pins_admm.test_returned_point_passes_tests_on_original_data("lp")),
     ("exp curve: sign of mu e^-rho", cones, "_exp_h", exp_curve_mu_sign, pins_cones.test_exp_kkt_random),
+    ("power cone: weights a, 1 - a swapped", cones, "proj_pow", pow_branch_weights_swapped,
+     lambda: pins_cones.test_pow_kkt_random(0.2)),
+    ("power cone: sign of z", cones, "proj_pow", pow_sign_of_z, lambda: pins_cones.test_pow_kkt_random(0.71)),
     ("CG residual update sign", admm.HSDSolver, "_pcg", pcg_residual_sign,
      pins_admm.test_direct_and_tight_indirect_agree),
     ("GELU derivative without z phi(z)", omlp, "gelu_grad", gelu_grad_drops_density_term,
