@@ -24,7 +24,8 @@
  *     q[0..nq) (head first: {(t, x): ||x|| <= t}), PSD blocks of orders
  *     s[0..ns) in svec form (lower triangle column by column, off-diagonal
  *     entries times sqrt 2), `ep` exponential triples (x, y, z) with
- *     Kexp = closure{y > 0, y e^(x/y) <= z} (Sec. 6.1).
+ *     Kexp = closure{y > 0, y e^(x/y) <= z}, `ed` triples of its dual, and
+ *     one triple per power-cone parameter p[i] (Sec. 6.1).
  *   - Host pointers unless stated.  Inputs are copied during the call; the
  *     caller keeps ownership.  A work object owns all device memory it uses
  *     until scs_finish.
@@ -67,7 +68,12 @@ typedef struct {
     const double *val;
 } scs_csc;
 
-/* K = {0}^z x R+^l x SOC(q_0) x ... x PSD(s_0) x ... x Kexp^ep (Sec. 6.1). */
+/* K = {0}^z x R+^l x SOC(q_0) x ... x PSD(s_0) x ... x Kexp^ep x (Kexp*)^ed
+ * x Kpow(p_0) x ... (Sec. 6.1), rows in that order.  p[i] in (0, 1) is the
+ * power cone Kpow^a = {(x, y, z): x^a y^(1-a) >= |z|, x, y >= 0}, a = p[i];
+ * p[i] in (-1, 0) its dual (Kpow^a)* = {(u/a)^a (v/(1-a))^(1-a) >= |w|,
+ * u, v >= 0} with a = -p[i]; each takes three rows (x, y, z).  Only the
+ * single-problem solver and scs_project take ed, np > 0. */
 typedef struct {
     int32_t z, l;
     const int32_t *q;
@@ -75,6 +81,9 @@ typedef struct {
     const int32_t *s;
     int32_t ns;
     int32_t ep;
+    int32_t ed;                 /* dual exponential triples: K holds Kexp* itself */
+    const double *p;            /* power-cone parameters, np of them          */
+    int32_t np;
 } scs_cone;
 
 typedef struct {
@@ -206,9 +215,9 @@ int32_t scs_dims(scs_work *w, int32_t *m, int32_t *n, int64_t *nnz, int64_t *dev
 /* Euclidean projection, on the device, of `count` vectors stacked back to
  * back (each of the cone's length m, rows ordered as in scs_cone) onto K
  * (dual = 0) or onto K* (dual = 1): block by block, the zero cone (its dual
- * is all of R), the nonnegative and second-order cones (self-dual) and the
- * exponential cone and its dual (Sec. 6.1; the dual through Moreau,
- * Eq. "e-moreau").  This puts a predicted warm start back into the cones.
+ * is all of R), the nonnegative and second-order cones (self-dual), the
+ * exponential and power cones and their duals (Sec. 6.1; the duals through
+ * Moreau, Eq. "e-moreau").  This puts a predicted warm start back into the cones.
  * v and out are device pointers to count * m doubles (out may equal v);
  * *dist2 (host, may be NULL) receives the sum over all vectors of
  * ||out - v||^2.  Runs on `stream` (a cudaStream_t, or NULL for the legacy
@@ -235,9 +244,9 @@ int32_t scs_project(const scs_cone *k, int32_t dual, const double *v, double *ou
  *     CUDA context is replaced, e.g. by cudaDeviceReset) looks up the
  *     array's device address, with the device current; make that first
  *     call before any stream capture.
- *   - Limits: at most 4096 SOC blocks per cone and no PSD blocks (their
- *     eigensolver needs matrix scratch); SCS_UNSUPPORTED otherwise, with
- *     the reason in scs_last_error().
+ *   - Limits: at most 4096 SOC blocks per cone, no PSD blocks (their
+ *     eigensolver needs matrix scratch) and no power cones (their parameter
+ *     table); SCS_UNSUPPORTED otherwise, with the reason in scs_last_error().
  *   - Every call shares the one array, and each call clears the part that
  *     must start at zero; calls that overlap on the GPU (different streams or
  *     threads at the same time) race on it and must not be issued. */
@@ -252,7 +261,7 @@ int32_t scs_project_noalloc(const scs_cone *k, int32_t dual, const double *v, do
  * vectors in shared memory.  Extends the paper's repeated-solve setting
  * (Sec. 4.2) to many programs at once; the paper has no batched form.
  * Cones: zero, nonnegative and second-order only (SCS_UNSUPPORTED
- * otherwise); a program must fit one CTA's shared memory (about 4 (2 N + 6 n
+ * otherwise, including any exponential, power or PSD block); a program must fit one CTA's shared memory (about 4 (2 N + 6 n
  * + 4 m) bytes in FP32, N = n + m + 1).  No time limit. */
 typedef struct scs_batch scs_batch;
 

@@ -53,9 +53,17 @@ int scs::validate_and_build(const scs_csc *A, const double *b, const double *c, 
     for (int32_t j = 0; j < n; ++j)
         if (!std::isfinite(c[j])) { set_error("non-finite entry in c"); return SCS_INVALID_INPUT; }
     // cone
-    if (k->z < 0 || k->l < 0 || k->nq < 0 || k->ns < 0 || k->ep < 0) { set_error("negative cone size"); return SCS_INVALID_INPUT; }
-    if ((k->nq > 0 && !k->q) || (k->ns > 0 && !k->s)) { set_error("null cone array"); return SCS_INVALID_INPUT; }
-    int64_t rows = (int64_t)k->z + k->l + 3 * (int64_t)k->ep;
+    if (k->z < 0 || k->l < 0 || k->nq < 0 || k->ns < 0 || k->ep < 0 || k->ed < 0 || k->np < 0) {
+        set_error("negative cone size");
+        return SCS_INVALID_INPUT;
+    }
+    if ((k->nq > 0 && !k->q) || (k->ns > 0 && !k->s) || (k->np > 0 && !k->p)) { set_error("null cone array"); return SCS_INVALID_INPUT; }
+    for (int32_t i = 0; i < k->np; ++i)
+        if (!(std::fabs(k->p[i]) > 0.0 && std::fabs(k->p[i]) < 1.0)) {
+            set_error("power cone parameter must lie in (-1, 0) or (0, 1)");
+            return SCS_INVALID_INPUT;
+        }
+    int64_t rows = (int64_t)k->z + k->l + 3 * ((int64_t)k->ep + k->ed + k->np);
     for (int32_t i = 0; i < k->nq; ++i) {
         if (k->q[i] < 1) { set_error("SOC size must be >= 1"); return SCS_INVALID_INPUT; }
         rows += k->q[i];
@@ -133,6 +141,8 @@ int scs::validate_and_build(const scs_csc *A, const double *b, const double *c, 
     P.z = k->z;
     P.l = k->l;
     P.ep = k->ep;
+    P.ed = k->ed;
+    P.pw.assign(k->p, k->p + k->np);
     P.q.assign(k->q, k->q + k->nq);
     P.s.assign(k->s, k->s + k->ns);
     return 0;

@@ -1226,7 +1226,7 @@ scs_batch *scs_batch_init(int32_t count, const scs_csc *A, const double *b, cons
         P.resize(count);
         int64_t yo = 0, xo = 0;
         for (int32_t i = 0; i < count && !e; ++i) {
-            if (k[i].ns > 0 || k[i].ep > 0) {
+            if (k[i].ns > 0 || k[i].ep > 0 || k[i].ed > 0 || k[i].np > 0) {
                 scs::set_last_error("batched programs take zero, nonnegative and second-order cones only");
                 e = SCS_UNSUPPORTED;
                 break;

@@ -1,5 +1,5 @@
-// Device cone projections, FP64 (and an FP32 exponential-cone projection for
-// the mixed-precision iteration).  The iteration projects the y-part of u onto
+// Device cone projections, FP64 (and FP32 exponential- and power-cone
+// projections for the mixed-precision iteration).  The iteration projects the y-part of u onto
 // the dual cone K* (Eq. "e-hsdnice": C = R^n x K* x R+): the dual of the zero
 // cone is R (identity), the nonnegative and second-order cones are
 // self-dual, and the dual exponential cone is reached through Moreau
@@ -245,6 +245,72 @@ __host__ __device__ inline void proj_exp_dual_f(float u, float v, float w, float
     float a, b, c;
     proj_exp_f(-u, -v, -w, a, b, c);
     pu = u + a; pv = v + b; pw = w + c;
+}
+
+// ---------------------------------------------------------------------------
+// power cone (Sec. 6.1), a in (0, 1):
+//   Kpow^a    = {(x, y, z): x^a y^(1-a) >= |z|, x >= 0, y >= 0}
+//   (Kpow^a)* = {(u, v, w): (u/a)^a (v/(1-a))^(1-a) >= |w|, u >= 0, v >= 0}
+// Outside K and the polar cone, and with z0 != 0, the projection of
+// v = (x0, y0, z0) lies on the curved boundary with z of the sign of z0 and
+// |z| = r, the root in (0, |z0|) of phi(r) = x(r)^a y(r)^(1-a) - r: the
+// stationarity of the distance with the multiplier |z0| - r makes x(r), y(r)
+// the positive roots of x^2 - x0 x - a r (|z0| - r) = 0 and
+// y^2 - y0 y - (1 - a) r (|z0| - r) = 0.  phi >= 0 at 0 and < 0 at |z0|;
+// the root is found by bisection in the iterate's precision T.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ float pw_sqrt(float x) { return sqrtf(x); }
+__host__ __device__ __forceinline__ double pw_sqrt(double x) { return sqrt(x); }
+__host__ __device__ __forceinline__ float pw_exp(float x) { return expf(x); }
+__host__ __device__ __forceinline__ double pw_exp(double x) { return exp(x); }
+__host__ __device__ __forceinline__ float pw_log(float x) { return logf(x); }
+__host__ __device__ __forceinline__ double pw_log(double x) { return log(x); }
+
+// x^a y^(1-a) for x, y >= 0 (0 when either is 0)
+template <typename T>
+__host__ __device__ __forceinline__ T pow_mean(T x, T y, T a) {
+    if (!(x > T(0)) || !(y > T(0))) return T(0);
+    return pw_exp(a * pw_log(x) + (T(1) - a) * pw_log(y));
+}
+
+// positive root t of t^2 - c0 t - k r (r0 - r) = 0, without cancellation for c0 < 0
+template <typename T>
+__host__ __device__ __forceinline__ T pow_branch(T c0, T k, T r, T r0) {
+    const T q = k * r * (r0 - r);
+    const T d = pw_sqrt(c0 * c0 + T(4) * q);
+    if (c0 >= T(0)) return T(0.5) * (c0 + d);
+    const T den = d - c0;
+    return den > T(0) ? T(2) * q / den : T(0);
+}
+
+template <typename T>
+__host__ __device__ inline void proj_pow(T x0, T y0, T z0, T a, T &px, T &py, T &pz) {
+    const T az = fabs(z0);
+    if (x0 >= T(0) && y0 >= T(0) && pow_mean(x0, y0, a) >= az) { px = x0; py = y0; pz = z0; return; }   // v in K
+    if (x0 <= T(0) && y0 <= T(0) && pow_mean(-x0 / a, -y0 / (T(1) - a), a) >= az) {                   // -v in K*
+        px = T(0); py = T(0); pz = T(0);
+        return;
+    }
+    if (az == T(0)) { px = fmax(x0, T(0)); py = fmax(y0, T(0)); pz = T(0); return; }
+    T lo = T(0), hi = az;
+    for (int it = 0; it < 200; ++it) {
+        const T mid = T(0.5) * (lo + hi);
+        if (!(mid > lo && mid < hi)) break;
+        const T phi = pow_mean(pow_branch(x0, a, mid, az), pow_branch(y0, T(1) - a, mid, az), a) - mid;
+        if (phi > T(0)) lo = mid; else hi = mid;
+    }
+    const T r = T(0.5) * (lo + hi);
+    px = pow_branch(x0, a, r, az);
+    py = pow_branch(y0, T(1) - a, r, az);
+    pz = z0 < T(0) ? -r : r;
+}
+
+// Moreau (Eq. "e-moreau"): Pi_{K*}(w) = w + Pi_K(-w)
+template <typename T>
+__host__ __device__ inline void proj_pow_dual(T u, T v, T w, T a, T &pu, T &pv, T &pw) {
+    T p0, p1, p2;
+    proj_pow(-u, -v, -w, a, p0, p1, p2);
+    pu = u + p0; pv = v + p1; pw = w + p2;
 }
 
 }  // namespace scs

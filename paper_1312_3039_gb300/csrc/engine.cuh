@@ -382,10 +382,14 @@ class Engine : public EngineBase {
             off += ss * (ss + 1) / 2;
         }
         K.exp_off = off;
-        for (int e = 0; e < P.ep; ++e) {
+        K.ed = P.ed;
+        K.np = static_cast<int>(P.pw.size());
+        const int ntri = P.ep + P.ed + K.np;      // exponential, dual exponential, power: 3 rows each
+        for (int e = 0; e < ntri; ++e) {
             avg_off.push_back(off + 3 * e);
             avg_len.push_back(3);
         }
+        K.pow_a = K.np ? upload(P.pw) : nullptr;
         K.q_off = upload(qoff);
         K.q_len = upload(P.q);
         // element and SOC ranges: at most one wave of resident CTAs each
@@ -395,7 +399,7 @@ class Engine : public EngineBase {
         K.nb_elem = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(
             wave, (static_cast<int64_t>(n_) + K.z + K.l + kBlock - 1) / kBlock)));
         K.nb_soc = static_cast<int>(std::min<int64_t>(wave, (K.nq + kWarps - 1) / kWarps));
-        K.nb_exp = (K.ep + kExpPerCta - 1) / kExpPerCta;
+        K.nb_exp = (ntri + kExpPerCta - 1) / kExpPerCta;
         K.npsd = static_cast<int>(P.s.size());
         if (K.npsd) {
             // PSD blocks: eigenvector storage (warm start), per-block step

@@ -29,7 +29,8 @@ struct HostProblem {
     int64_t nnz = 0;
     std::vector<int32_t> a_rowptr, a_col, at_rowptr, at_col;
     std::vector<double> a_val, at_val, b, c;
-    int32_t z = 0, l = 0, ep = 0;
+    int32_t z = 0, l = 0, ep = 0, ed = 0;
+    std::vector<double> pw;     // power-cone parameters (negative: dual power cone)
     std::vector<int32_t> q, s;
 };
 

@@ -1013,7 +1013,7 @@ scs_family *scs_family_init(const scs_csc *A, const scs_cone *k, int32_t count, 
     if (count <= 0 || !A || !k || !b || !c) {
         scs::set_last_error("bad family arguments");
         e = SCS_INVALID_INPUT;
-    } else if (k->ns > 0 || k->ep > 0) {
+    } else if (k->ns > 0 || k->ep > 0 || k->ed > 0 || k->np > 0) {
         scs::set_last_error("family programs take zero, nonnegative and second-order cones only");
         e = SCS_UNSUPPORTED;
     } else {

@@ -279,7 +279,8 @@ __global__ void __launch_bounds__(kBlock) smw_kernel(int n, int m, const T *__re
 
 // ---------------------------------------------------------------------------
 // K7: relax, project onto C = R^n x K* x R+, update v  (one launch)
-//   block ranges: [0, nb_exp)       exponential triples, kExpPerCta per CTA
+//   block ranges: [0, nb_exp)       exponential, dual exponential and power
+//                                   triples, kExpPerCta per CTA
 //                                   (long dependent chains: started first,
 //                                   spread over many SMs)
 //                 [.., + nb_soc)    second-order blocks, one warp per block,
@@ -298,7 +299,10 @@ struct ConeDev {
     int nq;                // second-order blocks
     const int32_t *q_off;  // row offset (within y) of each SOC block
     const int32_t *q_len;
-    int ep;                // exponential triples
+    int ep;                // exponential triples, then
+    int ed;                // dual exponential triples (K holds Kexp*), then
+    int np;                // power triples, parameter pow_a[i] (< 0: dual power cone)
+    const double *pow_a;
     int exp_off;           // row offset of the first triple
     int nb_elem, nb_soc, nb_exp;
     int npsd;              // PSD blocks (projected by psd_project_kernel)
@@ -332,7 +336,7 @@ __global__ void __launch_bounds__(kBlock) relax_project_kernel(ProjArgs<T> a, Co
     T dd = 0;               // squared length of this thread's part of the step
     if (bid < K.nb_exp) {
         const int tri = bid * kExpPerCta + threadIdx.x;
-        if (threadIdx.x < kExpPerCta && tri < K.ep) {
+        if (threadIdx.x < kExpPerCta && tri < K.ep + K.ed + K.np) {
             const int off = a.n + K.exp_off + 3 * tri;
             T t[3], up[3];
             T uo[3], vo[3];
@@ -342,11 +346,23 @@ __global__ void __launch_bounds__(kBlock) relax_project_kernel(ProjArgs<T> a, Co
                 vo[e] = a.v[off + e];
                 t[e] = relaxed(a, off + e, gamma, alpha) - vo[e];
             }
-            // in the precision of the iterates (FP32: no FP64 in this kernel)
-            if constexpr (std::is_same<T, float>::value)
-                proj_exp_dual_f(t[0], t[1], t[2], up[0], up[1], up[2]);
-            else
-                proj_exp_dual(t[0], t[1], t[2], up[0], up[1], up[2]);
+            // in the precision of the iterates (FP32: no FP64 in this kernel).
+            // The y-part goes to K*: Kexp* for an exponential triple, Kexp for
+            // a dual one, (Kpow^a)* for a power triple, Kpow^a for a dual one.
+            if (tri < K.ep + K.ed) {
+                const bool dual_cone = tri >= K.ep;
+                if constexpr (std::is_same<T, float>::value) {
+                    if (dual_cone) proj_exp_f(t[0], t[1], t[2], up[0], up[1], up[2]);
+                    else proj_exp_dual_f(t[0], t[1], t[2], up[0], up[1], up[2]);
+                } else {
+                    if (dual_cone) proj_exp(t[0], t[1], t[2], up[0], up[1], up[2]);
+                    else proj_exp_dual(t[0], t[1], t[2], up[0], up[1], up[2]);
+                }
+            } else {
+                const double pa = K.pow_a[tri - K.ep - K.ed];
+                if (pa > 0.0) proj_pow_dual<T>(t[0], t[1], t[2], static_cast<T>(pa), up[0], up[1], up[2]);
+                else proj_pow<T>(t[0], t[1], t[2], static_cast<T>(-pa), up[0], up[1], up[2]);
+            }
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
                 const T un = up[e], vn = up[e] - t[e];

@@ -3,7 +3,8 @@
 // squared distance moved summed by a deterministic grid reduction.  The
 // same projections as the iteration's kernels (zero/free, nonnegative,
 // second-order, PSD by a cold-started Jacobi eigensolver, exponential via
-// Moreau); used to put predicted warm starts back into the cones.
+// Moreau, power and its dual via Moreau); used to put predicted warm starts
+// back into the cones.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -26,7 +27,10 @@ struct ProjCone {
     int nq;
     const int32_t *q_off;  // row offset of each SOC block
     const int32_t *q_len;
-    int ep;
+    int ep;                // exponential triples, then dual exponential ones,
+    int ed;                // then power triples (pow_a[i] < 0: dual power cone)
+    int np;
+    const double *pow_a;
     int exp_off;
     int64_t count;         // vectors
     int g_elem, g_soc, g_exp;   // CTAs of each region (grid-stride inside)
@@ -34,7 +38,8 @@ struct ProjCone {
     const double *psd_dd;  // their squared distances
 };
 
-// Regions: [0, g_exp) exponential triples (64 per CTA pass), then
+// Regions: [0, g_exp) exponential, dual exponential and power triples (64
+// per CTA pass), then
 // [.., + g_soc) one warp per SOC block, then the elementwise rows.
 __global__ void __launch_bounds__(kBlock) cone_project_kernel(ProjCone P, int dual, const double *__restrict__ v,
                                                               double *__restrict__ out, ReduceBuf rb,
@@ -42,14 +47,23 @@ __global__ void __launch_bounds__(kBlock) cone_project_kernel(ProjCone P, int du
     double dd = 0.0;
     const int b = blockIdx.x;
     if (b < P.g_exp) {
-        const int64_t ntri = P.count * P.ep;
+        const int per = P.ep + P.ed + P.np;
+        const int64_t ntri = P.count * per;
         for (int64_t t = (int64_t)b * 64 + threadIdx.x; threadIdx.x < 64 && t < ntri; t += (int64_t)P.g_exp * 64) {
-            const int64_t vec = t / P.ep, tri = t % P.ep;
+            const int64_t vec = t / per;
+            const int tri = static_cast<int>(t % per);
             const int64_t off = vec * P.m + P.exp_off + 3 * tri;
             const double a0 = v[off], a1 = v[off + 1], a2 = v[off + 2];
             double p0, p1, p2;
-            if (dual) proj_exp_dual(a0, a1, a2, p0, p1, p2);
-            else proj_exp(a0, a1, a2, p0, p1, p2);
+            if (tri < P.ep + P.ed) {
+                // K* of Kexp is Kexp*, of Kexp* is Kexp: onto Kexp* when exactly one holds
+                if ((dual != 0) != (tri >= P.ep)) proj_exp_dual(a0, a1, a2, p0, p1, p2);
+                else proj_exp(a0, a1, a2, p0, p1, p2);
+            } else {
+                const double pa = P.pow_a[tri - P.ep - P.ed];
+                if ((dual != 0) != (pa < 0.0)) proj_pow_dual(a0, a1, a2, fabs(pa), p0, p1, p2);
+                else proj_pow(a0, a1, a2, fabs(pa), p0, p1, p2);
+            }
             out[off] = p0; out[off + 1] = p1; out[off + 2] = p2;
             dd += (p0 - a0) * (p0 - a0) + (p1 - a1) * (p1 - a1) + (p2 - a2) * (p2 - a2);
         }
@@ -156,7 +170,7 @@ __global__ void __launch_bounds__(kPsdThreads, 1) psd_batch_kernel(const double 
 // Region grids for a batch (each region gets CTAs only if it has work).
 inline void project_grid(ProjCone &P, int max_ctas) {
     const int64_t lin = P.count * ((int64_t)P.z + P.l);
-    const int64_t soc = P.count * P.nq, exp_ = P.count * P.ep;
+    const int64_t soc = P.count * P.nq, exp_ = P.count * ((int64_t)P.ep + P.ed + P.np);
     P.g_exp = exp_ ? (int)std::min<int64_t>((exp_ + 63) / 64, max_ctas / 4) : 0;
     P.g_soc = soc ? (int)std::min<int64_t>((soc + kWarps - 1) / kWarps, max_ctas / 4) : 0;
     P.g_elem = lin ? (int)std::min<int64_t>((lin + kBlock - 1) / kBlock, max_ctas / 2) : 0;
@@ -169,11 +183,16 @@ inline void project_grid(ProjCone &P, int max_ctas) {
 inline int project_setup(const scs_cone *k, int64_t count, ProjCone &P, std::vector<int32_t> &qoff,
                          std::vector<int32_t> &qlen, std::vector<int32_t> &soff, std::string &err) {
     if (!k || count < 0) { err = "bad argument"; return SCS_INVALID_INPUT; }
-    if (k->z < 0 || k->l < 0 || k->nq < 0 || k->ns < 0 || k->ep < 0 || (k->nq > 0 && !k->q) ||
-        (k->ns > 0 && !k->s)) {
+    if (k->z < 0 || k->l < 0 || k->nq < 0 || k->ns < 0 || k->ep < 0 || k->ed < 0 || k->np < 0 ||
+        (k->nq > 0 && !k->q) || (k->ns > 0 && !k->s) || (k->np > 0 && !k->p)) {
         err = "bad cone";
         return SCS_INVALID_INPUT;
     }
+    for (int i = 0; i < k->np; ++i)
+        if (!(fabs(k->p[i]) > 0.0 && fabs(k->p[i]) < 1.0)) {
+            err = "power cone parameter must lie in (-1, 0) or (0, 1)";
+            return SCS_INVALID_INPUT;
+        }
     int64_t off = (int64_t)k->z + k->l;
     qoff.clear();
     qlen.clear();
@@ -192,13 +211,15 @@ inline int project_setup(const scs_cone *k, int64_t count, ProjCone &P, std::vec
         if (off > (int64_t)1 << 30) { err = "cone too large"; return SCS_UNSUPPORTED; }
     }
     P.exp_off = (int)off;
-    off += 3 * (int64_t)k->ep;
+    off += 3 * ((int64_t)k->ep + k->ed + k->np);
     if (off > (int64_t)1 << 30) { err = "cone too large"; return SCS_UNSUPPORTED; }
     P.m = (int)off;
     P.z = k->z;
     P.l = k->l;
     P.nq = k->nq;
     P.ep = k->ep;
+    P.ed = k->ed;
+    P.np = k->np;
     P.count = count;
     return 0;
 }
@@ -242,7 +263,7 @@ extern "C" int32_t scs_project(const scs_cone *k, int32_t dual, const double *v,
     const int64_t wstride = nps ? psd_mat_elems(n_max) : 0;
     // scratch for this call: partial sums, arrival counters, SOC and PSD
     // tables, result, PSD partial sums and (large orders) PSD matrices
-    double *partials = nullptr, *res = nullptr, *psd_dd = nullptr, *psd_work = nullptr;
+    double *partials = nullptr, *res = nullptr, *psd_dd = nullptr, *psd_work = nullptr, *pow_tab = nullptr;
     unsigned *counter = nullptr;
     int32_t *tables = nullptr;
     rc = 0;
@@ -250,7 +271,8 @@ extern "C" int32_t scs_project(const scs_cone *k, int32_t dual, const double *v,
     if (cudaMalloc(&partials, sizeof(double) * kMaxRed * grid) || cudaMalloc(&counter, sizeof(unsigned) * kSiteCount) ||
         cudaMalloc(&res, sizeof(double)) || cudaMalloc(&tables, sizeof(int32_t) * ntab) ||
         (nps && cudaMalloc(&psd_dd, sizeof(double) * g_psd)) ||
-        (nps && !on_chip && cudaMalloc(&psd_work, sizeof(double) * 3 * wstride * g_psd)))
+        (nps && !on_chip && cudaMalloc(&psd_work, sizeof(double) * 3 * wstride * g_psd)) ||
+        (k->np > 0 && cudaMalloc(&pow_tab, sizeof(double) * k->np)))
         rc = SCS_DEVICE_ERROR;
     int32_t *t_soff = tables + 2 * qoff.size(), *t_sord = t_soff + soff.size();
     if (!rc) {
@@ -262,6 +284,8 @@ extern "C" int32_t scs_project(const scs_cone *k, int32_t dual, const double *v,
                     cudaMemcpyAsync(t_sord, k->s, 4 * soff.size(), cudaMemcpyHostToDevice, s)))
             rc = SCS_DEVICE_ERROR;
         if (cudaMemsetAsync(counter, 0, sizeof(unsigned) * kSiteCount, s)) rc = SCS_DEVICE_ERROR;
+        if (k->np > 0 && cudaMemcpyAsync(pow_tab, k->p, sizeof(double) * k->np, cudaMemcpyHostToDevice, s))
+            rc = SCS_DEVICE_ERROR;
     }
     if (!rc && nps) {
         auto kern = on_chip ? psd_batch_kernel<true> : psd_batch_kernel<false>;
@@ -278,6 +302,7 @@ extern "C" int32_t scs_project(const scs_cone *k, int32_t dual, const double *v,
     if (!rc) {
         P.q_off = tables;
         P.q_len = tables + qoff.size();
+        P.pow_a = pow_tab;
         ReduceBuf rb{partials, counter, grid};
         cone_project_kernel<<<grid, kBlock, 0, s>>>(P, dual ? 1 : 0, v, out, rb, res);
         double h = 0.0;
@@ -292,6 +317,7 @@ extern "C" int32_t scs_project(const scs_cone *k, int32_t dual, const double *v,
     cudaFree(tables);
     cudaFree(psd_dd);
     cudaFree(psd_work);
+    cudaFree(pow_tab);
     if (rc) set_last_error("scs_project: CUDA call failed");
     return rc;
 }
@@ -378,6 +404,10 @@ extern "C" int32_t scs_project_noalloc(const scs_cone *k, int32_t dual, const do
     }
     if (!soff.empty()) {
         set_last_error("scs_project_noalloc: PSD blocks need eigensolver matrix scratch; use scs_project");
+        return SCS_UNSUPPORTED;
+    }
+    if (k->np > 0) {
+        set_last_error("scs_project_noalloc: power cones need a parameter table; use scs_project");
         return SCS_UNSUPPORTED;
     }
     if (count == 0 || P.m == 0) {

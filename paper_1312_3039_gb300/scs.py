@@ -35,7 +35,8 @@ class CSC(C.Structure):
 
 class ConeC(C.Structure):
     _fields_ = [("z", C.c_int32), ("l", C.c_int32), ("q", C.POINTER(C.c_int32)), ("nq", C.c_int32),
-                ("s", C.POINTER(C.c_int32)), ("ns", C.c_int32), ("ep", C.c_int32)]
+                ("s", C.POINTER(C.c_int32)), ("ns", C.c_int32), ("ep", C.c_int32), ("ed", C.c_int32),
+                ("p", C.POINTER(C.c_double)), ("np", C.c_int32)]
 
 
 class Settings(C.Structure):
@@ -208,9 +209,11 @@ def cone_struct(cone):
     """ctypes scs_cone for a cone description (keeps its arrays alive)."""
     q = np.ascontiguousarray(list(getattr(cone, "q", ())) or [0], dtype=np.int32)
     s = np.ascontiguousarray(list(getattr(cone, "s", ())) or [0], dtype=np.int32)
+    pw = np.ascontiguousarray(list(getattr(cone, "p", ())) or [0.0], dtype=np.float64)
     kc = ConeC(int(cone.z), int(cone.l), q.ctypes.data_as(C.POINTER(C.c_int32)), len(getattr(cone, "q", ())),
-               s.ctypes.data_as(C.POINTER(C.c_int32)), len(getattr(cone, "s", ())), int(cone.ep))
-    return kc, (q, s)
+               s.ctypes.data_as(C.POINTER(C.c_int32)), len(getattr(cone, "s", ())), int(cone.ep),
+               int(getattr(cone, "ed", 0)), pw.ctypes.data_as(C.POINTER(C.c_double)), len(getattr(cone, "p", ())))
+    return kc, (q, s, pw)
 
 
 def project(cone, dual, v_ptr, out_ptr, count, stream=None):
@@ -254,14 +257,10 @@ class Solver:
         self._val = np.ascontiguousarray(A.data, dtype=np.float64)
         self._b = np.ascontiguousarray(b, dtype=np.float64)
         self._c = np.ascontiguousarray(c, dtype=np.float64)
-        self._q = np.ascontiguousarray(list(getattr(cone, "q", ())) or [0], dtype=np.int32)
-        self._s = np.ascontiguousarray(list(getattr(cone, "s", ())) or [0], dtype=np.int32)
         csc = CSC(self.m, self.n, self._colptr.ctypes.data_as(C.POINTER(C.c_int64)),
                   self._rowidx.ctypes.data_as(C.POINTER(C.c_int32)),
                   self._val.ctypes.data_as(C.POINTER(C.c_double)))
-        kc = ConeC(int(cone.z), int(cone.l), self._q.ctypes.data_as(C.POINTER(C.c_int32)),
-                   len(getattr(cone, "q", ())), self._s.ctypes.data_as(C.POINTER(C.c_int32)),
-                   len(getattr(cone, "s", ())), int(cone.ep))
+        kc, self._cone_keep = cone_struct(cone)
         st = settings if settings is not None else default_settings()
         for k, v in kw.items():
             setattr(st, k, v)
@@ -391,14 +390,10 @@ class Batch:
             cp = np.ascontiguousarray(A.indptr, dtype=np.int64)
             ri = np.ascontiguousarray(A.indices, dtype=np.int32)
             va = np.ascontiguousarray(A.data, dtype=np.float64)
-            q = np.ascontiguousarray(list(getattr(cone, "q", ())) or [0], dtype=np.int32)
-            sd = np.ascontiguousarray(list(getattr(cone, "s", ())) or [0], dtype=np.int32)
-            self._keep += [cp, ri, va, q, sd]
+            cones[i], keep = cone_struct(cone)
+            self._keep += [cp, ri, va, keep]
             cscs[i] = CSC(m, n, cp.ctypes.data_as(C.POINTER(C.c_int64)), ri.ctypes.data_as(C.POINTER(C.c_int32)),
                           va.ctypes.data_as(C.POINTER(C.c_double)))
-            cones[i] = ConeC(int(cone.z), int(cone.l), q.ctypes.data_as(C.POINTER(C.c_int32)),
-                             len(getattr(cone, "q", ())), sd.ctypes.data_as(C.POINTER(C.c_int32)),
-                             len(getattr(cone, "s", ())), int(cone.ep))
             self.ns.append(n)
             self.ms.append(m)
             bs.append(np.asarray(b, dtype=np.float64))

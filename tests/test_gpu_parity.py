@@ -121,6 +121,28 @@ def test_soc_exp_trajectory_fp64(scs):
     trajectory_parity(scs, P)
 
 
+def test_every_cone_type_trajectory_fp64(scs):
+    """Power cones and their duals, dual exponential triples, among every
+    other cone type (Sec. 6.1): the FP64 engine follows the oracle for 50
+    iterations."""
+    cone = synth.Cone(z=4, l=15, q=(3, 5), s=(3,), ep=4, ed=3, p=(0.3, -0.7, 0.5, -0.2, 0.9))
+    trajectory_parity(scs, synth.random_cone(31, n=45, cone=cone))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_power_cone_solve(scs, precision):
+    """A program with power, dual power and dual exponential cones among the
+    others reaches the Sec. 3.5 tests; objective parity with the oracle as in
+    test_lp_solve."""
+    cone = synth.Cone(z=3, l=12, q=(4,), ep=3, ed=3, p=(0.25, -0.6, 0.5, 0.8, -0.35, 0.1))
+    P = synth.random_cone(32, n=40, cone=cone)
+    st, x, y, s, info = scs.solve(P.A, P.b, P.c, P.cone, precision=precision)
+    assert st == scs.SOLVED, info
+    check_solution(P, x, y, s, cone_tol=1e-5 if precision else 1e-7)
+    ref = admm.solve(P.A, P.b, P.c, P.cone, same_settings())
+    assert_objective_parity(P, precision, info, x, y, s, ref)
+
+
 def test_mixed_small_trajectory_fp64(scs):
     trajectory_parity(scs, synth.mixed_small(0, scale=500))
 

@@ -53,3 +53,12 @@ def test_noalloc_rejects_cones_beyond_its_tables(env):
         scs.project_noalloc(cone, 0, dv.data_ptr(), dv.data_ptr(), 1)
     assert ei.value.code == scs.UNSUPPORTED
     assert "SOC blocks" in str(ei.value)          # the reason reaches scs_last_error
+
+
+def test_noalloc_rejects_power_cones(env):
+    torch, scs = env
+    cone = synth.Cone(l=2, p=(0.5,))
+    dv = torch.zeros(cone.m, dtype=torch.float64, device="cuda")
+    with pytest.raises(scs.ScsError) as ei:
+        scs.project_noalloc(cone, 0, dv.data_ptr(), dv.data_ptr(), 1)
+    assert ei.value.code == scs.UNSUPPORTED
