@@ -4,8 +4,10 @@
 //     C (M x N) = alpha * A (M x K) * B (K x N) + beta * C
 //
 // all three column-major with leading dimensions lda, ldb, ldc.  FP32 runs
-// 128 x 128 output tiles (8 x 8 per thread), FP64 64 x 64 tiles (4 x 4 per
-// thread); 256 threads; k-blocks of 8 staged in shared memory, the next
+// 128 x 128 output tiles (8 x 8 per thread) when that grid holds at least two
+// CTAs per SM and 64 x 64 tiles (4 x 4 per thread) otherwise (few member
+// columns: more CTAs, each with less reuse); FP64 64 x 64 tiles; 256
+// threads; k-blocks of 8 staged in shared memory, the next
 // block's global loads held in registers while the current one is consumed
 // (one barrier per k-block).  Edges of every dimension are bounds-checked
 // (zero-filled loads, masked stores), so no size needs padding.  CTAs walk the
@@ -23,26 +25,23 @@ namespace dense {
 
 constexpr int kGemmThreads = 256;
 
+template <typename T, int BM_, int TM_>
+struct GemmTile {
+    static constexpr int BM = BM_, BN = BM_, BK = 8, TM = TM_, TN = TM_;
+};
 template <typename T>
-struct GemmTile;
+struct VecOf;
 template <>
-struct GemmTile<float> {
-    static constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;
-    using Vec = float4;
-};
+struct VecOf<float> { using type = float4; };
 template <>
-struct GemmTile<double> {
-    static constexpr int BM = 64, BN = 64, BK = 8, TM = 4, TN = 4;
-    using Vec = double2;
-};
+struct VecOf<double> { using type = double2; };
 
-template <typename T>
+template <typename T, typename G>
 __global__ void __launch_bounds__(kGemmThreads) gemm_nn_kernel(int M, int N, int K, T alpha,
                                                                const T *__restrict__ A, int64_t lda,
                                                                const T *__restrict__ B, int64_t ldb, T beta,
                                                                T *__restrict__ C, int64_t ldc) {
-    using G = GemmTile<T>;
-    using V = typename G::Vec;
+    using V = typename VecOf<T>::type;
     constexpr int BM = G::BM, BN = G::BN, BK = G::BK, TM = G::TM, TN = G::TN;
     constexpr int TX = BN / TN, TY = BM / TM;
     static_assert(TX * TY == kGemmThreads, "one thread per TM x TN sub-tile");
@@ -132,16 +131,30 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_nn_kernel(int M, int N, int
 
 // Enqueue C = alpha A B + beta C on `stream` (beta == 0: C is not read).
 // Empty products (M, N or K zero) scale C by beta (K == 0) or do nothing.
-template <typename T>
-inline cudaError_t gemm_nn(cudaStream_t stream, int M, int N, int K, T alpha, const T *A, int64_t lda, const T *B,
-                           int64_t ldb, T beta, T *C, int64_t ldc) {
-    using G = GemmTile<T>;
-    if (M <= 0 || N <= 0) return cudaSuccess;
+template <typename T, typename G>
+inline cudaError_t gemm_nn_tiles(cudaStream_t stream, int M, int N, int K, T alpha, const T *A, int64_t lda,
+                                 const T *B, int64_t ldb, T beta, T *C, int64_t ldc) {
     const unsigned gx = static_cast<unsigned>((M + G::BM - 1) / G::BM);
     const unsigned gy = static_cast<unsigned>((N + G::BN - 1) / G::BN);
     if (gy > 65535u) return cudaErrorInvalidConfiguration;
-    gemm_nn_kernel<T><<<dim3(gx, gy), kGemmThreads, 0, stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    gemm_nn_kernel<T, G><<<dim3(gx, gy), kGemmThreads, 0, stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
     return cudaGetLastError();
+}
+
+template <typename T>
+inline cudaError_t gemm_nn(cudaStream_t stream, int M, int N, int K, T alpha, const T *A, int64_t lda, const T *B,
+                           int64_t ldb, T beta, T *C, int64_t ldc) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    if constexpr (sizeof(T) == 4) {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return cudaErrorInvalidDevice;
+        const int64_t big = (int64_t)((M + 127) / 128) * ((N + 127) / 128);
+        if (big >= 2 * (int64_t)sms)
+            return gemm_nn_tiles<T, GemmTile<T, 128, 8>>(stream, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    }
+    return gemm_nn_tiles<T, GemmTile<T, 64, 4>>(stream, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 
 }  // namespace dense

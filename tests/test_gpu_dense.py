@@ -7,7 +7,8 @@ recursively summed dot product holds entrywise:
     |C_gpu - C_exact| <= gamma_K (|alpha| |A| |B| + |beta| |C0|) + u |C_exact|,
 gamma_K = K u / (1 - K u), u the unit roundoff (2^-24 FP32, 2^-53 FP64; the
 last term is the rounding of the stored result).  Shapes cover one tile, many
-tiles with ragged edges in M, N and K, the family solver's own shapes, K = 0,
+tiles with ragged edges in M, N and K, the family solver's own shapes (with
+few member columns: 64 x 64 tiles; with many: FP32 128 x 128 tiles), K = 0,
 leading dimensions above the row count, and beta = 0 with NaN in C.
 """
 import numpy as np
@@ -60,7 +61,7 @@ def run(env, precision, M, N, K, alpha, beta, lda_pad=0, ldb_pad=0, ldc_pad=0, n
 
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("shape", [(1, 1, 1), (128, 128, 8), (64, 64, 8), (129, 257, 9), (7, 3, 1000),
-                                   (801, 700, 1802), (1802, 333, 801), (801, 513, 801)])
+                                   (801, 700, 1802), (1802, 333, 801), (801, 513, 801), (1802, 4100, 801)])
 def test_gemm_matches_fp64_bound(env, precision, shape):
     M, N, K = shape
     run(env, precision, M, N, K, -1.0, 1.0, seed=M + N + K)
