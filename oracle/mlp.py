@@ -9,6 +9,12 @@ compared with this module's gradients on the same (BF16-rounded) inputs.
 Conventions: a layer holds W (out x in) and b (out); for a batch X
 (rows = samples) the layer computes Z = X W^T + b.  GELU(z) = z Phi(z) with
 Phi the standard normal distribution function, GELU'(z) = Phi(z) + z phi(z).
+
+``bf16_points=True`` rounds to BF16 where a BF16 network stores values that
+feed a product: each hidden activation GELU(Z), and each layer's dZ before
+the products dW = dZ^T A and dA = dZ W (the bias gradient sums the unrounded
+dZ).  Inputs and weights are rounded by the caller (``bf16_round``).  Every
+other step stays in FP64.
 """
 from __future__ import annotations
 
@@ -37,21 +43,26 @@ def init_params(rng, sizes):
     return out
 
 
-def forward(params, X):
+def forward(params, X, bf16_points=False):
     """Returns (output, cache) with cache = [(input, Z), ...] per layer."""
     cache = []
     A = np.asarray(X, dtype=np.float64)
     for li, (W, b) in enumerate(params):
         Z = A @ W.T + b
         cache.append((A, Z))
-        A = gelu(Z) if li < len(params) - 1 else Z
+        if li < len(params) - 1:
+            A = gelu(Z)
+            if bf16_points:
+                A = bf16_round(A)
+        else:
+            A = Z
     return A, cache
 
 
-def loss_and_grads(params, X, T, mask=None):
+def loss_and_grads(params, X, T, mask=None, bf16_points=False):
     """MSE = mean over samples and unmasked outputs of (Y - T)^2, and its
     gradients [(dW, db), ...] by the chain rule through every layer."""
-    Y, cache = forward(params, X)
+    Y, cache = forward(params, X, bf16_points)
     M = np.ones(Y.shape[1]) if mask is None else np.asarray(mask, dtype=np.float64)
     cnt = Y.shape[0] * M.sum()
     R = (Y - T) * M
@@ -62,8 +73,9 @@ def loss_and_grads(params, X, T, mask=None):
         A_in, Z = cache[li]
         dZ = dA if li == len(params) - 1 else dA * gelu_grad(Z)
         W, _ = params[li]
-        grads[li] = (dZ.T @ A_in, dZ.sum(axis=0))
-        dA = dZ @ W
+        dZp = bf16_round(dZ) if bf16_points else dZ
+        grads[li] = (dZp.T @ A_in, dZ.sum(axis=0))
+        dA = dZp @ W
     return loss, grads
 
 
