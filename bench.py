@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--workload", choices=["mixed", "mixed_small", "sdp", "sdp_small", "sdp_blocks", "lp",
                                            "portfolio_batch", "portfolio_batch_small", "lasso_warm",
-                                           "lasso_warm_small", "mlp_train"],
+                                           "lasso_warm_small", "mlp_train"] + sorted(PAPER_APPS),
                     default="mixed")
     ap.add_argument("--train", type=int, default=None, help="training members of a lasso_warm workload")
     ap.add_argument("--epochs", type=int, default=30)
@@ -84,8 +84,35 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+# The paper's application workloads at the sizes of its Tables 1-4 (small and
+# medium), built as the paper prints them (Sec. 6.2-6.5), with the paper's
+# own GPU result for context: the indirect method on a GeForce GTX Titan X,
+# eps 1e-3, setup included (its standard forms differ from the printed
+# SOCP/SDP for the lasso, portfolio and RPCA tables: see n, m, nnz).
+PAPER_APPS = {
+    "paper_lasso": (("lasso_paper", dict(p=10_000, q=2_000)), "lasso (Sec. 6.2) small: p=1e4 features, q=2e3 "
+                    "measurements, dense F", dict(gpu_s=4.6, iters=400, n=2001, m=22002, nnz=3.8e6)),
+    "paper_lasso_medium": (("lasso_paper", dict(p=30_000, q=6_000)), "lasso (Sec. 6.2) medium: p=3e4, q=6e3, "
+                           "dense F", dict(gpu_s=22.0, iters=540, n=6001, m=66002, nnz=3.4e7)),
+    "paper_portfolio": (("portfolio_paper", dict(p=100_000, q=100)), "portfolio (Sec. 6.3, both risk SOCs) small: "
+                        "p=1e5 assets, q=100 factors", dict(gpu_s=27.8, iters=500, n=100103, m=200104, nnz=1.3e6)),
+    "paper_portfolio_medium": (("portfolio_paper", dict(p=500_000, q=500)), "portfolio (Sec. 6.3) medium: p=5e5, "
+                               "q=500", dict(gpu_s=184.0, iters=440, n=500503, m=1000504, nnz=2.5e7)),
+    "paper_rpca": (("rpca_paper", dict(p=100)), "robust PCA (Sec. 6.4) small: p=q=100, rank 10, PSD block of "
+                   "order 200", dict(gpu_s=6.1, iters=120, n=10001, m=40101, nnz=5.0e4)),
+    "paper_logreg": (("logreg_paper", dict(p=100, q=10_000)), "l1 logistic regression (Sec. 6.5) small: p=100, "
+                     "q=1e4 samples, 2e4 exponential cones", dict(gpu_s=4.4, iters=280, n=30200, m=70200, nnz=1.6e5)),
+    "paper_logreg_medium": (("logreg_paper", dict(p=1_000, q=100_000)), "l1 logistic regression (Sec. 6.5) medium: "
+                            "p=1e3, q=1e5", dict(gpu_s=120.0, iters=380, n=302000, m=702000, nnz=1.0e7)),
+}
+
+
 def make_problem(workload, seed):
     from paper_1312_3039_gb300 import synth
+    if workload in PAPER_APPS:
+        (fn, kw), desc, _paper = PAPER_APPS[workload]
+        P = getattr(synth, fn)(seed, **kw)
+        return P, f"{desc} (n={P.n}, m={P.m}, nnz={P.A.nnz})"
     if workload == "mixed":
         return synth.mixed(seed), ("mixed-cone program n=1e6 m=2e6 nnz=2e7 (power-law rows; zero 1e5, "
                                    "SOC 2e4 blocks of 3-50, exp 1e4, nonneg rest)")
@@ -228,6 +255,72 @@ def cpu_oracle_job(workload, seed, seconds, queue):
         queue.put({"error": repr(e)})
 
 
+ORACLE_ERR_SCALES = (500, 50)
+
+
+def oracle_err_job(seed, queue):
+    """FP64 oracle solves of the down-scaled siblings of the large mixed
+    program (the same generator divided by 500 and by 50), with the GPU
+    engine's method and settings (indirect CG, (1/k)^1.5 capped at 0.3 x the
+    last step, 50 CG steps at most, eps 1e-4); runs in a spawned process
+    alongside the GPU legs.  The full-size program is beyond the oracle."""
+    try:
+        from oracle import admm
+        from paper_1312_3039_gb300 import synth
+        out = {}
+        for sc in ORACLE_ERR_SCALES:
+            P = synth.mixed_small(seed, scale=sc)
+            t0 = time.perf_counter()
+            r = admm.solve(P.A, P.b, P.c, P.cone, admm.Settings(linsys="indirect", cg_max_iters=50))
+            out[sc] = {"status": r.status, "iters": r.iters, "pobj": r.pobj, "x": r.x, "y": r.y, "s": r.s,
+                       "seconds": time.perf_counter() - t0}
+        queue.put(out)
+    except Exception as e:
+        queue.put({"error": repr(e)})
+
+
+def two_point_bound(P, x1, y1, s1, x2, y2, s2):
+    """Largest objective difference weak duality allows between two points
+    with these residuals (s in K, y in K*): c^T x1 - c^T x2 lies in
+    [-g2 - ||y2|| ||r_p1|| - ||x1|| ||r_d2||, g1 + ||y1|| ||r_p2|| + ||x2|| ||r_d1||],
+    r_p = A x + s - b, r_d = A^T y + c, g = c^T x + b^T y."""
+    import numpy as np
+
+    def parts(x, y, s):
+        return (float(np.linalg.norm(P.A @ x + s - P.b)), float(np.linalg.norm(P.A.T @ y + P.c)),
+                float(P.c @ x + P.b @ y), float(np.linalg.norm(x)), float(np.linalg.norm(y)))
+    rp1, rd1, g1, nx1, ny1 = parts(x1, y1, s1)
+    rp2, rd2, g2, nx2, ny2 = parts(x2, y2, s2)
+    return max(g2 + ny2 * rp1 + nx1 * rd2, g1 + ny1 * rp2 + nx2 * rd1)
+
+
+def oracle_err(seed, orc, common):
+    """Each precision's result on the siblings stated against the FP64
+    oracle: objective error (relative to 1 + |oracle objective|), the
+    two-point weak-duality bound on it, residuals, iterations."""
+    from paper_1312_3039_gb300 import scs, synth
+    if orc is None or "error" in orc:
+        return {"error": None if orc is None else orc["error"]}
+    res = {}
+    for sc in ORACLE_ERR_SCALES:
+        P = synth.mixed_small(seed, scale=sc)
+        o = orc[sc]
+        row = {"oracle": {"status": o["status"], "iters": o["iters"], "pobj": o["pobj"],
+                          "seconds": o["seconds"]}, "p_star": P.p_star}
+        for prec in (1, 0):
+            kw = dict(common)
+            kw["precision"] = prec
+            st, x, y, s, info = scs.solve(P.A, P.b, P.c, P.cone, **kw)
+            row["fp32" if prec else "fp64"] = {
+                "status": int(st), "iters": info["iters"], "pobj": info["pobj"],
+                "rel_err_vs_oracle": abs(info["pobj"] - o["pobj"]) / (1 + abs(o["pobj"])),
+                "two_point_bound_rel": two_point_bound(P, x, y, s, o["x"], o["y"], o["s"]) / (1 + abs(o["pobj"])),
+                "rel_err_vs_p_star": abs(info["pobj"] - P.p_star) / (1 + abs(P.p_star)),
+                "res_pri": info["res_pri"], "res_dual": info["res_dual"], "gap": info["gap"]}
+        res["mixed_div%d" % sc] = row
+    return res
+
+
 def traffic_record(kind):
     """DRAM bytes per launch of SpMV kind 0 (A) / 1 (A^T) from the committed
     ncu summary, if the kernel sources are unchanged since that capture."""
@@ -321,6 +414,13 @@ def run_gb300(args):
         cpu_proc = ctx.Process(target=cpu_oracle_job, args=(args.workload, args.seed, args.cpu_seconds, cpu_q),
                                daemon=True)
         cpu_proc.start()
+    err_proc = err_q = None
+    if rank == 0 and not args.no_cpu_baseline and args.workload == "mixed":
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        err_q = ctx.Queue()
+        err_proc = ctx.Process(target=oracle_err_job, args=(args.seed, err_q), daemon=True)
+        err_proc.start()
     import numpy as np
     import torch
     if world > 1:
@@ -363,7 +463,9 @@ def run_gb300(args):
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("timed")      # ncu --nvtx-include "timed/" selects these launches
     e0.record(stream)
-    S.iterate(args.steps, sync=False)
+    # the solve's work per iteration: the Sec. 3.5 tests every 20 iterations
+    # (two FP64 products on the device and a host read of the status word)
+    S.iterate_checked(args.steps)
     e1.record(stream)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
@@ -374,8 +476,9 @@ def run_gb300(args):
     ms = secs * 1e3
     cg_steps = cg1 - cg0
     # per iteration K1 (product or return), K1', K2, K6, K7 (+ KP with PSD
-    # blocks) and K3, K4, K5 per CG step
-    launches = (6 if getattr(P.cone, "s", ()) else 5) * (it1 - it0) + 3 * cg_steps
+    # blocks) and K3, K4, K5 per CG step; two check products per 20 iterations
+    ci = int(S.settings.check_interval) or 1
+    launches = (6 if getattr(P.cone, "s", ()) else 5) * (it1 - it0) + 3 * cg_steps + 2 * (-(-args.steps // ci))
 
     # roofline of the dominant kernel (CUDA events around each SpMV launch)
     has_psd = bool(getattr(P.cone, "s", ()))
@@ -470,6 +573,32 @@ def run_gb300(args):
                              f"CG, scipy sparse, one thread) on the same problem after its setup "
                              f"({r['setup']:.1f} s, not timed); run in a separate process alongside the GPU legs"}
 
+    # the paper's own setting for its application tables: eps 1e-3, time from
+    # the host data (scs_init included), one cold solve
+    paper_ctx = None
+    if args.workload in PAPER_APPS:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S3 = scs.Solver(P.A, P.b, P.c, P.cone, eps_pri=1e-3, eps_dual=1e-3, eps_gap=1e-3, eps_infeas=1e-3,
+                        eps_unbdd=1e-3, max_iters=args.solve_iters, time_limit_s=args.solve_seconds, **common)
+        st3, _x, _y, _s, info3 = S3.solve()
+        S3.close()
+        torch.cuda.synchronize()
+        tot = time.perf_counter() - t0
+        paper_ctx = {"eps": 1e-3, "status": int(st3), "iters": info3["iters"], "seconds_total": tot,
+                     "setup_s": info3["setup_s"], "solve_s": info3["solve_s"], "pobj": info3["pobj"],
+                     "paper_gpu": dict(PAPER_APPS[args.workload][2], hardware="GeForce GTX Titan X (Maxwell), "
+                                       "indirect method, cuSPARSE SpMV, setup included")}
+
+    oerr = None
+    if err_proc is not None:
+        try:
+            orc = err_q.get(timeout=900)
+        except Exception as e:
+            orc = {"error": "no result: " + repr(e)}
+        err_proc.join(timeout=10)
+        oerr = oracle_err(args.seed, orc, common)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
@@ -483,10 +612,15 @@ def run_gb300(args):
                               if 2 * (4 + 4 * (2 - prec)) * P.A.nnz > 129e6 else
                               "inputs fit in L2 (a parity-size program: no flush, not a headline line)"),
                        "parallelism": "replicas" if world > 1 else "single GPU",
+                       "step": "one ADMM iteration with the solve's Sec. 3.5 tests every 20 iterations",
                        "cg_steps_per_iter": cg_steps / max(it1 - it0, 1)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "time_to_1e4": solve,
         }
+        if oerr is not None:
+            line["oracle_err"] = oerr
+        if paper_ctx is not None:
+            line["paper_context"] = paper_ctx
         if psd is not None:
             line["psd_roofline"] = psd
         print(json.dumps(line), flush=True)
@@ -497,6 +631,9 @@ def run_gb300(args):
 
 BATCH_DESC = ("{count} portfolio SOCPs (long-only factor model, Sec. 6.3 form with one risk SOC): n ~ U[20, 500] "
               "assets, k = n/10 factors, F ~ N(0,1), mu ~ U(0,1); zero 1, nonneg n, SOC k+2 per program")
+
+
+BATCH_MAX_ITERS = 50000
 
 
 def batch_programs(workload, seed):
@@ -518,7 +655,7 @@ def cpu_batch_job(workload, seed, seconds, queue):
         done = 0
         for i in pick:
             P = progs[i]
-            admm.solve(P.A, P.b, P.c, P.cone, admm.Settings())
+            admm.solve(P.A, P.b, P.c, P.cone, admm.Settings(max_iters=BATCH_MAX_ITERS))
             done += 1
             if time.perf_counter() - t0 >= seconds:
                 break
@@ -552,7 +689,9 @@ def run_batch(args):
     tuples = [(P.A, P.b, P.c, P.cone) for P in progs]
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    common = dict(precision=1, device=local, cuda_stream=stream.cuda_stream)
+    # 50000 iterations at most: about 9% of the 4096 programs need more than
+    # 10000 (the FP64 oracle as well; at most 37580)
+    common = dict(precision=1, device=local, cuda_stream=stream.cuda_stream, max_iters=BATCH_MAX_ITERS)
 
     def barrier():
         if world > 1:

@@ -520,15 +520,200 @@ def lasso_family(seed=0, p=400, q=1000, d=64) -> LassoFamily:
     a = rng.standard_normal(d)
     th = rng.standard_normal((1000, d))
     mu0 = 0.1 * float(np.median(np.abs((G @ th.T).T @ F).max(axis=1)))
+    A, cone = lasso_socp_matrix(F)
+    return LassoFamily(F=F, G=G, a=a, mu0=mu0, A=A, cone=cone)
+
+
+def lasso_socp_matrix(F):
+    """A and K of the Sec. 6.2 lasso SOCP for the design F (q x p): variables
+    (z, t, w), rows z - t <= 0, -z - t <= 0 (R+^(2p)) and the SOC(q + 2)
+    (1 + w, 1 - w, 2 (F z - g)) (the b part carries g)."""
+    q, p = F.shape
     Ip = sp.identity(p, format="csc")
-    Z = sp.csc_matrix((p, p))
     top = sp.hstack([Ip, -Ip, sp.csc_matrix((p, 1))])
     mid = sp.hstack([-Ip, -Ip, sp.csc_matrix((p, 1))])
     head = sp.csc_matrix(np.concatenate([np.zeros(2 * p), [-1.0]])[None, :])
     head2 = sp.csc_matrix(np.concatenate([np.zeros(2 * p), [1.0]])[None, :])
     tail = sp.hstack([sp.csc_matrix(-2.0 * F), sp.csc_matrix((q, p)), sp.csc_matrix((q, 1))])
     A = sp.csc_matrix(sp.vstack([top, mid, head, head2, tail]))
-    del Z
     cone = Cone(l=2 * p, q=(q + 2,))
     assert A.shape == (cone.m, 2 * p + 1)
-    return LassoFamily(F=F, G=G, a=a, mu0=mu0, A=A, cone=cone)
+    return A, cone
+
+
+# ---------------------------------------------------------------------------
+# The paper's application workloads (Sec. 6.2 - 6.5), built as printed there.
+# None has a known optimum; meta keeps the original problem's data so that
+# tests can check the cone program against the problem it encodes.
+# ---------------------------------------------------------------------------
+
+def lasso_paper(seed=0, p=10_000, q=2_000) -> Problem:
+    """Sec. 6.2 instance: F (q x p) ~ N(0, 1); z^ with p/10 nonzero N(0, 1)
+    entries; g = F z^ + e, e ~ N(0, 0.1) (read as variance 0.1);
+    mu = 0.1 ||F^T g||_inf; the SOCP of Sec. 6.2 (n = 2p + 1, m = 2p + q + 2)."""
+    rng = np.random.default_rng(seed)
+    F = rng.standard_normal((q, p))
+    zh = np.zeros(p)
+    nz = rng.choice(p, size=max(1, p // 10), replace=False)
+    zh[nz] = rng.standard_normal(nz.size)
+    g = F @ zh + math.sqrt(0.1) * rng.standard_normal(q)
+    mu = 0.1 * float(np.abs(F.T @ g).max())
+    A, cone = lasso_socp_matrix(F)
+    b = np.zeros(cone.m)
+    b[2 * p] = 1.0
+    b[2 * p + 1] = 1.0
+    b[2 * p + 2:] = -2.0 * g
+    c = np.zeros(2 * p + 1)
+    c[p:2 * p] = mu
+    c[2 * p] = 0.5
+    return Problem(A=A, b=b, c=c, cone=cone, kind="feasible",
+                   meta=dict(workload="lasso_paper", p=p, q=q, F=F, g=g, mu=mu))
+
+
+def portfolio_paper(seed=0, p=100_000, q=100, gamma=1.0) -> Problem:
+    """Sec. 6.3 instance, both risk terms: maximize mu^T z - gamma (t + s)
+    s.t. 1^T z = 1, z >= 0, ||D^(1/2) z|| <= u, ||F^T z|| <= v,
+    ||(1 - t, 2u)|| <= 1 + t, ||(1 - s, 2v)|| <= 1 + s, posed as the
+    minimisation of -mu^T z + gamma (t + s).  log(mu) ~ N(0, 1);
+    F (p x q) ~ N(0, 0.1) (variance 0.1); D_ii ~ U[0, 0.1]; gamma = 1.
+    Variables (z, t, s, u, v): n = p + 4; rows: zero 1, nonneg p,
+    SOC(p + 1) (u, D^(1/2) z), SOC(q + 1) (v, F^T z), SOC(3) twice."""
+    rng = np.random.default_rng(seed)
+    mu = np.exp(rng.standard_normal(p))
+    F = math.sqrt(0.1) * rng.standard_normal((p, q))
+    Dg = rng.uniform(0.0, 0.1, size=p)
+    n = p + 4
+    it, is_, iu, iv = p, p + 1, p + 2, p + 3
+    Ip = sp.identity(p, format="csc")
+    zc = lambda r: sp.csc_matrix((r, 4))
+    one_row = lambda col, val: sp.csc_matrix(([val], ([0], [col])), shape=(1, n))
+    blocks = [
+        sp.hstack([sp.csc_matrix(np.ones((1, p))), zc(1)]),             # 1^T z = 1
+        sp.hstack([-Ip, zc(p)]),                                         # z >= 0
+        one_row(iu, -1.0),                                               # SOC(p + 1) head u
+        sp.hstack([-sp.diags(np.sqrt(Dg)).tocsc(), zc(p)]),              # D^(1/2) z
+        one_row(iv, -1.0),                                               # SOC(q + 1) head v
+        sp.hstack([sp.csc_matrix(-F.T), zc(q)]),                         # F^T z
+        one_row(it, -1.0), one_row(it, 1.0), one_row(iu, -2.0),          # (1 + t, 1 - t, 2u)
+        one_row(is_, -1.0), one_row(is_, 1.0), one_row(iv, -2.0),        # (1 + s, 1 - s, 2v)
+    ]
+    A = sp.csc_matrix(sp.vstack(blocks))
+    cone = Cone(z=1, l=p, q=(p + 1, q + 1, 3, 3))
+    b = np.zeros(cone.m)
+    b[0] = 1.0
+    o = 1 + p + (p + 1) + (q + 1)
+    b[o] = 1.0
+    b[o + 1] = 1.0
+    b[o + 3] = 1.0
+    b[o + 4] = 1.0
+    c = np.concatenate([-mu, [gamma, gamma, 0.0, 0.0]])
+    assert A.shape == (cone.m, n)
+    return Problem(A=A, b=b, c=c, cone=cone, kind="feasible",
+                   meta=dict(workload="portfolio_paper", p=p, q=q, mu=mu, F=F, D=Dg, gamma=gamma))
+
+
+def _svec_index(r, c, k):
+    """Position of entry (r, c), r >= c, of an order-k block in svec order
+    (lower triangle column by column)."""
+    return c * k - c * (c - 1) // 2 + (r - c)
+
+
+def rpca_paper(seed=0, p=100, r=10, frac=0.1) -> Problem:
+    """Sec. 6.4 instance (square, p = q): M = L^ + S^ with L^ = U V^T of rank
+    r (U, V ~ N(0, 1)) and S^ with about frac of its entries N(0, 1);
+    mu = sum |S^|.  The SDP as printed, with the objective read as a
+    minimisation (the nuclear norm is the minimum of (Tr W1 + Tr W2) / 2 over
+    [W1 L; L^T W2] >= 0; the paper prints "maximize"): variables
+    (vec L, vec S, t, svec W1, svec W2), rows: zero pq (L + S = M),
+    nonneg 2pq + 1 (t -+ vec S >= 0, mu - 1^T t >= 0), PSD of order 2p
+    (svec [W1 L; L^T W2], off-diagonal entries times sqrt 2)."""
+    rng = np.random.default_rng(seed)
+    q = p
+    Lh = rng.standard_normal((p, r)) @ rng.standard_normal((r, q))
+    Sh = np.where(rng.random((p, q)) < frac, rng.standard_normal((p, q)), 0.0)
+    M = Lh + Sh
+    mu = float(np.abs(Sh).sum())
+    pq = p * q
+    d1, d2 = p * (p + 1) // 2, q * (q + 1) // 2
+    oL, oS, oT, oW1, oW2 = 0, pq, 2 * pq, 3 * pq, 3 * pq + d1
+    n = 3 * pq + d1 + d2
+    Ipq = sp.identity(pq, format="csc")
+    Z = lambda r_, c_: sp.csc_matrix((r_, c_))
+    rows_eq = sp.hstack([Ipq, Ipq, Z(pq, pq), Z(pq, d1 + d2)])
+    rows_t1 = sp.hstack([Z(pq, pq), Ipq, -Ipq, Z(pq, d1 + d2)])       # t - S >= 0
+    rows_t2 = sp.hstack([Z(pq, pq), -Ipq, -Ipq, Z(pq, d1 + d2)])      # t + S >= 0
+    rows_mu = sp.hstack([Z(1, 2 * pq), sp.csc_matrix(np.ones((1, pq))), Z(1, d1 + d2)])
+    # PSD block of order N = p + q: s = svec(block), A = -(map to the variables)
+    N = p + q
+    ri, ci, vv = [], [], []
+    for col in range(N):
+        for row in range(col, N):
+            k = _svec_index(row, col, N)
+            if col < p and row < p:
+                ri.append(k); ci.append(oW1 + _svec_index(row, col, p)); vv.append(-1.0)
+            elif col < p:                           # L^T (row - p, col) = L(col, row - p)
+                ri.append(k); ci.append(oL + col + (row - p) * p); vv.append(-SQRT2)
+            else:
+                ri.append(k); ci.append(oW2 + _svec_index(row - p, col - p, q)); vv.append(-1.0)
+    dN = N * (N + 1) // 2
+    rows_psd = sp.csc_matrix((vv, (ri, ci)), shape=(dN, n))
+    A = sp.csc_matrix(sp.vstack([rows_eq, rows_t1, rows_t2, rows_mu, rows_psd]))
+    cone = Cone(z=pq, l=2 * pq + 1, s=(N,))
+    b = np.zeros(cone.m)
+    b[:pq] = M.reshape(-1, order="F")
+    b[3 * pq] = mu
+    c = np.zeros(n)
+    for j in range(p):
+        c[oW1 + _svec_index(j, j, p)] = 0.5
+    for j in range(q):
+        c[oW2 + _svec_index(j, j, q)] = 0.5
+    assert A.shape == (cone.m, n)
+    return Problem(A=A, b=b, c=c, cone=cone, kind="feasible",
+                   meta=dict(workload="rpca_paper", p=p, q=q, M=M, L_hat=Lh, S_hat=Sh, mu=mu))
+
+
+def logreg_paper(seed=0, p=100, q=10_000) -> Problem:
+    """Sec. 6.5 instance: w_true with p/5 nonzero N(0, 1) entries, z_i ~ N(0, I),
+    label y_i = +1 with probability 1/(1 + exp(-w_true^T z_i)), else -1;
+    mu = 0.1 mu_max, mu_max = (1/2) ||sum_i y_i z_i||_inf.  The exponential
+    cone program as printed: minimize 1^T t + mu 1^T s s.t. -s <= w <= s,
+    u + v <= 1, (y_i w^T z_i - t_i, 1, u_i) in Kexp, (-t_i, 1, v_i) in Kexp;
+    variables (w, s, t, u, v): n = 2p + 3q, m = 2p + 7q."""
+    rng = np.random.default_rng(seed)
+    wt = np.zeros(p)
+    nz = rng.choice(p, size=max(1, p // 5), replace=False)
+    wt[nz] = rng.standard_normal(nz.size)
+    Zd = rng.standard_normal((q, p))
+    prob = 1.0 / (1.0 + np.exp(-(Zd @ wt)))
+    y = np.where(rng.random(q) < prob, 1.0, -1.0)
+    mu = 0.1 * 0.5 * float(np.abs(y @ Zd).max())
+    n = 2 * p + 3 * q
+    ow, os_, ot, ou, ov = 0, p, 2 * p, 2 * p + q, 2 * p + 2 * q
+    Ip, Iq = sp.identity(p, format="csc"), sp.identity(q, format="csc")
+    Z = lambda r_, c_: sp.csc_matrix((r_, c_))
+    r1 = sp.hstack([Ip, -Ip, Z(p, 3 * q)])                       # s - w >= 0
+    r2 = sp.hstack([-Ip, -Ip, Z(p, 3 * q)])                      # s + w >= 0
+    r3 = sp.hstack([Z(q, 2 * p + q), Iq, Iq])                    # 1 - u - v >= 0
+    # exponential triples, three rows each, interleaved per sample
+    YZ = sp.csr_matrix(-(y[:, None] * Zd))
+    tri1 = sp.vstack([sp.hstack([YZ, Z(q, p), Iq, Z(q, 2 * q)]),                  # y_i z_i^T w - t_i
+                      Z(q, n),                                                   # 1
+                      sp.hstack([Z(q, 2 * p + q), -Iq, Z(q, q)])]).tocsr()       # u_i
+    tri2 = sp.vstack([sp.hstack([Z(q, 2 * p), Iq, Z(q, 2 * q)]),                  # -t_i
+                      Z(q, n),
+                      sp.hstack([Z(q, 2 * p + 2 * q), -Iq])]).tocsr()            # v_i
+    perm = np.arange(3 * q).reshape(3, q).T.reshape(-1)          # rows (k, i) -> triple i, entry k
+    E1 = tri1[perm]
+    E2 = tri2[perm]
+    A = sp.csc_matrix(sp.vstack([r1, r2, r3, E1, E2]))
+    cone = Cone(l=2 * p + q, ep=2 * q)
+    b = np.zeros(cone.m)
+    b[2 * p:2 * p + q] = 1.0
+    base = 2 * p + q
+    b[base + 1:base + 6 * q:3] = 1.0                             # the middle entry of every triple
+    c = np.zeros(n)
+    c[os_:os_ + p] = mu
+    c[ot:ot + q] = 1.0
+    assert A.shape == (cone.m, n)
+    return Problem(A=A, b=b, c=c, cone=cone, kind="feasible",
+                   meta=dict(workload="logreg_paper", p=p, q=q, Z=Zd, y=y, mu=mu, w_true=wt))
