@@ -114,6 +114,12 @@ typedef struct {
     int32_t verbose;
     int32_t device;                       /* CUDA device ordinal                        */
     void *cuda_stream;                    /* cudaStream_t to run on, or NULL            */
+    int32_t linsys;                       /* subspace step (Sec. 4.1): 0 indirect (PCG on
+                                             I + A^T A); 1 direct: (I + A^T A)^-1 formed
+                                             once at scs_init (FP64 Gauss-Jordan on the
+                                             device) and reused by every iteration and
+                                             warm-started solve (Sec. 4.2); n <= 8192 and
+                                             m n <= 2^30 (SCS_UNSUPPORTED otherwise)    */
 } scs_settings;
 
 typedef struct {
@@ -125,7 +131,8 @@ typedef struct {
                                              product of the CG's warm start on every 20th
                                              iteration (A z is carried in between), two
                                              per CG step (Table 5 counts 2 per iteration
-                                             outside CG)                                */
+                                             outside CG); linsys 1 adds one A product per
+                                             iteration and takes no CG step             */
     double pobj, dobj;                    /* c^T x and -b^T y of the returned point      */
     double res_pri, res_dual, gap;        /* unscaled ||Ax+s-b||, ||A^T y+c||, |c^T x+b^T y| */
     double tau, kappa;
@@ -137,7 +144,8 @@ typedef struct scs_work scs_work;
 /* Fill *s with defaults: eps 1e-4, alpha 1.5, cg_rate 1.5, cg_adapt 0.3,
  * cg_tol_rel 0, psd_fp64_cond 1e6,
  * max_iters 10000, check_interval 20, cg_max_iters 50, normalize 1,
- * scale_passes 10, block_scale 1, precision 1, use_graph 1, device 0. */
+ * scale_passes 10, block_scale 1, precision 1, use_graph 1, device 0,
+ * linsys 0. */
 void scs_default_settings(scs_settings *s);
 
 /* Validate and copy A, b (m), c (n) and the cone to the device, equilibrate
@@ -150,7 +158,9 @@ scs_work *scs_init(const scs_csc *A, const double *b, const double *c,
 
 /* Run the iteration from the current starting point (cold, or the one set by
  * scs_warm_start) until a Sec. 3.5 test passes, max_iters or the time limit.
- * x (n), y (m), s (m) receive, in host memory, the solution (status 1, 2) or
+ * x (n), y (m), s (m) receive, in host or device memory (unified addressing
+ * tells them apart; the call returns when the copies are done), the solution
+ * (status 1, 2) or
  * the certificate (status -1: y with b^T y = -1, x and s NaN; status -2: x
  * with c^T x = -1, s = -A x, y NaN).  Any output pointer may be NULL.  info
  * may be NULL.  The next call starts cold unless scs_warm_start is called. */
@@ -166,6 +176,13 @@ int32_t scs_warm_start(scs_work *w, const double *x, const double *y, const doub
 void scs_finish(scs_work *w);
 
 /* ---- extensions (not in the paper's interface) ---------------------------- */
+
+/* Sec. 4.2, repeated solves with the same A: new b (m) and c (n), host
+ * arrays.  The scaling D, E, the sparse layouts and (linsys 1) the cached
+ * (I + A^T A)^-1 depend on A only and are kept; sigma, rho, the scaled b^,
+ * c^ and the cached p = M^-1 h are recomputed.  The next scs_solve starts
+ * cold unless scs_warm_start is called after this. */
+int32_t scs_update_bc(scs_work *w, const double *b, const double *c);
 
 /* Reset the iterates to u0 = (0,0,1), v0 = (0,0,1) and the CG warm start to 0. */
 int32_t scs_reset(scs_work *w);
@@ -193,7 +210,8 @@ int32_t scs_get_scaling(scs_work *w, double *D, double *E, double *sigma, double
 /* Per-kernel device time since the last call (CUDA events on the work's
  * stream, collected only by scs_iterate_profiled).  kind: 0 = SpMV with A in
  * the CG loop, 1 = SpMV with A^T in the CG loop, 2 = cone projection of the
- * non-PSD rows, 3 = projection of the PSD blocks.
+ * non-PSD rows, 3 = projection of the PSD blocks, 4 = the direct subspace
+ * step (linsys 1: the dense solve and its A product).
  * Writes the summed milliseconds and the launch count. */
 int32_t scs_iterate_profiled(scs_work *w, int32_t iters);
 int32_t scs_kernel_time(scs_work *w, int32_t kind, double *ms, int64_t *launches);

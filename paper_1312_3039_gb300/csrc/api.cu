@@ -160,6 +160,7 @@ int validate_settings(const scs_settings &s) {
     if (!(s.psd_fp64_cond >= 1.0)) { set_error("psd_fp64_cond must be >= 1"); return SCS_INVALID_INPUT; }
     if (s.precision != 0 && s.precision != 1) { set_error("precision must be 0 or 1"); return SCS_INVALID_INPUT; }
     if (s.block_scale < 0 || s.block_scale > 2) { set_error("block_scale must be 0, 1 or 2"); return SCS_INVALID_INPUT; }
+    if (s.linsys != 0 && s.linsys != 1) { set_error("linsys must be 0 or 1"); return SCS_INVALID_INPUT; }
     return 0;
 }
 
@@ -208,6 +209,7 @@ void scs_default_settings(scs_settings *s) {
     s->verbose = 0;
     s->device = 0;
     s->cuda_stream = nullptr;
+    s->linsys = 0;
 }
 
 scs_work *scs_init(const scs_csc *A, const double *b, const double *c, const scs_cone *k, const scs_settings *st,
@@ -265,6 +267,17 @@ int32_t scs_reset(scs_work *w) {
 int32_t scs_iterate(scs_work *w, int32_t iters, int32_t sync) {
     if (!w || !w->eng || iters < 0) { set_error("bad argument"); return SCS_INVALID_INPUT; }
     return guarded([&] { return w->eng->iterate(iters, sync); });
+}
+
+int32_t scs_update_bc(scs_work *w, const double *b, const double *c) {
+    if (!w || !w->eng || !b || !c) { set_error("bad argument"); return SCS_INVALID_INPUT; }
+    int32_t m = 0, n = 0;
+    w->eng->dims(&m, &n, nullptr, nullptr);
+    for (int32_t i = 0; i < m; ++i)
+        if (!std::isfinite(b[i])) { set_error("non-finite entry in b"); return SCS_INVALID_INPUT; }
+    for (int32_t j = 0; j < n; ++j)
+        if (!std::isfinite(c[j])) { set_error("non-finite entry in c"); return SCS_INVALID_INPUT; }
+    return guarded([&] { return w->eng->update_bc(b, c); });
 }
 
 int32_t scs_iterate_checked(scs_work *w, int32_t iters, int32_t *status) {

@@ -1220,6 +1220,10 @@ scs_batch *scs_batch_init(int32_t count, const scs_csc *A, const double *b, cons
     if (!e) {
         if (st) s = *st;
         else scs_default_settings(&s);
+        if (s.linsys != 0) {
+            scs::set_last_error("batched programs take the indirect subspace step only (linsys 0)");
+            e = SCS_UNSUPPORTED;
+        }
     }
     std::vector<scs::HostProblem> P;
     if (!e) {

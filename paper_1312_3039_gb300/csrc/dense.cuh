@@ -4,7 +4,9 @@
 //     C (M x N) = alpha * A (M x K) * B (K x N) + beta * C
 //
 // all three column-major with leading dimensions lda, ldb, ldc.  FP32 runs
-// 128 x 128 output tiles (8 x 8 per thread) when that grid holds at least two
+// 128 x 128 output tiles (8 x 8 per thread: two groups of 4 rows and of 4
+// columns, 64 apart, so that a warp's shared-memory vector loads cover
+// contiguous 256-byte spans without bank conflicts) when that grid holds at least two
 // CTAs per SM and 64 x 64 tiles (4 x 4 per thread) otherwise (few member
 // columns: more CTAs, each with less reuse); FP64 64 x 64 tiles; 256
 // threads; k-blocks of 8 staged in shared memory, the next
@@ -47,7 +49,9 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_nn_kernel(int M, int N, int
     static_assert(TX * TY == kGemmThreads, "one thread per TM x TN sub-tile");
     constexpr int LA = BM * BK / kGemmThreads, LB = BN * BK / kGemmThreads;
     constexpr int PB = 16 / sizeof(T);              // pad of the B rows (keeps 16-byte rows, spreads banks)
-    constexpr int VA = TM * sizeof(T) / 16, VB = TN * sizeof(T) / 16;
+    constexpr int GA = TM / 4, GB = TN / 4;       // groups of 4 rows / columns per thread
+    constexpr int SA = BM / GA, SB = BN / GB;     // their spacing
+    constexpr int V4 = 4 * sizeof(T) / 16;        // vectors per group of 4
     __shared__ __align__(16) T As[2][BK][BM];
     __shared__ __align__(16) T Bs[2][BK][BN + PB];
 
@@ -100,12 +104,18 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_nn_kernel(int M, int N, int
 #pragma unroll
         for (int k = 0; k < BK; ++k) {
             T a[TM], b[TN];
-            const V *pa = reinterpret_cast<const V *>(&As[buf][k][ty * TM]);
-            const V *pb = reinterpret_cast<const V *>(&Bs[buf][k][tx * TN]);
 #pragma unroll
-            for (int v = 0; v < VA; ++v) reinterpret_cast<V *>(a)[v] = pa[v];
+            for (int g = 0; g < GA; ++g) {
+                const V *pa = reinterpret_cast<const V *>(&As[buf][k][g * SA + ty * 4]);
 #pragma unroll
-            for (int v = 0; v < VB; ++v) reinterpret_cast<V *>(b)[v] = pb[v];
+                for (int v = 0; v < V4; ++v) reinterpret_cast<V *>(a + 4 * g)[v] = pa[v];
+            }
+#pragma unroll
+            for (int g = 0; g < GB; ++g) {
+                const V *pb = reinterpret_cast<const V *>(&Bs[buf][k][g * SB + tx * 4]);
+#pragma unroll
+                for (int v = 0; v < V4; ++v) reinterpret_cast<V *>(b + 4 * g)[v] = pb[v];
+            }
 #pragma unroll
             for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -118,12 +128,12 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_nn_kernel(int M, int N, int
 
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
-        const int64_t gj = n0 + tx * TN + j;
-        if (gj >= N) break;
+        const int64_t gj = n0 + (j / 4) * SB + tx * 4 + (j % 4);
+        if (gj >= N) continue;
         T *col = C + gj * ldc;
 #pragma unroll
         for (int i = 0; i < TM; ++i) {
-            const int64_t gi = m0 + ty * TM + i;
+            const int64_t gi = m0 + (i / 4) * SA + ty * 4 + (i % 4);
             if (gi < M) col[gi] = beta == T(0) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * col[gi];
         }
     }
@@ -155,6 +165,44 @@ inline cudaError_t gemm_nn(cudaStream_t stream, int M, int N, int K, T alpha, co
             return gemm_nn_tiles<T, GemmTile<T, 128, 8>>(stream, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
     }
     return gemm_nn_tiles<T, GemmTile<T, 64, 4>>(stream, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+// ---------------------------------------------------------------------------
+// In-place inverse of a symmetric positive definite G (n x n, column-major)
+// by Gauss-Jordan elimination without pivoting (the pivots of an SPD matrix
+// are positive; for G = I + A^T A they are at least 1).  Step k:
+//   colk = G[:, k] with entry k taken as 0; row k of G divided by G[k][k]
+//   (with G[k][k] := 1); G[i][j] -= colk_i row_k[j] for i != k (G[i][k]
+//   taken as 0).  After the n steps G holds G^-1.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void gj_pivot_kernel(T *G, int n, int k, T *colk) {
+    const T piv = G[(size_t)k * n + k];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        colk[i] = i == k ? T(0) : G[(size_t)k * n + i];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        colk[n + j] = (j == k ? T(1) : G[(size_t)j * n + k]) / piv;
+}
+
+template <typename T>
+__global__ void gj_update_kernel(T *G, int n, int k, const T *colk) {
+    const int64_t total = (int64_t)n * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = static_cast<int>(e / n), i = static_cast<int>(e % n);   // column-major: e = j n + i
+        const T rkj = colk[n + j];
+        if (i == k) G[e] = rkj;
+        else G[e] = (j == k ? T(0) : G[e]) - colk[i] * rkj;
+    }
+}
+
+// Enqueue the n steps on `stream`; colk is device scratch of 2 n entries.
+template <typename T>
+inline cudaError_t invert_spd_gj(cudaStream_t stream, T *G, int n, T *colk, int grid) {
+    for (int k = 0; k < n; ++k) {
+        gj_pivot_kernel<T><<<1, 1024, 0, stream>>>(G, n, k, colk);
+        gj_update_kernel<T><<<grid, 256, 0, stream>>>(G, n, k, colk);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace dense

@@ -17,10 +17,14 @@
 #include <vector>
 
 #include "../../include/scs_gpu.h"
+#include "dense.cuh"
 #include "engine_base.h"
 #include "kernels.cuh"
 
 namespace scs {
+
+// largest n of the direct subspace step (the dense inverse: 512 MB in FP64)
+constexpr int kDirectMaxN = 8192;
 
 template <typename T>
 class Engine : public EngineBase {
@@ -127,6 +131,15 @@ class Engine : public EngineBase {
             for (auto &e : ev_) SCS_CUDA(cudaEventCreate(&e));
         }
         for (int it = 0; it < iters; ++it) {
+            if (direct_) {
+                launch_K1();
+                timed(1, [&] { launch_K2(CondHandle{0, 0}); });
+                timed(4, [&] { launch_D1(); launch_D2(); });
+                launch_K6();
+                if (psd_.npsd) timed(3, [&] { launch_KP(); });
+                timed(2, [&] { launch_K7(); });
+                continue;
+            }
             launch_K1();                  // kind 0 times the CG products q = A p only
             timed(1, [&] { launch_K2(CondHandle{0, 0}); });
             for (int c = 0; c < st_.cg_max_iters; ++c) {
@@ -146,7 +159,7 @@ class Engine : public EngineBase {
     }
 
     int kernel_time(int kind, double *ms, int64_t *launches) override {
-        if (kind < 0 || kind > 3) return SCS_INVALID_INPUT;
+        if (kind < 0 || kind > 4) return SCS_INVALID_INPUT;
         if (ms) *ms = prof_ms_[kind];
         if (launches) *launches = prof_n_[kind];
         prof_ms_[kind] = 0.0;
@@ -234,16 +247,18 @@ class Engine : public EngineBase {
         output_kernel<T><<<grid_for(n_ + 2 * m_), kBlock, 0, stream_>>>(n_, m_, status, u_, v_, D_, E_, ax_, S_,
                                                                     out_, out_ + n_, out_ + n_ + m_);
         SCS_CUDA(cudaGetLastError());
-        if (x) SCS_CUDA(cudaMemcpyAsync(x, out_, sizeof(double) * n_, cudaMemcpyDeviceToHost, stream_));
-        if (y) SCS_CUDA(cudaMemcpyAsync(y, out_ + n_, sizeof(double) * m_, cudaMemcpyDeviceToHost, stream_));
-        if (s) SCS_CUDA(cudaMemcpyAsync(s, out_ + n_ + m_, sizeof(double) * m_, cudaMemcpyDeviceToHost, stream_));
+        // host or device outputs: unified addressing tells them apart
+        if (x) SCS_CUDA(cudaMemcpyAsync(x, out_, sizeof(double) * n_, cudaMemcpyDefault, stream_));
+        if (y) SCS_CUDA(cudaMemcpyAsync(y, out_ + n_, sizeof(double) * m_, cudaMemcpyDefault, stream_));
+        if (s) SCS_CUDA(cudaMemcpyAsync(s, out_ + n_ + m_, sizeof(double) * m_, cudaMemcpyDefault, stream_));
         SCS_CUDA(cudaMemcpyAsync(Sh_, S_, sizeof(Scalars), cudaMemcpyDeviceToHost, stream_));
         SCS_CUDA(cudaStreamSynchronize(stream_));
         if (info) {
             info->status = status;
             info->iters = Sh_->k;
             info->cg_iters = static_cast<int32_t>(Sh_->cg_total);
-            info->matvecs = Sh_->k + (Sh_->k + kAzEvery - 1) / kAzEvery + 2 * static_cast<int32_t>(Sh_->cg_total);
+            info->matvecs = Sh_->k + (Sh_->k + kAzEvery - 1) / kAzEvery + 2 * static_cast<int32_t>(Sh_->cg_total) +
+                            (direct_ ? Sh_->k : 0);     // the direct step's A d
             info->tau = Sh_->tau;
             info->kappa = Sh_->kappa;
             info->res_pri = Sh_->res_pri;
@@ -350,6 +365,7 @@ class Engine : public EngineBase {
         az_ = dalloc<T>(m_);
         double *tmp_m = dalloc<double>(m_), *tmp_n = dalloc<double>(n_);
         double *red_out = dalloc<double>(4);
+        red_out_ = red_out;
 
         fill(D_, m_, 1.0);
         fill(E_, n_, 1.0);
@@ -480,6 +496,7 @@ class Engine : public EngineBase {
             SCS_CUDA(cudaStreamSynchronize(stream_));
             double mean_row = m_ ? h[0] / m_ : 1.0;
             if (!(mean_row > 0.0)) mean_row = 1.0;
+            mean_row_ = mean_row;
             sigma_ = 1.0 / std::max(std::sqrt(h[1]), 1e-4);
             rho_ = mean_row / std::max(std::sqrt(h[2]), 1e-4);
         } else {
@@ -534,7 +551,18 @@ class Engine : public EngineBase {
         // FP64 values (the same arrays in the FP64 engine) for the termination tests
         A64_ = mkcsr(a_val64, a_rowptr, a_col, a_rowid, LA, m_);
         At64_ = mkcsr(at_val64, at_rowptr, at_col, at_rowid, LAt, n_);
+        if (st_.linsys == 1) setup_direct(a_rowptr, a_col, a_val64, a_rowid);
 
+        // reciprocals of the scaling for the termination tests (the FP64
+        // divide is slow on this part; the tests run every 20 iterations)
+        Dinv_ = dalloc<double>(m_);
+        Einv_ = dalloc<double>(n_);
+        {
+            double *di = Dinv_, *ei = Einv_;
+            const double *Dd = D_, *Ed = E_;
+            foreach_kernel<<<grid_for(m_), kBlock, 0, stream_>>>([=] __device__(int i) { di[i] = 1.0 / Dd[i]; }, m_);
+            foreach_kernel<<<grid_for(n_), kBlock, 0, stream_>>>([=] __device__(int j) { ei[j] = 1.0 / Ed[j]; }, n_);
+        }
         // host copies of the scaling (warm start, scs_get_scaling)
         Dh_.resize(m_);
         Eh_.resize(n_);
@@ -557,13 +585,127 @@ class Engine : public EngineBase {
         sh.sigma = sigma_;
         sh.rho = rho_;
         sh.hp1 = 1.0;
-        // cached p = M^-1 h solved tightly (Sec. 4.1): CG from zero with the
-        // right-hand side r = h, i.e. u = (c^, b^, 0), v = 0
+        sh.cg_rate = st_.cg_rate;
+        sh.cg_adapt = st_.cg_adapt;
+        sh.cg_tol_rel = st_.cg_tol_rel;
+        sh.cg_max = st_.cg_max_iters;
+        SCS_CUDA(cudaMemcpy(S_, &sh, sizeof(Scalars), cudaMemcpyHostToDevice));
+        compute_p();
+        dfree(tmp_m);
+        dfree(tmp_n);
+        set_initial_point();
+        if (st_.use_graph) build_graph();
+        SCS_CUDA(cudaStreamSynchronize(stream_));
+    }
+
+    // Direct method (Sec. 4.1 with the factorization cached, Sec. 4.2): dense
+    // A^ and A^T from the scaled FP64 CSR (stored rows in length-class order,
+    // rowid maps them back), G = I + A^T A by the FP64 GEMM, G^-1 in place by
+    // FP64 Gauss-Jordan, then kept in the iteration's precision.
+    void setup_direct(const int32_t *rp, const int32_t *col, const double *val, const int32_t *rowid) {
+        if (n_ > kDirectMaxN || (int64_t)m_ * n_ > ((int64_t)1 << 30))
+            throw CudaError("linsys 1 (direct): needs n <= 8192 and m n <= 2^30", SCS_UNSUPPORTED);
+        const int m = m_, n = n_;
+        const size_t mn = (size_t)m * n, nn = (size_t)n * n;
+        double *Ad = dalloc<double>(mn), *Atd = dalloc<double>(mn), *G = dalloc<double>(nn);
+        double *colk = dalloc<double>(2 * (size_t)n);
+        SCS_CUDA(cudaMemsetAsync(Ad, 0, sizeof(double) * mn, stream_));
+        SCS_CUDA(cudaMemsetAsync(Atd, 0, sizeof(double) * mn, stream_));
+        foreach_kernel<<<grid_for(m), kBlock, 0, stream_>>>(
+            [=] __device__(int r) {
+                const int i = rowid[r];
+                for (int k = rp[r]; k < rp[r + 1]; ++k) {
+                    Ad[(size_t)col[k] * m + i] = val[k];
+                    Atd[(size_t)i * n + col[k]] = val[k];
+                }
+            },
+            m);
+        foreach_kernel<<<grid_for((int64_t)nn), kBlock, 0, stream_>>>(
+            [=] __device__(int64_t e) { G[e] = (e % (n + 1) == 0) ? 1.0 : 0.0; }, (int64_t)nn);
+        SCS_CUDA(dense::gemm_nn<double>(stream_, n, n, m, 1.0, Atd, n, Ad, m, 1.0, G, n));   // I + A^T A
+        SCS_CUDA(dense::invert_spd_gj<double>(stream_, G, n, colk, grid_for((int64_t)nn)));
+        if (std::is_same<T, double>::value) {
+            Minv_ = reinterpret_cast<T *>(G);
+        } else {
+            Minv_ = dalloc<T>(nn);
+            T *mi = Minv_;
+            foreach_kernel<<<grid_for((int64_t)nn), kBlock, 0, stream_>>>(
+                [=] __device__(int64_t e) { mi[e] = static_cast<T>(G[e]); }, (int64_t)nn);
+        }
+        SCS_CUDA(cudaGetLastError());
+        SCS_CUDA(cudaStreamSynchronize(stream_));
+        dfree(Ad);
+        dfree(Atd);
+        dfree(colk);
+        if (!std::is_same<T, double>::value) dfree(G);
+        direct_ = true;
+    }
+
+    // New b, c with the same A (Sec. 4.2): D, E, the layouts and a cached
+    // (I + A^T A)^-1 depend on A only and are kept; sigma, rho, b^, c^,
+    // p = M^-1 h and 1 + h^T p are recomputed, and the next solve starts cold.
+    int update_bc(const double *b, const double *c) override {
+        SCS_CUDA(cudaSetDevice(device_));
+        double nb = 0.0, nc = 0.0;
+        for (int i = 0; i < m_; ++i) nb += b[i] * b[i];
+        for (int j = 0; j < n_; ++j) nc += c[j] * c[j];
+        SCS_CUDA(cudaMemcpyAsync(b_, b, sizeof(double) * m_, cudaMemcpyHostToDevice, stream_));
+        SCS_CUDA(cudaMemcpyAsync(c_, c, sizeof(double) * n_, cudaMemcpyHostToDevice, stream_));
+        if (st_.normalize) {
+            const double *Db = D_, *bb = b_, *Ec = E_, *cc = c_;
+            reduce_kernel<<<grid_for(m_), kBlock, 0, stream_>>>(
+                [=] __device__(int i) { const double t = Db[i] * bb[i]; return t * t; }, m_, rb_, red_out_ + 1);
+            reduce_kernel<<<grid_for(n_), kBlock, 0, stream_>>>(
+                [=] __device__(int i) { const double t = Ec[i] * cc[i]; return t * t; }, n_, rb_, red_out_ + 2);
+            double h[2];
+            SCS_CUDA(cudaMemcpyAsync(h, red_out_ + 1, sizeof(h), cudaMemcpyDeviceToHost, stream_));
+            SCS_CUDA(cudaStreamSynchronize(stream_));
+            sigma_ = 1.0 / std::max(std::sqrt(h[0]), 1e-4);
+            rho_ = mean_row_ / std::max(std::sqrt(h[1]), 1e-4);
+        }
+        {
+            double *bd = b_, *cd = c_;
+            const double *Dd = D_, *Ed = E_;
+            const double sg = sigma_, rh = rho_;
+            foreach_kernel<<<grid_for(m_), kBlock, 0, stream_>>>([=] __device__(int i) { bd[i] *= sg * Dd[i]; }, m_);
+            foreach_kernel<<<grid_for(n_), kBlock, 0, stream_>>>([=] __device__(int j) { cd[j] *= rh * Ed[j]; }, n_);
+            if (!std::is_same<T, double>::value) {
+                T *bt = bT_, *ct = cT_;
+                foreach_kernel<<<grid_for(m_), kBlock, 0, stream_>>>(
+                    [=] __device__(int i) { bt[i] = static_cast<T>(bd[i]); }, m_);
+                foreach_kernel<<<grid_for(n_), kBlock, 0, stream_>>>(
+                    [=] __device__(int j) { ct[j] = static_cast<T>(cd[j]); }, n_);
+            }
+        }
+        Scalars sh{};
+        SCS_CUDA(cudaMemcpyAsync(&sh, S_, sizeof(Scalars), cudaMemcpyDeviceToHost, stream_));
+        SCS_CUDA(cudaStreamSynchronize(stream_));
+        sh.sigma = sigma_;
+        sh.rho = rho_;
+        sh.nb = std::sqrt(nb);
+        sh.nc = std::sqrt(nc);
+        SCS_CUDA(cudaMemcpy(S_, &sh, sizeof(Scalars), cudaMemcpyHostToDevice));
+        compute_p();
+        set_initial_point();
+        warm_pending_ = false;
+        SCS_CUDA(cudaStreamSynchronize(stream_));
+        return 0;
+    }
+
+    // cached p = M^-1 h (Sec. 4.1), h = (c^, b^), solved tightly: CG from
+    // zero with the right-hand side r = h, i.e. u = (c^, b^, 0), v = 0; then
+    // 1 + h^T p.  The device scalars keep every other field.
+    void compute_p() {
+        double *red_out = red_out_;
+        Scalars sh{};
+        SCS_CUDA(cudaMemcpy(&sh, S_, sizeof(Scalars), cudaMemcpyDeviceToHost));
+        const Scalars keep = sh;
         sh.cg_rate = 0.0;
         sh.cg_adapt = 0.0;
         sh.dstep = INFINITY;
         sh.cg_tol_rel = std::is_same<T, double>::value ? 1e-14 : 1e-7;
         sh.cg_max = std::max(10 * st_.cg_max_iters, 500);
+        sh.k = 0;          // K1 takes the product A z (z restarts from 0 here)
         SCS_CUDA(cudaMemcpyAsync(S_, &sh, sizeof(Scalars), cudaMemcpyHostToDevice, stream_));
         SCS_CUDA(cudaMemsetAsync(u_, 0, sizeof(T) * N_, stream_));
         SCS_CUDA(cudaMemsetAsync(v_, 0, sizeof(T) * N_, stream_));
@@ -595,7 +737,7 @@ class Engine : public EngineBase {
             if (std::is_same<T, double>::value) {
                 pT_ = reinterpret_cast<T *>(p_);
             } else {
-                pT_ = dalloc<T>(n_ + m_);
+                if (!pT_) pT_ = dalloc<T>(n_ + m_);
                 T *pt = pT_;
                 foreach_kernel<<<grid_for(n_ + m_), kBlock, 0, stream_>>>(
                     [=] __device__(int i) { pt[i] = static_cast<T>(pd[i]); }, n_ + m_);
@@ -604,17 +746,9 @@ class Engine : public EngineBase {
         double hp;
         SCS_CUDA(cudaMemcpyAsync(&hp, red_out + 3, sizeof(double), cudaMemcpyDeviceToHost, stream_));
         SCS_CUDA(cudaStreamSynchronize(stream_));
-        sh.hp1 = 1.0 + hp;
-        sh.cg_rate = st_.cg_rate;
-        sh.cg_adapt = st_.cg_adapt;
-        sh.cg_tol_rel = st_.cg_tol_rel;
-        sh.cg_max = st_.cg_max_iters;
-        SCS_CUDA(cudaMemcpy(S_, &sh, sizeof(Scalars), cudaMemcpyHostToDevice));
-        dfree(tmp_m);
-        dfree(tmp_n);
-        set_initial_point();
-        if (st_.use_graph) build_graph();
-        SCS_CUDA(cudaStreamSynchronize(stream_));
+        Scalars out = keep;
+        out.hp1 = 1.0 + hp;
+        SCS_CUDA(cudaMemcpy(S_, &out, sizeof(Scalars), cudaMemcpyHostToDevice));
     }
 
     // eigenvectors of every PSD block back to I (cold Jacobi start)
@@ -689,12 +823,19 @@ class Engine : public EngineBase {
     }
     void launch_K4() {
         guard(At_.grid());
-        EpiAtCG<T> e{diag_, z_, r_, pv_, S_, T(0)};
+        EpiAtCG<T> e{diag_, z_, r_, pv_, S_, T(0), q_, yacc_, az_, m_};
         spmv_kernel<T, T, T, EpiAtCG<T>><<<At_.grid(), kBlock, 0, cur_>>>(At_, q_, e, rb_);
     }
     void launch_K5(CondHandle h) {
-        cg_update_kernel<T><<<grid_for(std::max(n_, m_)), kBlock, 0, cur_>>>(n_, m_, q_, yacc_, az_, r_, diag_, pv_,
-                                                                              S_, h, rb_);
+        cg_update_kernel<T><<<grid_for(n_), kBlock, 0, cur_>>>(n_, m_, q_, yacc_, az_, r_, diag_, pv_, S_, h, rb_);
+    }
+    void launch_D1() {
+        direct_gemv_kernel<T><<<grid_for((int64_t)n_ * 32), kBlock, 0, cur_>>>(n_, Minv_, r_, z_, pv_);
+    }
+    void launch_D2() {
+        guard(A_.grid());
+        EpiADirect<T> e{q_, yacc_, az_, S_};
+        spmv_kernel<T, T, T, EpiADirect<T>><<<A_.grid(), kBlock, 0, cur_>>>(A_, pv_, e, rb_);
     }
     void launch_K6() {
         smw_kernel<T><<<grid_for(n_ + m_), kBlock, 0, cur_>>>(n_, m_, cT_, bT_, z_, yacc_, S_, rb_);
@@ -717,9 +858,9 @@ class Engine : public EngineBase {
     void launch_check() {
         guard(A64_.grid());
         guard(At64_.grid());
-        EpiChkA<T> ea{u_, v_, b_, D_, ax_, S_, n_, N_, 0.0};
+        EpiChkA<T> ea{u_, v_, b_, Dinv_, ax_, S_, n_, N_, 0.0};
         spmv_kernel<double, T, double, EpiChkA<T>><<<A64_.grid(), kBlock, 0, stream_>>>(A64_, u_, ea, rb_);
-        EpiChkAt<T> eb{u_, v_, c_, E_, S_, N_, 0.0};
+        EpiChkAt<T> eb{u_, v_, c_, Einv_, S_, N_, 0.0};
         spmv_kernel<double, T, double, EpiChkAt<T>><<<At64_.grid(), kBlock, 0, stream_>>>(At64_, u_ + n_, eb,
                                                                                                   rb_);
         SCS_CUDA(cudaGetLastError());
@@ -742,6 +883,14 @@ class Engine : public EngineBase {
     void launch_iteration_plain() {
         launch_K1();
         launch_K2(CondHandle{0, 0});
+        if (direct_) {
+            launch_D1();
+            launch_D2();
+            launch_K6();
+            launch_KP();
+            launch_K7();
+            return;
+        }
         for (int c = 0; c < st_.cg_max_iters; ++c) {
             launch_K3();
             launch_K4();
@@ -765,6 +914,20 @@ class Engine : public EngineBase {
 
     // Graph of one iteration: K1 -> K2 -> WHILE(active){K3 -> K4 -> K5} -> K6 -> K7.
     void build_graph() {
+        if (direct_) {      // K1 -> K2 -> KD1 -> KD2 -> K6 -> KP -> K7: no CG loop
+            SCS_CUDA(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal));
+            cur_ = stream_;
+            launch_K1();
+            launch_K2(CondHandle{0, 0});
+            launch_D1();
+            launch_D2();
+            launch_K6();
+            launch_KP();
+            launch_K7();
+            SCS_CUDA(cudaStreamEndCapture(stream_, &graph_));
+            SCS_CUDA(cudaGraphInstantiate(&exec_, graph_, 0));
+            return;
+        }
         SCS_CUDA(cudaGraphCreate(&graph_, 0));
         cudaGraphConditionalHandle h;
         SCS_CUDA(cudaGraphConditionalHandleCreate(&h, graph_, 1, cudaGraphCondAssignDefault));
@@ -821,6 +984,7 @@ class Engine : public EngineBase {
     T *u_ = nullptr, *v_ = nullptr, *bT_ = nullptr, *cT_ = nullptr, *pT_ = nullptr;
     double *b_ = nullptr, *c_ = nullptr, *D_ = nullptr, *E_ = nullptr;
     double *p_ = nullptr, *ax_ = nullptr, *out_ = nullptr;
+    double *Dinv_ = nullptr, *Einv_ = nullptr;   // 1 / D, 1 / E for the termination tests
     T *z_ = nullptr, *r_ = nullptr, *pv_ = nullptr, *diag_ = nullptr, *q_ = nullptr, *yacc_ = nullptr;
     T *az_ = nullptr;      // A^ z_x carried between iterations (kernels.cuh, K1')
     std::vector<double> Dh_, Eh_;
@@ -828,8 +992,13 @@ class Engine : public EngineBase {
     cudaGraph_t graph_ = nullptr;
     cudaGraphExec_t exec_ = nullptr;
     std::vector<cudaEvent_t> ev_;
-    double prof_ms_[4] = {0, 0, 0, 0};
-    int64_t prof_n_[4] = {0, 0, 0, 0};
+    double prof_ms_[5] = {0, 0, 0, 0, 0};
+    int64_t prof_n_[5] = {0, 0, 0, 0, 0};
+    // direct subspace step (linsys 1): (I + A^T A)^-1, n x n, in T
+    bool direct_ = false;
+    T *Minv_ = nullptr;
+    double *red_out_ = nullptr;   // device scratch of the setup reductions
+    double mean_row_ = 1.0;       // mean row norm of A^ (rho's numerator, Sec. 5)
     PsdDev<T> psd_{};
     size_t psd_smem_ = 0;
 };

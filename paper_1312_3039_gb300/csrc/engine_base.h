@@ -46,6 +46,7 @@ class EngineBase {
     virtual int solve(double *x, double *y, double *s, scs_info *info) = 0;
     virtual int warm_start(const double *x, const double *y, const double *s) = 0;
     virtual int reset() = 0;
+    virtual int update_bc(const double *b, const double *c) = 0;
     virtual int iterate(int iters, int sync) = 0;
     virtual int iterate_checked(int iters, int32_t *status) = 0;
     virtual int iterate_profiled(int iters) = 0;

@@ -382,29 +382,6 @@ static __global__ void densify_kernel(const int32_t *__restrict__ rp, const int3
         }
 }
 
-// Gauss-Jordan inversion of the SPD G (n x n, in place), step k:
-//   colk = G[:, k] (i != k); row k /= G[k][k] (with G[k][k] := 1);
-//   G[i][j] -= colk_i row_k[j] (G[i][k] taken as 0) for i != k
-static __global__ void gj_pivot_kernel(double *G, int n, int k, double *colk) {
-    const double piv = G[(size_t)k * n + k];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        colk[i] = i == k ? 0.0 : G[(size_t)k * n + i];
-    }
-    __syncthreads();
-    if (blockIdx.x == 0)
-        for (int j = threadIdx.x; j < n; j += blockDim.x)
-            colk[n + j] = (j == k ? 1.0 : G[(size_t)j * n + k]) / piv;
-}
-static __global__ void gj_update_kernel(double *G, int n, int k, const double *colk) {
-    const int64_t total = (int64_t)n * n;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int j = static_cast<int>(e / n), i = static_cast<int>(e % n);   // column-major: e = j n + i
-        const double rkj = colk[n + j];
-        if (i == k) G[e] = rkj;
-        else G[e] = (j == k ? 0.0 : G[e]) - colk[i] * rkj;
-    }
-}
-
 template <typename T>
 static __global__ void cast_kernel(const double *__restrict__ a, T *__restrict__ b, int64_t len) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x)
@@ -618,11 +595,7 @@ class FamilyEngine : public FamilyBase {
             for (int j = 0; j < n; ++j) I[(size_t)j * n + j] = 1.0;
             SCS_CUDA(cudaMemcpyAsync(G, I.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice, stream_));
             SCS_CUDA(dense::gemm_nn<double>(stream_, n, n, m, 1.0, At64, n, A64, m, 1.0, G, n));   // I + A^T A
-            for (int k = 0; k < n; ++k) {
-                gj_pivot_kernel<<<1, 1024, 0, stream_>>>(G, n, k, colk);
-                gj_update_kernel<<<grid((int64_t)n * n), kBlock, 0, stream_>>>(G, n, k, colk);
-            }
-            SCS_CUDA(cudaGetLastError());
+            SCS_CUDA(dense::invert_spd_gj<double>(stream_, G, n, colk, grid((int64_t)n * n)));
             SCS_CUDA(cudaStreamSynchronize(stream_));
         }
         Ah_ = dalloc<T>((size_t)m * n);

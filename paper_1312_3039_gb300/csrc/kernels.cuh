@@ -27,9 +27,10 @@
 //                  p0 = r0 / diag, CG dots, CG tolerance zeta^k
 //   CG step (while not converged):
 //   K3  SpMV A   : q = A p,  alpha = r.s / (p.p + q.q)   (p^T (I + A^T A) p)
-//   K4  SpMV A^T : z += alpha p,  r -= alpha (p + A^T q),  new r.s, ||r||
-//   K5  update   : y_acc += alpha q (keeps y_acc = r_y + A z), az += alpha q,
-//                  p = s + beta p
+//   K4  SpMV A^T : z += alpha p,  r -= alpha (p + A^T q),  new r.s, ||r||;
+//                  its CTAs also run y_acc += alpha q (keeps y_acc = r_y + A z)
+//                  and az += alpha q over the m rows
+//   K5  update   : p = s + beta p
 //   K6  SMW      : gamma = (c^.z_x + b^.y_acc) / (1 + h^T p)
 //   KP  relax + project + dual update of the PSD blocks (one CTA per block,
 //       Jacobi eigensolver; psd.cuh), when the cone has PSD blocks
@@ -189,7 +190,9 @@ struct EpiACG {
 };
 
 // ---------------------------------------------------------------------------
-// K4: rows of A^T.  (I + A^T A) p = p + A^T q; z += alpha p; r -= alpha G p
+// K4: rows of A^T.  (I + A^T A) p = p + A^T q; z += alpha p; r -= alpha G p;
+// side task over the m rows of A: y_acc += alpha q (keeps y_acc = r_y + A z)
+// and az += alpha q (the carried A z), while the product's gathers wait
 // ---------------------------------------------------------------------------
 template <typename T>
 struct EpiAtCG {
@@ -199,6 +202,16 @@ struct EpiAtCG {
     T *z, *r, *p;
     Scalars *S;
     T alpha;
+    const T *q;
+    T *yacc, *az;
+    int m;
+    __device__ void side(int b, int nb) {
+        for (int i = b * kBlock + threadIdx.x; i < m; i += nb * kBlock) {
+            const T qi = q[i];
+            yacc[i] = yacc[i] + alpha * qi;
+            az[i] = az[i] + alpha * qi;
+        }
+    }
     struct In { T p, z, r, d; };
     __device__ bool skip() const { return !S->active; }
     __device__ void begin() { alpha = static_cast<T>(S->alpha); }
@@ -225,7 +238,7 @@ struct EpiAtCG {
 };
 
 // ---------------------------------------------------------------------------
-// K5: y_acc += alpha q;  az += alpha q;  p = r / diag + beta p
+// K5: p = r / diag + beta p (K4's side task has updated y_acc and az)
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kBlock) cg_update_kernel(int n, int m, const T *__restrict__ q,
@@ -234,21 +247,13 @@ __global__ void __launch_bounds__(kBlock) cg_update_kernel(int n, int m, const T
                                                            T *__restrict__ p, Scalars *S, CondHandle cond,
                                                            ReduceBuf rb) {
     if (!S->active) return;
-    const T alpha = static_cast<T>(S->alpha);
     const T beta = static_cast<T>(S->beta);
     const int done = S->done;
     T acc = 0;
-    const int total = n > m ? n : m;
-    for (int i = blockIdx.x * kBlock + threadIdx.x; i < total; i += gridDim.x * kBlock) {
-        if (i < m) {
-            yacc[i] = yacc[i] + alpha * q[i];
-            az[i] = az[i] + alpha * q[i];
-        }
-        if (i < n && !done) {
-            const T pj = r[i] / diag[i] + beta * p[i];
-            p[i] = pj;
-            acc += pj * pj;
-        }
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < n && !done; i += gridDim.x * kBlock) {
+        const T pj = r[i] / diag[i] + beta * p[i];
+        p[i] = pj;
+        acc += pj * pj;
     }
     double red[1] = {static_cast<double>(acc)}, tot[1];
     if (grid_sum<1>(red, rb, kSiteCGUpd, tot)) {
@@ -259,6 +264,55 @@ __global__ void __launch_bounds__(kBlock) cg_update_kernel(int n, int m, const T
         }
     }
 }
+
+// ---------------------------------------------------------------------------
+// Direct subspace step (settings.linsys = 1, Sec. 4.1 "direct method" with
+// the factorization cached, Sec. 4.2): after K2 has formed
+// r0 = t - (I + A^T A) z_prev, one exact correction d = (I + A^T A)^-1 r0
+// replaces the CG loop:
+//   KD1 dense   : d = Minv r0 (Minv symmetric, n x n, column j read as row j;
+//                 one warp per row, lanes striding over the row, a fixed
+//                 shuffle tree: deterministic); z += d; p = d
+//   KD2 SpMV A  : q = A^ d; y_acc += q (keeps y_acc = r_y + A^ z);
+//                 az += q (keeps the carried az = A^ z)
+// so that z = Minv t and y_acc = r_y + A^ z up to rounding.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kBlock) direct_gemv_kernel(int n, const T *__restrict__ Minv,
+                                                             const T *__restrict__ r, T *__restrict__ z,
+                                                             T *__restrict__ p) {
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * kWarps;
+    for (int j = blockIdx.x * kWarps + (threadIdx.x >> 5); j < n; j += warps) {
+        const T *row = Minv + (size_t)j * n;
+        T acc = 0;
+        for (int i = lane; i < n; i += 32) acc += row[i] * r[i];
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            z[j] = z[j] + acc;
+            p[j] = acc;
+        }
+    }
+}
+
+template <typename T>
+struct EpiADirect {
+    static constexpr int NV = 1;
+    static constexpr int kSite = kSiteACG;     // K3 does not run in the direct step
+    T *q, *yacc, *az;
+    Scalars *S;
+    struct In { T y, a; };
+    __device__ bool skip() const { return false; }
+    __device__ void begin() {}
+    __device__ In load(int i) const { return In{yacc[i], az[i]}; }
+    __device__ void row(int i, T s, const In &in, T (&red)[NV]) {
+        q[i] = s;
+        yacc[i] = in.y + s;
+        az[i] = in.a + s;
+        red[0] += s * s;
+    }
+    __device__ void finish(const double (&t)[NV]) { S->qq = t[0]; }
+};
 
 // ---------------------------------------------------------------------------
 // K6: gamma = h^T z / (1 + h^T p)
@@ -554,22 +608,22 @@ struct EpiChkA {
     static constexpr int NV = 3;
     static constexpr int kSite = kSiteChkA;
     const T *u, *v;
-    const double *b, *D;
+    const double *b, *Dinv;     // 1 / D: no FP64 division per row
     double *ax;
     Scalars *S;
     int n, N;
     double tau;
-    struct In { double vs, b, d, uy; };
+    struct In { double vs, b, dinv, uy; };
     __device__ bool skip() const { return false; }
     __device__ void begin() { tau = static_cast<double>(u[N - 1]); }
     __device__ In load(int i) const {
-        return In{static_cast<double>(v[n + i]), b[i], D[i], static_cast<double>(u[n + i])};
+        return In{static_cast<double>(v[n + i]), b[i], Dinv[i], static_cast<double>(u[n + i])};
     }
     __device__ void row(int i, double s, const In &in, double (&red)[NV]) {
         ax[i] = s;
         const double a = s + in.vs;
-        const double pr = (a - tau * in.b) / in.d;
-        const double ub = a / in.d;
+        const double pr = (a - tau * in.b) * in.dinv;
+        const double ub = a * in.dinv;
         red[0] += pr * pr;
         red[1] += ub * ub;
         red[2] += in.b * in.uy;
@@ -586,17 +640,17 @@ struct EpiChkAt {
     static constexpr int NV = 3;
     static constexpr int kSite = kSiteChkAt;
     const T *u, *v;
-    const double *c, *E;
+    const double *c, *Einv;     // 1 / E
     Scalars *S;
     int N;
     double tau;
-    struct In { double c, e, ux; };
+    struct In { double c, einv, ux; };
     __device__ bool skip() const { return false; }
     __device__ void begin() { tau = static_cast<double>(u[N - 1]); }
-    __device__ In load(int j) const { return In{c[j], E[j], static_cast<double>(u[j])}; }
+    __device__ In load(int j) const { return In{c[j], Einv[j], static_cast<double>(u[j])}; }
     __device__ void row(int j, double s, const In &in, double (&red)[NV]) {
-        const double du = (s + tau * in.c) / in.e;
-        const double inf = s / in.e;
+        const double du = (s + tau * in.c) * in.einv;
+        const double inf = s * in.einv;
         red[0] += du * du;
         red[1] += inf * inf;
         red[2] += in.c * in.ux;

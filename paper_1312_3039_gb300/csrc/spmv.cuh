@@ -26,6 +26,9 @@
 // epilogue's finisher.
 #pragma once
 
+#include <type_traits>
+#include <utility>
+
 #include <stdint.h>
 
 #include <algorithm>
@@ -80,6 +83,13 @@ struct Csr {
     int32_t ntiles;
     int32_t grid() const { return reg.cta0[reg.n]; }
 };
+
+// Epilogues may carry an elementwise task unrelated to the product's rows
+// (side(cta, nctas)); the kernel runs it in every CTA after its rows.
+template <typename E, typename = void>
+struct HasSide : std::false_type {};
+template <typename E>
+struct HasSide<E, std::void_t<decltype(std::declval<E &>().side(0, 0))>> : std::true_type {};
 
 template <typename Acc, typename TA, typename TX>
 __device__ __forceinline__ Acc fmul(TA a, TX x) {
@@ -258,6 +268,8 @@ __global__ void __launch_bounds__(kBlock) spmv_kernel(Csr<TA> A, const TX *__res
             }
         }
     }
+    // an epilogue's elementwise side task (if it has one), spread over the CTAs
+    if constexpr (HasSide<Epi>::value) epi.side(b, gridDim.x);
     double redd[NV], tot[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) redd[i] = static_cast<double>(red[i]);

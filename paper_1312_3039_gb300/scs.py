@@ -48,7 +48,7 @@ class Settings(C.Structure):
                 ("normalize", C.c_int32), ("scale_passes", C.c_int32), ("block_scale", C.c_int32),
                 ("precision", C.c_int32),
                 ("use_graph", C.c_int32), ("verbose", C.c_int32), ("device", C.c_int32),
-                ("cuda_stream", C.c_void_p)]
+                ("cuda_stream", C.c_void_p), ("linsys", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -87,6 +87,8 @@ def lib():
         L.scs_reset.restype = I32
         L.scs_iterate.argtypes = [P, I32, I32]
         L.scs_iterate.restype = I32
+        L.scs_update_bc.argtypes = [P, D, D]
+        L.scs_update_bc.restype = I32
         L.scs_iterate_checked.argtypes = [P, I32, C.POINTER(I32)]
         L.scs_iterate_checked.restype = I32
         L.scs_iterate_profiled.argtypes = [P, I32]
@@ -285,6 +287,21 @@ class Solver:
         st = lib().scs_solve(self._w, _dptr(x), _dptr(y), _dptr(s), C.byref(info))
         self._check(st)
         return st, x, y, s, info.as_dict()
+
+    def update_bc(self, b, c):
+        """scs_update_bc: new b, c with the same A (Sec. 4.2)."""
+        self._b = np.ascontiguousarray(b, dtype=np.float64)
+        self._c = np.ascontiguousarray(c, dtype=np.float64)
+        return self._check(lib().scs_update_bc(self._w, _dptr(self._b), _dptr(self._c)))
+
+    def solve_to(self, x_ptr, y_ptr, s_ptr):
+        """scs_solve writing x, y, s to the given addresses (host or device,
+        ints; 0 skips one); returns (status, info_dict)."""
+        info = Info()
+        ptr = lambda a: C.cast(C.c_void_p(a), C.POINTER(C.c_double)) if a else None
+        st = lib().scs_solve(self._w, ptr(x_ptr), ptr(y_ptr), ptr(s_ptr), C.byref(info))
+        self._check(st)
+        return st, info.as_dict()
 
     def warm_start(self, x=None, y=None, s=None):
         x = None if x is None else np.ascontiguousarray(x, dtype=np.float64)

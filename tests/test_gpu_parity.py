@@ -320,3 +320,43 @@ def test_tiny_and_ragged(scs):
                                       (257, synth.Cone(z=13, l=300, q=(33,), ep=5))]):
         P = synth.random_cone(20 + seed, n=n, cone=cone, density=0.5 if n < 10 else 0.05)
         trajectory_parity(scs, P, iters=20)
+
+
+@pytest.mark.parametrize("linsys", [0, 1])
+def test_update_bc_equals_a_fresh_solver(scs, linsys):
+    """Sec. 4.2 repeated solves: new b, c on the same A (scs_update_bc) give
+    the FP64 solve a fresh scs_init on the new data gives (same iterations,
+    same objective); the cached scaling D, E and, with the direct step, the
+    cached inverse are reused."""
+    P1 = synth.lp(3)
+    P2 = synth.from_pair(P1.A, P1.cone, np.random.default_rng(77))
+    with scs.Solver(P1.A, P1.b, P1.c, P1.cone, precision=0, linsys=linsys) as g:
+        st1, *_r, info1 = g.solve()
+        assert st1 == scs.SOLVED
+        D1, E1, _s1, _r1 = g.scaling()
+        g.update_bc(P2.b, P2.c)
+        st2, x2, y2, s2, info2 = g.solve()
+        D2, E2, sg2, rh2 = g.scaling()
+    st3, x3, y3, s3, info3 = scs.solve(P2.A, P2.b, P2.c, P2.cone, precision=0, linsys=linsys)
+    assert st2 == st3 == scs.SOLVED
+    np.testing.assert_array_equal(D1, D2)
+    np.testing.assert_array_equal(E1, E2)
+    assert info2["iters"] == info3["iters"], (info2["iters"], info3["iters"])
+    assert rel(info2["pobj"], info3["pobj"]) <= 1e-9, (info2["pobj"], info3["pobj"])
+    check_solution(P2, x2, y2, s2)
+
+
+def test_solve_writes_device_outputs(scs):
+    """scs_solve accepts device pointers for x, y, s (unified addressing)."""
+    import torch
+    P = synth.lp(2)
+    with scs.Solver(P.A, P.b, P.c, P.cone, precision=0) as g:
+        st, x, y, s, info = g.solve()
+        dx = torch.full((P.n,), float("nan"), dtype=torch.float64, device="cuda")
+        dy = torch.full((P.m,), float("nan"), dtype=torch.float64, device="cuda")
+        ds = torch.full((P.m,), float("nan"), dtype=torch.float64, device="cuda")
+        st2, info2 = g.solve_to(dx.data_ptr(), dy.data_ptr(), ds.data_ptr())
+    assert st == st2 == scs.SOLVED and info["iters"] == info2["iters"]
+    np.testing.assert_array_equal(dx.cpu().numpy(), x)
+    np.testing.assert_array_equal(dy.cpu().numpy(), y)
+    np.testing.assert_array_equal(ds.cpu().numpy(), s)
