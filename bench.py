@@ -207,7 +207,8 @@ def spmv_bytes(P, it, cg, elt=4):
     mat_at = (elt + 4) * nnz + 4 * (n + 1)
     k3 = mat_a + elt * n + elt * m                                # p gathered; q written
     k2 = mat_at + elt * m + (8 + 8 + elt + elt) * n + 2 * elt * n  # y_acc gathered; u_x, c, z, diag read; r, p written
-    k4 = mat_at + elt * m + 4 * elt * n + 2 * elt * n             # q gathered; p, z, r, diag read; z, r written
+    k4 = (mat_at + elt * m + 4 * elt * n + 2 * elt * n            # q gathered; p, z, r, diag read; z, r written
+          + 5 * elt * m)                                          # side task: q, y_acc, az read; y_acc, az written
     # kind 0 counts the CG products q = A p only (the profiled pass does not
     # time K1, whose product runs on one iteration in 20)
     return {0: cg * k3, 1: it * k2 + cg * k4, "per_launch": {"A_cg": k3, "At_cg": k4}}
@@ -321,16 +322,36 @@ def oracle_err(seed, orc, common):
     return res
 
 
+def spmv_device_digest():
+    """Digest of the device code behind the SpMV traffic record: the SpMV
+    kernels (csrc/spmv.cuh up to its host-side layout builder), the CG
+    epilogues of the two measured launches (EpiACG, EpiAtCG in
+    csrc/kernels.cuh) and csrc/common.cuh's device helpers.  Host code (the
+    layout builder, the engine) is left out, so host-only changes keep it."""
+    import hashlib
+    import re
+    src = os.path.join(ROOT, "paper_1312_3039_gb300", "csrc")
+    with open(os.path.join(src, "spmv.cuh")) as f:
+        spmv = f.read()
+    cut = spmv.find("// Stored layout of one CSR matrix")
+    parts = [spmv[:cut if cut >= 0 else len(spmv)]]
+    with open(os.path.join(src, "kernels.cuh")) as f:
+        ker = f.read()
+    for name in ("EpiACG", "EpiAtCG"):
+        m = re.search(r"struct %s \{.*?\n\};" % name, ker, re.S)
+        parts.append(m.group(0) if m else "")
+    with open(os.path.join(src, "common.cuh")) as f:
+        parts.append(f.read())
+    h = hashlib.sha256()
+    for t in parts:
+        h.update(t.encode())
+    return h.hexdigest()[:16]
+
+
 def traffic_record(kind):
     """DRAM bytes per launch of SpMV kind 0 (A) / 1 (A^T) from the committed
-    ncu summary, if the kernel sources are unchanged since that capture."""
-    import hashlib
-    src = os.path.join(ROOT, "paper_1312_3039_gb300", "csrc")
-    h = hashlib.sha256()
-    for f in ("spmv.cuh", "kernels.cuh", "common.cuh"):
-        with open(os.path.join(src, f), "rb") as fh:
-            h.update(fh.read())
-    digest = h.hexdigest()[:16]
+    ncu summary, if the kernels' device code is unchanged since that capture."""
+    digest = spmv_device_digest()
     path = os.path.join(ROOT, "profiles", "spmv_traffic.txt")
     try:
         with open(path) as f:
