@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--solve-seconds", type=float, default=90.0, help="time limit of the time-to-1e-4 leg")
     ap.add_argument("--solve-iters", type=int, default=100000, help="iteration limit of the time-to-1e-4 leg")
+    ap.add_argument("--linsys", type=int, default=0, choices=[0, 1],
+                    help="subspace step: 0 indirect (PCG), 1 direct (cached dense (I + A^T A)^-1, n <= 8192)")
     return ap.parse_args()
 
 
@@ -458,7 +460,7 @@ def run_gb300(args):
     # the small LP runs in FP64 throughout (its parity configuration); the
     # other programs in the mixed-precision engine
     prec = 0 if args.workload == "lp" else 1
-    common = dict(precision=prec, device=local, cuda_stream=stream.cuda_stream)
+    common = dict(precision=prec, device=local, cuda_stream=stream.cuda_stream, linsys=args.linsys)
 
     def barrier():
         if world > 1:
@@ -509,7 +511,7 @@ def run_gb300(args):
     torch.cuda.nvtx.range_push("profiled")
     S.iterate_profiled(5)
     torch.cuda.nvtx.range_pop()
-    prof = {k: S.kernel_time(k) for k in (0, 1, 2, 3)}
+    prof = {k: S.kernel_time(k) for k in (0, 1, 2, 3, 4)}
     it_p, cg_p = S.counters()
     # counters include the profiled iterations: take CG steps of those 5 from
     # the launch counts (kind 0 = the CG launches of q = A p)
@@ -527,7 +529,8 @@ def run_gb300(args):
                 "avg_launch_us": 1e3 * prof[kind][0] / prof[kind][1],
                 "other_kernel_avg_us": 1e3 * prof[1 - kind][0] / max(prof[1 - kind][1], 1),
                 "projection_avg_us": 1e3 * prof[2][0] / max(prof[2][1], 1),
-                "psd_projection_avg_us": 1e3 * prof[3][0] / prof[3][1] if prof[3][1] else None}
+                "psd_projection_avg_us": 1e3 * prof[3][0] / prof[3][1] if prof[3][1] else None,
+                "direct_step_avg_us": 1e3 * prof[4][0] / prof[4][1] if prof[4][1] else None}
 
     psd = None
     if has_psd and prof[3][1]:
@@ -634,6 +637,7 @@ def run_gb300(args):
                               "inputs fit in L2 (a parity-size program: no flush, not a headline line)"),
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "step": "one ADMM iteration with the solve's Sec. 3.5 tests every 20 iterations",
+                       "linsys": "direct (cached dense inverse)" if args.linsys else "indirect (PCG)",
                        "cg_steps_per_iter": cg_steps / max(it1 - it0, 1)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "time_to_1e4": solve,
