@@ -429,10 +429,15 @@ int32_t scs_bf16_gemm_async(const void *A, int32_t lda, const void *B, int32_t l
  * form), for tests and tuning: C (M x N) = alpha A (M x K) B (K x N) +
  * beta C, all column-major device arrays with leading dimensions lda >= M,
  * ldb >= K, ldc >= M; precision 0: FP64, 1: FP32 (alpha, beta rounded to
- * FP32).  beta == 0 does not read C.  Plain CUDA-core fused multiply-adds in
- * k order, no reduced-precision arithmetic.  Enqueued on `stream` (no
- * allocation, no synchronisation); SCS_INVALID_INPUT for bad sizes or
- * pointers, SCS_DEVICE_ERROR if the launch fails. */
+ * FP32), both plain CUDA-core fused multiply-adds in k order, enqueued on
+ * `stream` (no allocation, no synchronisation); precision 2: FP32 operands
+ * through the tensor cores, each split three ways into BF16 (x = x1 + x2 +
+ * x3) and the six cross products above 2^-24 |a||b| accumulated in FP32 by
+ * two tcgen05 products (a1 b1, then the five smaller ones added to it; the
+ * FP32 family solver's path; this call allocates its scratch and
+ * synchronises).  beta == 0 does not read C.
+ * SCS_INVALID_INPUT for bad sizes or pointers, SCS_DEVICE_ERROR if the
+ * launch fails. */
 int32_t scs_dense_gemm(int32_t precision, int32_t M, int32_t N, int32_t K, double alpha, const void *A, int64_t lda,
                        const void *B, int64_t ldb, double beta, void *C, int64_t ldc, void *stream);
 

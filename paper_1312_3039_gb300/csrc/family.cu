@@ -37,6 +37,7 @@
 #include "dense.cuh"
 #include "engine_base.h"
 #include "kernels.cuh"
+#include "tc_split.h"
 
 namespace scs {
 namespace family {
@@ -604,6 +605,20 @@ class FamilyEngine : public FamilyBase {
         cast_kernel<T><<<grid((int64_t)m * n), kBlock, 0, stream_>>>(A64, Ah_, (int64_t)m * n);
         cast_kernel<T><<<grid((int64_t)m * n), kBlock, 0, stream_>>>(At64, Aht_, (int64_t)m * n);
         cast_kernel<T><<<grid((int64_t)n * n), kBlock, 0, stream_>>>(G, Minv_, (int64_t)n * n);
+        if constexpr (std::is_same<T, float>::value) {
+            // FP32 family: the three fixed matrices split once for the tensor-core products
+            Kpn_ = (n + 63) / 64 * 64;
+            Kpm_ = (m + 63) / 64 * 64;
+            S_At_ = dalloc<__nv_bfloat16>((size_t)n * 3 * Kpm_);   // A^T x: rows n, K = m (A^ column-major)
+            S_A_ = dalloc<__nv_bfloat16>((size_t)m * 3 * Kpn_);    // A^ x: rows m, K = n (A^T column-major)
+            S_M_ = dalloc<__nv_bfloat16>((size_t)n * 3 * Kpn_);    // (I + A^T A)^-1, symmetric
+            mlp::split3_bf16(Ah_, n, m, m, 0, Kpm_, S_At_, stream_);
+            mlp::split3_bf16(Aht_, m, n, n, 0, Kpn_, S_A_, stream_);
+            mlp::split3_bf16(Minv_, n, n, n, 0, Kpn_, S_M_, stream_);
+            S_mem_ = dalloc<__nv_bfloat16>((size_t)B_ * 3 * std::max(Kpn_, Kpm_));
+            tc_err_ = dalloc<int>(1);
+            SCS_CUDA(cudaMemsetAsync(tc_err_, 0, sizeof(int), stream_));
+        }
         // ---- member arrays
         const size_t nx = (size_t)n * B_, ny = (size_t)m * B_;
         F_.n = n;
@@ -681,9 +696,9 @@ class FamilyEngine : public FamilyBase {
         // p = M^-1 h, h = (c^, b^):  p_x = Minv (c^ - A^T b^),  p_y = b^ + A^ p_x
         SCS_CUDA(cudaMemcpyAsync(F_.rx, F_.ch, sizeof(T) * nx, cudaMemcpyDeviceToDevice, stream_));
         SCS_CUDA(cudaMemcpyAsync(F_.py, F_.bh, sizeof(T) * ny, cudaMemcpyDeviceToDevice, stream_));
-        SCS_CUDA(dense::gemm_nn<T>(stream_, n_, B_, m_, T(-1), Aht_, n_, F_.bh, m_, T(1), F_.rx, n_));
-        SCS_CUDA(dense::gemm_nn<T>(stream_, n_, B_, n_, T(1), Minv_, n_, F_.rx, n_, T(0), F_.px, n_));
-        SCS_CUDA(dense::gemm_nn<T>(stream_, m_, B_, n_, T(1), Ah_, m_, F_.px, n_, T(1), F_.py, m_));
+        prod_At(B_, F_.bh, F_.rx, T(-1), T(1));
+        prod_M(B_, F_.rx, F_.px);
+        prod_A(B_, F_.px, F_.py, T(1), T(1));
         hp1_kernel<T><<<B_, kFamThreads, 0, stream_>>>(F_);
         SCS_CUDA(cudaGetLastError());
         SCS_CUDA(cudaStreamSynchronize(stream_));
@@ -725,14 +740,47 @@ class FamilyEngine : public FamilyBase {
             }
     }
 
+    // The member products (Sec. 4.1 direct step in dense form) over the first
+    // `cols` member columns, all column-major:
+    //   prod_At: C (n x cols) = alpha A^T X (m x cols) + beta C
+    //   prod_M:  C (n x cols) = (I + A^T A)^-1 X (n x cols)
+    //   prod_A:  C (m x cols) = alpha A^ X (n x cols) + beta C
+    // FP32: three-way BF16 split of X, then one tcgen05 product against the
+    // matrix's split (FP32-accurate); FP64: the CUDA-core GEMM.
+    void prod_At(int cols, const T *X, T *C, T alpha, T beta) {
+        if constexpr (std::is_same<T, float>::value)
+            prod_tc(S_At_, n_, m_, Kpm_, X, cols, C, alpha, beta);
+        else
+            SCS_CUDA(dense::gemm_nn<T>(stream_, n_, cols, m_, alpha, Aht_, n_, X, m_, beta, C, n_));
+    }
+    void prod_M(int cols, const T *X, T *C) {
+        if constexpr (std::is_same<T, float>::value)
+            prod_tc(S_M_, n_, n_, Kpn_, X, cols, C, T(1), T(0));
+        else
+            SCS_CUDA(dense::gemm_nn<T>(stream_, n_, cols, n_, T(1), Minv_, n_, X, n_, T(0), C, n_));
+    }
+    void prod_A(int cols, const T *X, T *C, T alpha, T beta) {
+        if constexpr (std::is_same<T, float>::value)
+            prod_tc(S_A_, m_, n_, Kpn_, X, cols, C, alpha, beta);
+        else
+            SCS_CUDA(dense::gemm_nn<T>(stream_, m_, cols, n_, alpha, Ah_, m_, X, n_, beta, C, m_));
+    }
+    void prod_tc(const __nv_bfloat16 *B3, int rows, int K, int Kp, const T *X, int cols, T *C, T alpha, T beta) {
+        if (cols <= 0) return;
+        const float *Xf = reinterpret_cast<const float *>(X);
+        mlp::split3_bf16(Xf, cols, K, K, 0, Kp, S_mem_, stream_);
+        mlp::gemm_fp32x3(S_mem_, cols, B3, rows, Kp, reinterpret_cast<float *>(C), rows, static_cast<float>(alpha),
+                         static_cast<float>(beta), tc_err_, stream_);
+    }
+
     // one iteration of the first A columns (the active members)
     void launch_iteration(int A) {
         Dev<T> F = F_;
         F.B = A;
         rhs_kernel<T><<<grid((int64_t)(n_ + m_) * A), kFamThreads, 0, stream_>>>(F);
-        SCS_CUDA(dense::gemm_nn<T>(stream_, n_, A, m_, T(-1), Aht_, n_, F_.ry, m_, T(1), F_.rx, n_));
-        SCS_CUDA(dense::gemm_nn<T>(stream_, n_, A, n_, T(1), Minv_, n_, F_.rx, n_, T(0), F_.zx, n_));
-        SCS_CUDA(dense::gemm_nn<T>(stream_, m_, A, n_, T(1), Ah_, m_, F_.zx, n_, T(1), F_.ry, m_));
+        prod_At(A, F_.ry, F_.rx, T(-1), T(1));
+        prod_M(A, F_.rx, F_.zx);
+        prod_A(A, F_.zx, F_.ry, T(1), T(1));
         update_kernel<T><<<A, kFamThreads, 0, stream_>>>(F);
     }
     void launch_iteration() { launch_iteration(B_); }
@@ -740,8 +788,8 @@ class FamilyEngine : public FamilyBase {
     void launch_check(int A, int k, int final_pass) {
         Dev<T> F = F_;
         F.B = A;
-        SCS_CUDA(dense::gemm_nn<T>(stream_, m_, A, n_, T(1), Ah_, m_, F_.ux, n_, T(0), F_.ax, m_));
-        SCS_CUDA(dense::gemm_nn<T>(stream_, n_, A, m_, T(1), Aht_, n_, F_.uy, m_, T(0), F_.aty, n_));
+        prod_A(A, F_.ux, F_.ax, T(1), T(0));
+        prod_At(A, F_.uy, F_.aty, T(1), T(0));
         check_kernel<T><<<A, kFamThreads, 0, stream_>>>(F, k, final_pass);
     }
 
@@ -879,6 +927,7 @@ class FamilyEngine : public FamilyBase {
             }
         }
         SCS_CUDA(cudaStreamSynchronize(stream_));
+        check_tc();
         return 0;
     }
 
@@ -887,7 +936,16 @@ class FamilyEngine : public FamilyBase {
         for (int i = 0; i < iters; ++i) launch_iteration();
         SCS_CUDA(cudaGetLastError());
         SCS_CUDA(cudaStreamSynchronize(stream_));
+        check_tc();
         return 0;
+    }
+
+    // a bounded wait of a tensor-core product timed out: its output is not written
+    void check_tc() {
+        if (!tc_err_) return;
+        int e = 0;
+        SCS_CUDA(cudaMemcpy(&e, tc_err_, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e) throw CudaError("a tensor-core product's bounded wait timed out", SCS_DEVICE_ERROR);
     }
 
     int get_iterates(int idx, double *u, double *v) override {
@@ -944,6 +1002,11 @@ class FamilyEngine : public FamilyBase {
     cudaStream_t stream_ = nullptr;
     std::vector<void *> allocs_;
     T *Ah_ = nullptr, *Aht_ = nullptr, *Minv_ = nullptr;   // A^ (m x n), A^T (n x m), (I + A^T A)^-1
+    // FP32 family: BF16 three-way splits of A^T, A^, (I + A^T A)^-1 and of the
+    // member operand of the product in progress; the products' error flag
+    __nv_bfloat16 *S_At_ = nullptr, *S_A_ = nullptr, *S_M_ = nullptr, *S_mem_ = nullptr;
+    int *tc_err_ = nullptr;
+    int Kpn_ = 0, Kpm_ = 0;
     double *bdev_ = nullptr, *cdev_ = nullptr;
     int32_t *pairs_ = nullptr;
     std::vector<int32_t> swap_log_;
@@ -1072,12 +1135,45 @@ void scs_family_finish(scs_family *w) {
 int32_t scs_dense_gemm(int32_t precision, int32_t M, int32_t N, int32_t K, double alpha, const void *A, int64_t lda,
                        const void *B, int64_t ldb, double beta, void *C, int64_t ldc, void *stream) {
     using namespace scs;
-    if (M < 0 || N < 0 || K < 0 || (precision != 0 && precision != 1) || lda < std::max(1, M) ||
+    if (M < 0 || N < 0 || K < 0 || precision < 0 || precision > 2 || lda < std::max(1, M) ||
         ldb < std::max(1, K) || ldc < std::max(1, M) || (M && N && (!C || (K && (!A || !B))))) {
         set_last_error("scs_dense_gemm: bad sizes, leading dimensions or pointers");
         return SCS_INVALID_INPUT;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision == 2) {
+        // FP32 through the three-way BF16 split on the tensor cores: C^T
+        // (N x M) = B^T A^T, B's columns and A's rows K-contiguous after the split
+        if (!M || !N) return 0;
+        const int Kp = std::max(64, (K + 63) / 64 * 64);
+        __nv_bfloat16 *a3 = nullptr, *b3 = nullptr;
+        int *err = nullptr;
+        int rc = 0;
+        if (cudaMalloc(&a3, sizeof(__nv_bfloat16) * 3 * (size_t)Kp * N) != cudaSuccess ||
+            cudaMalloc(&b3, sizeof(__nv_bfloat16) * 3 * (size_t)Kp * M) != cudaSuccess ||
+            cudaMalloc(&err, sizeof(int)) != cudaSuccess || cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) {
+            rc = SCS_DEVICE_ERROR;
+        } else {
+            try {
+                mlp::split3_bf16(static_cast<const float *>(B), N, K, ldb, 0, Kp, a3, s);
+                mlp::split3_bf16(static_cast<const float *>(A), M, K, lda, 1, Kp, b3, s);
+                mlp::gemm_fp32x3(a3, N, b3, M, Kp, static_cast<float *>(C), ldc, static_cast<float>(alpha),
+                                 static_cast<float>(beta), err, s);
+                int h = 0;
+                if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                    cudaStreamSynchronize(s) != cudaSuccess || h)
+                    rc = SCS_DEVICE_ERROR;
+            } catch (const CudaError &ex) {
+                set_last_error(std::string("scs_dense_gemm: ") + ex.what());
+                rc = ex.code;
+            }
+        }
+        cudaFree(a3);
+        cudaFree(b3);
+        cudaFree(err);
+        if (rc == SCS_DEVICE_ERROR) set_last_error("scs_dense_gemm: the tensor-core product failed");
+        return rc;
+    }
     const cudaError_t e =
         precision == 0 ? dense::gemm_nn<double>(s, M, N, K, alpha, static_cast<const double *>(A), lda,
                                                 static_cast<const double *>(B), ldb, beta, static_cast<double *>(C),

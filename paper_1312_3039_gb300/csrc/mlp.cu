@@ -250,11 +250,19 @@ __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// K blocks of a product whose operands are stored in chunks: K block kt lies
+// in chunk c = kt / kchunk of the product and reads chunk a[c] of A and b[c]
+// of B (each chunk kchunk K blocks wide).  kchunk = 0: one plain K range.
+struct TcKMap {
+    int kchunk;
+    signed char a[8], b[8];
+};
+
 // C = A B^T, A M x K and B N x K (K-contiguous, described by tmA and tmB)
 template <typename Epi, int BNt>
 __global__ void __launch_bounds__(kTcThreads, 1) gemm_nt_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                    const __grid_constant__ CUtensorMap tmB, int M,
-                                                                   int N, int K, Epi epi, int *err) {
+                                                                   int N, int K, Epi epi, int *err, TcKMap km) {
     constexpr int S = tc_stages<BNt>();
     constexpr int kStageB = tc_stage_b<BNt>();
     constexpr uint32_t kStageBytes = kTcStageA + kStageB;
@@ -310,9 +318,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_nt_tc_kernel(const __grid_
                     ok = false;
                     break;
                 }
+                int xa = kt * TBK, xb = kt * TBK;
+                if (km.kchunk) {
+                    const int c = kt / km.kchunk, j = kt % km.kchunk;
+                    xa = (km.a[c] * km.kchunk + j) * TBK;
+                    xb = (km.b[c] * km.kchunk + j) * TBK;
+                }
                 mbar_expect(bar(&full[s]), kStageBytes);
-                tma_load(sA(s), &tmA, kt * TBK, tm * TBM, bar(&full[s]));
-                tma_load(sB(s), &tmB, kt * TBK, tn * BNt, bar(&full[s]));
+                tma_load(sA(s), &tmA, xa, tm * TBM, bar(&full[s]));
+                tma_load(sB(s), &tmB, xb, tn * BNt, bar(&full[s]));
             }
         }
         // the copies of the last uses of each stage have landed (bounded)
@@ -532,9 +546,12 @@ inline CUtensorMap tc_map(const __nv_bfloat16 *p, int rows, int cols, int ld, in
     return m;
 }
 
+// M, N: the tiles' extent (multiples of 128 and BNt); rows_a, rows_b, cols_a,
+// cols_b: the operands' stored extent (rows beyond it read as zeros)
 template <typename Epi, int BNt>
 void launch_tc(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, int M, int N, int K, Epi epi, int *err,
-               cudaStream_t stream) {
+               cudaStream_t stream, TcKMap km = TcKMap{}, int rows_a = -1, int rows_b = -1, int cols_a = -1,
+               int cols_b = -1) {
     // per device: the kernel's shared-memory attribute set once, its SM count
     constexpr int kDevs = 64;
     static std::mutex mu;
@@ -552,9 +569,11 @@ void launch_tc(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb,
         }
         nsm = sms[dev];
     }
-    const CUtensorMap ma = tc_map(A, M, K, lda, TBM), mb = tc_map(B, N, K, ldb, BNt);
+    const CUtensorMap ma = tc_map(A, rows_a < 0 ? M : rows_a, cols_a < 0 ? K : cols_a, lda, TBM),
+                      mb = tc_map(B, rows_b < 0 ? N : rows_b, cols_b < 0 ? K : cols_b, ldb, BNt);
     const int tiles = (M / TBM) * (N / BNt);
-    gemm_nt_tc_kernel<Epi, BNt><<<std::min(tiles, nsm), kTcThreads, tc_smem<BNt>(), stream>>>(ma, mb, M, N, K, epi, err);
+    gemm_nt_tc_kernel<Epi, BNt><<<std::min(tiles, nsm), kTcThreads, tc_smem<BNt>(), stream>>>(ma, mb, M, N, K, epi, err,
+                                                                                              km);
 }
 
 // C = A B^T through either kernel; the shape must meet the kernel's tiling
@@ -577,6 +596,95 @@ void launch_gemm(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ld
         gemm_nt_kernel<Epi><<<dim3(N / BN, M / BM), kGemmThreads, 0, stream>>>(A, lda, B, ldb, K, epi);
     }
     SCS_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// FP32-accurate products on the tensor cores (three-way BF16 split).
+//   x = x1 + x2 + x3,  x1 = bf16(x), x2 = bf16(x - x1), x3 = bf16(x - x1 - x2)
+// (each difference is exact in FP32, so x - x1 - x2 - x3 is below 2^-24 |x|).
+// A sum of products a.b is taken as the six BF16 x BF16 products
+//   a1 b1 + a1 b2 + a2 b1 + a1 b3 + a2 b2 + a3 b1
+// (the three dropped ones are below 2^-24 |a||b|), in two tcgen05 launches:
+// a1 b1 first, then the five smaller products added to it.  The tensor
+// cores' FP32 accumulation aligns a group of products to its largest one, so
+// in a single accumulator the 2^-16-sized products would lose their low bits
+// next to a1 b1 (measured: about 2^-15 relative); summed on their own, their
+// accumulation error is 2^-8 smaller.  The operands are stored as three
+// chunks of Kp columns each (x1 | x2 | x3, zero-padded from K to Kp); the
+// kernel's chunk map reads chunk 0 of A against chunk 0 of B (K' = Kp), then
+// chunks (0, 1, 0, 1, 2) of A against (1, 0, 2, 1, 0) of B (K' = 5 Kp).
+// ---------------------------------------------------------------------------
+// dst (rows x 3 Kp, row-major) from src rows x K: element (r, k) at
+// src[r ld + k], or at src[k ld + r] when trans (a column-major source read
+// along its rows)
+static __global__ void split3_kernel(const float *__restrict__ src, int rows, int K, int64_t ld, int trans, int Kp,
+                                     __nv_bfloat16 *__restrict__ dst) {
+    const int64_t total = (int64_t)rows * Kp;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / Kp;
+        const int k = static_cast<int>(e % Kp);
+        const float x = k < K ? (trans ? src[(int64_t)k * ld + r] : src[r * ld + k]) : 0.f;
+        const __nv_bfloat16 h1 = __float2bfloat16_rn(x);
+        const float r1 = x - __bfloat162float(h1);
+        const __nv_bfloat16 h2 = __float2bfloat16_rn(r1);
+        const __nv_bfloat16 h3 = __float2bfloat16_rn(r1 - __bfloat162float(h2));
+        __nv_bfloat16 *row = dst + r * 3 * (int64_t)Kp;
+        row[k] = h1;
+        row[Kp + k] = h2;
+        row[2 * Kp + k] = h3;
+    }
+}
+
+// C'(r, c) = alpha acc + beta C'(r, c) stored at C[r ldc + c], r < rows,
+// c < cols (beta == 0: C is not read)
+struct EpiScaledT {
+    float *C;
+    int64_t ldc;
+    int rows, cols;
+    float alpha, beta;
+    __device__ void put(int r, int c, float v) const {
+        float *p = C + (int64_t)r * ldc + c;
+        *p = beta == 0.f ? alpha * v : alpha * v + beta * *p;
+    }
+    __device__ void operator()(int r, int c, float v0, float v1) const {
+        if (r >= rows) return;
+        if (c < cols) put(r, c, v0);
+        if (c + 1 < cols) put(r, c + 1, v1);
+    }
+};
+
+void split3_bf16(const float *src, int rows, int K, int64_t ld, int trans, int Kp, __nv_bfloat16 *dst,
+                 cudaStream_t stream) {
+    const int64_t total = (int64_t)rows * Kp;
+    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 4096)));
+    split3_kernel<<<grid, 256, 0, stream>>>(src, rows, K, ld, trans, Kp, dst);
+    SCS_CUDA(cudaGetLastError());
+}
+
+void gemm_fp32x3(const __nv_bfloat16 *A3, int rows_a, const __nv_bfloat16 *B3, int rows_b, int Kp, float *C,
+                 int64_t ldc, float alpha, float beta, int *err, cudaStream_t stream) {
+    if (rows_a <= 0 || rows_b <= 0) return;
+    if (Kp <= 0 || Kp % TBK || (reinterpret_cast<uintptr_t>(A3) & 15) || (reinterpret_cast<uintptr_t>(B3) & 15))
+        throw CudaError("split product: Kp must be a positive multiple of 64, operands 16-byte aligned",
+                        SCS_INVALID_INPUT);
+    const TcKMap big{Kp / TBK, {0, 0, 0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0, 0, 0}};
+    const TcKMap small{Kp / TBK, {0, 1, 0, 1, 2, 0, 0, 0}, {1, 0, 2, 1, 0, 0, 0, 0}};
+    const int M = round_up(rows_a, TBM), ld = 3 * Kp;
+    for (int pass = 0; pass < 2; ++pass) {
+        const TcKMap &km = pass == 0 ? big : small;
+        const int K = pass == 0 ? Kp : 5 * Kp;
+        const EpiScaledT epi{C, ldc, rows_a, rows_b, alpha, pass == 0 ? beta : 1.f};
+        if (round_up(rows_b, 256) == round_up(rows_b, 128))
+            launch_tc<EpiScaledT, 256>(A3, ld, B3, ld, M, round_up(rows_b, 256), K, epi, err, stream, km, rows_a,
+                                       rows_b, ld, ld);
+        else if (rows_b > 64)
+            launch_tc<EpiScaledT, 128>(A3, ld, B3, ld, M, round_up(rows_b, 128), K, epi, err, stream, km, rows_a,
+                                       rows_b, ld, ld);
+        else
+            launch_tc<EpiScaledT, 64>(A3, ld, B3, ld, M, round_up(rows_b, 64), K, epi, err, stream, km, rows_a,
+                                      rows_b, ld, ld);
+        SCS_CUDA(cudaGetLastError());
+    }
 }
 
 class Net {
