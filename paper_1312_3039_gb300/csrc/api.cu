@@ -7,6 +7,8 @@
 
 #include "../../include/scs_gpu.h"
 #include <algorithm>
+#include <new>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -30,8 +32,155 @@ void set_error(const std::string &s) { g_last_error = s; }
 
 void scs::set_last_error(const std::string &s) { set_error(s); }
 
-int scs::validate_and_build(const scs_csc *A, const double *b, const double *c, const scs_cone *k,
-                            scs::HostProblem &P) {
+namespace {
+
+// Threads for a host pass over `work` stored entries: one below 2^20, else
+// up to 16 (the passes are bound by memory bandwidth well before that).
+int host_threads(int64_t work) {
+    if (work < (int64_t(1) << 20)) return 1;
+    const unsigned hc = std::thread::hardware_concurrency();
+    return static_cast<int>(std::min<unsigned>(16, hc > 0 ? hc : 1));
+}
+
+// f(0) .. f(T - 1): part 0 on this thread, the others on new threads; a part
+// whose thread cannot be started runs here after part 0.  f must not throw.
+template <typename F>
+void run_parts(int T, F f) {
+    std::vector<std::thread> pool;
+    int started = 1;
+    try {
+        for (; started < T; ++started) pool.emplace_back(f, started);
+    } catch (...) {
+        // no more threads: the remaining parts run here
+    }
+    f(0);
+    for (int t = started; t < T; ++t) f(t);
+    for (auto &th : pool) th.join();
+}
+
+// T + 1 column boundaries splitting the stored entries of a CSC matrix into
+// parts of about equal size.
+std::vector<int32_t> column_cuts(const int64_t *colptr, int32_t n, int T) {
+    std::vector<int32_t> cut(1, 0);
+    for (int t = 1; t < T; ++t) {
+        const int64_t target = colptr[n] * t / T;
+        const int32_t j = static_cast<int32_t>(std::lower_bound(colptr + cut.back(), colptr + n, target) - colptr);
+        cut.push_back(std::max(cut.back(), std::min(j, n)));
+    }
+    cut.push_back(n);
+    return cut;
+}
+
+// Canonical CSC (row indices strictly increasing in every column) from any
+// CSC: each column sorted by row (stable), entries with equal row summed in
+// input order.  Threads over parts of the columns.
+void canonicalize(const scs_csc *A, int T, std::vector<int64_t> &cp, std::vector<int32_t> &ri,
+                  std::vector<double> &vv) {
+    const int32_t n = A->n;
+    const int64_t nnz = A->colptr[n];
+    ri.resize(nnz);
+    vv.resize(nnz);
+    std::vector<int64_t> len(n);
+    const std::vector<int32_t> cut = column_cuts(A->colptr, n, T);
+    std::vector<char> failed(T, 0);
+    run_parts(T, [&](int t) {
+        try {
+            std::vector<int64_t> ord;
+            for (int32_t j = cut[t]; j < cut[t + 1]; ++j) {
+                const int64_t a = A->colptr[j], e = A->colptr[j + 1];
+                ord.resize(e - a);
+                for (int64_t u = a; u < e; ++u) ord[u - a] = u;
+                std::stable_sort(ord.begin(), ord.end(),
+                                 [&](int64_t x, int64_t y) { return A->rowidx[x] < A->rowidx[y]; });
+                int64_t w = a;
+                for (int64_t u : ord) {
+                    if (w > a && ri[w - 1] == A->rowidx[u]) {
+                        vv[w - 1] += A->val[u];
+                    } else {
+                        ri[w] = A->rowidx[u];
+                        vv[w] = A->val[u];
+                        ++w;
+                    }
+                }
+                len[j] = w - a;
+            }
+        } catch (...) {
+            failed[t] = 1;
+        }
+    });
+    for (char f : failed)
+        if (f) throw std::bad_alloc();
+    cp.assign(n + 1, 0);
+    for (int32_t j = 0; j < n; ++j) cp[j + 1] = cp[j] + len[j];
+    // compact in place: column j moves from colptr[j] down to cp[j] <= colptr[j]
+    for (int32_t j = 0; j < n; ++j) {
+        const int64_t a = A->colptr[j];
+        if (cp[j] != a) {
+            std::copy(ri.begin() + a, ri.begin() + a + len[j], ri.begin() + cp[j]);
+            std::copy(vv.begin() + a, vv.begin() + a + len[j], vv.begin() + cp[j]);
+        }
+    }
+    ri.resize(cp[n]);
+    vv.resize(cp[n]);
+}
+
+// CSR (rowptr, col, val) of a canonical CSC matrix with m rows: a counting
+// sort by row.  The rows are split into T parts; each thread visits every
+// column in order and keeps the entries of its own rows, so each CSR row
+// comes out sorted by column and the result does not depend on T.
+void csc_to_csr(const int64_t *colptr, const int32_t *rowidx, const double *val, int32_t m, int32_t n, int T,
+                std::vector<int32_t> &rowptr, std::vector<int32_t> &col, std::vector<double> &out) {
+    const int64_t nnz = colptr[n];
+    rowptr.assign(m + 1, 0);
+    col.resize(nnz);
+    out.resize(nnz);
+    std::vector<int32_t> r0(T + 1);
+    for (int t = 0; t <= T; ++t) r0[t] = static_cast<int32_t>((int64_t)m * t / T);
+    std::vector<int64_t> total(T, 0);
+    // pass 1: row lengths (into rowptr[i + 1])
+    run_parts(T, [&](int t) {
+        const uint32_t lo = static_cast<uint32_t>(r0[t]), span = static_cast<uint32_t>(r0[t + 1] - r0[t]);
+        int32_t *cnt = rowptr.data() + 1;
+        for (int64_t u = 0; u < nnz; ++u) {
+            const uint32_t i = static_cast<uint32_t>(rowidx[u]);
+            if (i - lo < span) cnt[i]++;
+        }
+        int64_t s = 0;
+        for (uint32_t i = lo; i < lo + span; ++i) s += cnt[i];
+        total[t] = s;
+    });
+    // row starts: the parts' offsets, then a running sum inside each part
+    std::vector<int64_t> off(T + 1, 0);
+    for (int t = 0; t < T; ++t) off[t + 1] = off[t] + total[t];
+    run_parts(T, [&](int t) {
+        int64_t s = off[t];
+        for (int32_t i = r0[t]; i < r0[t + 1]; ++i) {
+            s += rowptr[i + 1];
+            rowptr[i + 1] = static_cast<int32_t>(s);
+        }
+    });
+    // pass 2: scatter, columns in order
+    std::vector<std::vector<int32_t>> cursor(T);
+    for (int t = 0; t < T; ++t) cursor[t].assign(rowptr.begin() + r0[t], rowptr.begin() + r0[t + 1]);
+    run_parts(T, [&](int t) {
+        const uint32_t lo = static_cast<uint32_t>(r0[t]), span = static_cast<uint32_t>(r0[t + 1] - r0[t]);
+        std::vector<int32_t> &pos = cursor[t];
+        for (int32_t j = 0; j < n; ++j)
+            for (int64_t u = colptr[j]; u < colptr[j + 1]; ++u) {
+                const uint32_t i = static_cast<uint32_t>(rowidx[u]);
+                if (i - lo < span) {
+                    const int32_t w = pos[i - lo]++;
+                    col[w] = j;
+                    out[w] = val[u];
+                }
+            }
+    });
+}
+
+}  // namespace
+
+static int build_problem(const scs_csc *A, const double *b, const double *c, const scs_cone *k,
+                         scs::HostProblem &P) {
     if (!A || !b || !c || !k) { set_error("null argument"); return SCS_INVALID_INPUT; }
     if (A->m <= 0 || A->n <= 0) { set_error("m and n must be positive"); return SCS_INVALID_INPUT; }
     if (!A->colptr || (!A->rowidx && A->colptr[A->n] > 0) || (!A->val && A->colptr[A->n] > 0)) {
@@ -44,10 +193,24 @@ int scs::validate_and_build(const scs_csc *A, const double *b, const double *c, 
         if (A->colptr[j + 1] < A->colptr[j]) { set_error("colptr must be nondecreasing"); return SCS_INVALID_INPUT; }
     const int64_t nnz_in = A->colptr[n];
     if (nnz_in >= (int64_t)1 << 31) { set_error("nnz must be below 2^31"); return SCS_UNSUPPORTED; }
-    for (int64_t t = 0; t < nnz_in; ++t) {
-        if (A->rowidx[t] < 0 || A->rowidx[t] >= m) { set_error("row index out of range"); return SCS_INVALID_INPUT; }
-        if (!std::isfinite(A->val[t])) { set_error("non-finite entry in A"); return SCS_INVALID_INPUT; }
-    }
+    // entries: row range, finiteness, and whether the rows of every column
+    // are strictly increasing (then the CSC already is the CSR of A^T)
+    const int T = host_threads(nnz_in);
+    const std::vector<int32_t> cut = column_cuts(A->colptr, n, T);
+    std::vector<char> bad_row(T, 0), bad_val(T, 0), unsorted(T, 0);
+    run_parts(T, [&](int t) {
+        for (int32_t j = cut[t]; j < cut[t + 1]; ++j)
+            for (int64_t u = A->colptr[j]; u < A->colptr[j + 1]; ++u) {
+                const int32_t i = A->rowidx[u];
+                if (i < 0 || i >= m) bad_row[t] = 1;
+                if (!std::isfinite(A->val[u])) bad_val[t] = 1;
+                if (u > A->colptr[j] && i <= A->rowidx[u - 1]) unsorted[t] = 1;
+            }
+    });
+    for (int t = 0; t < T; ++t)
+        if (bad_row[t]) { set_error("row index out of range"); return SCS_INVALID_INPUT; }
+    for (int t = 0; t < T; ++t)
+        if (bad_val[t]) { set_error("non-finite entry in A"); return SCS_INVALID_INPUT; }
     for (int32_t i = 0; i < m; ++i)
         if (!std::isfinite(b[i])) { set_error("non-finite entry in b"); return SCS_INVALID_INPUT; }
     for (int32_t j = 0; j < n; ++j)
@@ -75,67 +238,31 @@ int scs::validate_and_build(const scs_csc *A, const double *b, const double *c, 
     }
     if (rows != m) { set_error("cone sizes do not add up to m"); return SCS_INVALID_INPUT; }
 
-    // CSR of A (counting sort by row; columns visited in order keep each row
-    // sorted by column, so duplicates are adjacent and are summed)
+    // CSR of A^T: the canonical CSC of A (A's own arrays when its columns
+    // are canonical); CSR of A: its counting-sort transpose
     P.m = m;
     P.n = n;
-    std::vector<int32_t> cnt(m + 1, 0);
-    for (int64_t t = 0; t < nnz_in; ++t) cnt[A->rowidx[t] + 1]++;
-    std::vector<int32_t> rp(m + 1, 0);
-    for (int32_t i = 0; i < m; ++i) rp[i + 1] = rp[i] + cnt[i + 1];
-    std::vector<int32_t> col(nnz_in), pos(rp.begin(), rp.end() - 1);
-    std::vector<double> val(nnz_in);
-    for (int32_t j = 0; j < n; ++j)
-        for (int64_t t = A->colptr[j]; t < A->colptr[j + 1]; ++t) {
-            const int32_t i = A->rowidx[t];
-            col[pos[i]] = j;
-            val[pos[i]] = A->val[t];
-            pos[i]++;
-        }
-    P.a_rowptr.assign(m + 1, 0);
-    P.a_col.reserve(nnz_in);
-    P.a_val.reserve(nnz_in);
-    for (int32_t i = 0; i < m; ++i) {
-        // within a row, sort by column (entries of one column may come unsorted)
-        std::vector<std::pair<int32_t, double>> row;
-        bool sorted = true;
-        for (int32_t t = rp[i]; t < rp[i + 1]; ++t) {
-            if (t > rp[i] && col[t] < col[t - 1]) sorted = false;
-        }
-        if (!sorted) {
-            for (int32_t t = rp[i]; t < rp[i + 1]; ++t) row.emplace_back(col[t], val[t]);
-            std::sort(row.begin(), row.end(), [](const auto &a, const auto &b) { return a.first < b.first; });
-            for (int32_t t = rp[i]; t < rp[i + 1]; ++t) {
-                col[t] = row[t - rp[i]].first;
-                val[t] = row[t - rp[i]].second;
-            }
-        }
-        for (int32_t t = rp[i]; t < rp[i + 1]; ++t) {
-            if (!P.a_col.empty() && (int32_t)P.a_col.size() > P.a_rowptr[i] && P.a_col.back() == col[t]) {
-                P.a_val.back() += val[t];
-            } else {
-                P.a_col.push_back(col[t]);
-                P.a_val.push_back(val[t]);
-            }
-        }
-        P.a_rowptr[i + 1] = (int32_t)P.a_col.size();
+    const bool canonical = std::none_of(unsorted.begin(), unsorted.end(), [](char f) { return f != 0; });
+    if (canonical) {
+        P.at_rowptr.resize(n + 1);
+        P.at_col.resize(nnz_in);
+        P.at_val.resize(nnz_in);
+        run_parts(T, [&](int t) {
+            const int64_t a = A->colptr[cut[t]], e = A->colptr[cut[t + 1]];
+            std::copy(A->rowidx + a, A->rowidx + e, P.at_col.begin() + a);
+            std::copy(A->val + a, A->val + e, P.at_val.begin() + a);
+            for (int32_t j = cut[t]; j < cut[t + 1]; ++j) P.at_rowptr[j + 1] = static_cast<int32_t>(A->colptr[j + 1]);
+        });
+        csc_to_csr(A->colptr, A->rowidx, A->val, m, n, T, P.a_rowptr, P.a_col, P.a_val);
+    } else {
+        std::vector<int64_t> cp;
+        canonicalize(A, T, cp, P.at_col, P.at_val);
+        P.at_rowptr.resize(n + 1);
+        for (int32_t j = 0; j <= n; ++j) P.at_rowptr[j] = static_cast<int32_t>(cp[j]);
+        csc_to_csr(cp.data(), P.at_col.data(), P.at_val.data(), m, n, host_threads(cp[n]), P.a_rowptr, P.a_col,
+                   P.a_val);
     }
-    P.nnz = (int64_t)P.a_col.size();
-    // CSR of A^T from CSR of A (counting sort by column; rows come in order)
-    std::vector<int32_t> ccnt(n + 1, 0);
-    for (int64_t t = 0; t < P.nnz; ++t) ccnt[P.a_col[t] + 1]++;
-    P.at_rowptr.assign(n + 1, 0);
-    for (int32_t j = 0; j < n; ++j) P.at_rowptr[j + 1] = P.at_rowptr[j] + ccnt[j + 1];
-    P.at_col.resize(P.nnz);
-    P.at_val.resize(P.nnz);
-    std::vector<int32_t> cpos(P.at_rowptr.begin(), P.at_rowptr.end() - 1);
-    for (int32_t i = 0; i < m; ++i)
-        for (int32_t t = P.a_rowptr[i]; t < P.a_rowptr[i + 1]; ++t) {
-            const int32_t j = P.a_col[t];
-            P.at_col[cpos[j]] = i;
-            P.at_val[cpos[j]] = P.a_val[t];
-            cpos[j]++;
-        }
+    P.nnz = static_cast<int64_t>(P.a_col.size());
     P.b.assign(b, b + m);
     P.c.assign(c, c + n);
     P.z = k->z;
@@ -146,6 +273,16 @@ int scs::validate_and_build(const scs_csc *A, const double *b, const double *c, 
     P.q.assign(k->q, k->q + k->nq);
     P.s.assign(k->s, k->s + k->ns);
     return 0;
+}
+
+int scs::validate_and_build(const scs_csc *A, const double *b, const double *c, const scs_cone *k,
+                            scs::HostProblem &P) {
+    try {
+        return build_problem(A, b, c, k, P);
+    } catch (const std::bad_alloc &) {
+        set_error("host allocation failed");
+        return SCS_DEVICE_ERROR;
+    }
 }
 
 namespace {

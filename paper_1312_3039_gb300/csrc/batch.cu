@@ -16,8 +16,8 @@
 // warp shuffle, one shared-memory exchange and one barrier.
 //
 // The host autotuner (BatchEngine::tune) times the team size (64, 128, 256
-// or 512 threads) and the row split on a sample of programs and keeps the
-// fastest.  Setup (equilibration in FP64, Jacobi diagonal, cached
+// or 512 threads) and the row split on a sample of programs that keeps every
+// resident team busy and keeps the fastest.  Setup (equilibration in FP64, Jacobi diagonal, cached
 // p = M^-1 h) is a second persistent launch run once by scs_batch_init; each
 // solve is a CUDA graph of a queue reset and the solve launch.
 //
@@ -1107,13 +1107,19 @@ class BatchEngine : public BatchBase {
     }
 
     // Autotuner: team size x row split, timed over `kTuneIters` iterations of
-    // a sample of programs spread over the size order; keeps the fastest.
+    // a sample of programs spread over the size order (kept largest first, as
+    // the solve's queue is); keeps the fastest.  The sample holds at least
+    // four programs per resident team of every candidate, so each candidate
+    // is timed with all of its teams busy, as in the solve: a sample that
+    // fills only part of the resident teams favours large teams.
     void tune() {
         const auto t0 = std::chrono::steady_clock::now();
         static const int kThreads[] = {64, 128, 256, 512};
         static const int kSplits[] = {4, 16, 64};
         const int kTuneIters = 10;
-        const int ns = std::min(count_, 2 * sms_);
+        int teams = 1;
+        for (int nt : kThreads) teams = std::max(teams, grid_for(nt));
+        const int ns = static_cast<int>(std::min<int64_t>(count_, 4 * static_cast<int64_t>(teams)));
         std::vector<int32_t> sample;
         for (int i = 0; i < ns; ++i) sample.push_back(order_[(int64_t)i * count_ / ns]);
         int32_t *sample_d = upload(sample);
@@ -1125,6 +1131,10 @@ class BatchEngine : public BatchBase {
         SCS_CUDA(cudaEventCreate(&e1));
         float best = INFINITY;
         int best_nt = 256, best_split = 16;
+        set_split(kSplits[0]);     // one untimed launch first (module load, cold caches)
+        upload_meta();
+        reset_state();
+        run(Ds, kThreads[0], 1, 1);
         for (int sp : kSplits) {
             set_split(sp);
             upload_meta();
