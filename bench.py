@@ -219,14 +219,28 @@ def spmv_bytes(P, it, cg, elt=4):
 def psd_flops(orders, sweeps_per_block):
     """Flop model of one PSD launch (every block once), FP32 arithmetic:
     re-orthonormalisation of V and the similarity V^T X V (4 products of
-    order ne: 8 ne^3), the Jacobi sweeps ((ne - 1) rounds of 12 h^2 + 6 n h
-    flops, h = ne / 2: both sides of the lower 2 x 2 blocks and the rows of V)
-    and the reconstruction over half of the eigenvalues (ne^3)."""
+    order ne: 8 ne^3), the Jacobi sweeps and the reconstruction over half of
+    the eigenvalues (ne^3).  Orders up to 48 (ne = n rounded up to 4): a
+    sweep is ne - 1 rounds of 12 h^2 + 6 n h flops (h = ne / 2: both sides of
+    the lower 2 x 2 blocks and the rows of V).  Above (ne = n rounded up to
+    16, nb = ne / 8 blocks): a sweep is nb - 1 block rounds, each with one
+    15-round sweep of every block pair's 16 x 16 subproblem (36 2 x 2 blocks
+    of 24 flops and 16 x 8 Q updates of 6 flops a round) and the panel
+    products X[R, :] <- Q^T X[R, :], X[:, R] <- X[:, R] Q (32 ne^2 flops
+    each over all pairs) and V[:, R] <- V[:, R] Q (32 n ne), counted as the
+    kernel performs them."""
     tot = 0.0
     for n in orders:
-        ne = max(4, (n + 3) // 4 * 4)
-        h = ne // 2
-        tot += 8.0 * ne ** 3 + sweeps_per_block * (ne - 1) * (12.0 * h * h + 6.0 * n * h) + 1.0 * ne ** 3
+        if n <= 48:
+            ne = max(4, (n + 3) // 4 * 4)
+            h = ne // 2
+            sweep = (ne - 1) * (12.0 * h * h + 6.0 * n * h)
+        else:
+            ne = (n + 15) // 16 * 16
+            nb, npairs = ne // 8, ne // 16
+            sub = 15 * (36 * 24.0 + 16 * 8 * 6.0)
+            sweep = (nb - 1) * (npairs * sub + 64.0 * ne * ne + 32.0 * n * ne)
+        tot += 8.0 * ne ** 3 + sweeps_per_block * sweep + 1.0 * ne ** 3
     return tot
 
 
@@ -540,7 +554,7 @@ def run_gb300(args):
         flops = psd_flops(P.cone.s, per_block)
         peak_t = fp32_alu_peak_tflops(clk.get("sm_mhz"))
         achieved_t = flops / (avg_us * 1e-6) / 1e12
-        psd = {"bound": "alu", "kernel": "psd_project_kernel (Jacobi per block, one CTA per block)",
+        psd = {"bound": "alu", "kernel": "psd_project_kernel (Jacobi per block, blocked above order 48; one CTA per block)",
                "achieved": achieved_t, "peak": peak_t, "unit": "TFLOP/s", "frac": achieved_t / peak_t,
                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x sampled SM clock",
                "avg_launch_us": avg_us, "blocks": len(P.cone.s), "sweeps_per_block": per_block,

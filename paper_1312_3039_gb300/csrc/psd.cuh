@@ -9,7 +9,8 @@
 // projection of the matrix).
 //
 // On the CTA the block is a dense ne x ne matrix, ne = n rounded up to a
-// multiple of 4 (the padding rows and columns are zero and never rotated),
+// multiple of 4, or of 16 above order 48 (the padding rows and columns are
+// zero and never rotated),
 // row-major with leading dimension ld = ne + 1 (odd, so a column walk hits
 // 32 different shared-memory banks).  Three such matrices X, V, W live in
 // shared memory when they fit, else in a global scratch area of the CTA.
@@ -30,6 +31,20 @@
 // thread walks its 2 x 2 blocks (the lower triangle folded into an
 // h/2 x (h + 1) rectangle) and its rows of V by increments, without integer
 // division in the sweep.
+//
+// Above order 48 the same cyclic Jacobi runs blocked, so that most of its
+// work is dense panel products instead of two CTA barriers per round: the
+// ne indices are split into nb = ne / 8 blocks, and a block round pairs
+// the blocks by the round-robin tournament (nb - 1 block rounds a sweep).
+// For each block pair one warp runs one cyclic sweep (15 rounds of 8
+// disjoint rotations, same rotation and skip rules) on the 16 x 16
+// subproblem S = X[R, R] (R: the pair's 16 indices), accumulating its
+// rotations in Q (16 x 16, S <- Q^T S Q).  The pairs of a block round are
+// disjoint, so the round's transformation is J = Q_1 (+) Q_2 (+) ... on
+// disjoint index sets: X <- J^T X J and V <- V J, applied as the row panel
+// product X[R, :] <- Q^T X[R, :], then the column panel products
+// X[:, R] <- X[:, R] Q and V[:, R] <- V[:, R] Q, with the diagonal block
+// X[R, R] taken from the rotated S.  The stopping test is the same.
 //
 // Warm start (the iteration's blocks change little from one ADMM step to
 // the next): V from the previous projection is first made orthogonal again
@@ -67,7 +82,12 @@ template <> struct PsdEps<double> {
     static constexpr double off_tol = 1e-14;
 };
 
-__host__ __device__ inline int psd_ne(int n) { return n < 4 ? 4 : (n + 3) & ~3; }
+// Blocks of order above kPsdBlockedMin run the blocked eigensolver, which
+// needs ne to be a multiple of 16 (pairs of 8-index blocks).
+constexpr int kPsdBlockedMin = 48;
+__host__ __device__ inline int psd_ne(int n) {
+    return n < 4 ? 4 : n <= kPsdBlockedMin ? (n + 3) & ~3 : (n + 15) & ~15;
+}
 __host__ __device__ inline int psd_ld(int n) { return psd_ne(n) + 1; }
 __host__ __device__ inline int64_t psd_svec_len(int n) { return (int64_t)n * (n + 1) / 2; }
 __host__ __device__ inline int64_t psd_mat_elems(int n) { return (int64_t)psd_ne(n) * psd_ld(n); }
@@ -294,6 +314,65 @@ __device__ __forceinline__ void psd_rotate_block(T *X, int ld, const PsdRot<T> &
     X[qj * ld + qi] = d2;
 }
 
+// Rotation of pair (p, q) that zeroes a_pq of the 2 x 2 block
+// [[a_pp, a_pq], [a_pq, a_qq]]; the identity (s = 0) when
+// |a_pq| <= max(eps sqrt|a_pp a_qq|, floor_abs).
+template <typename T>
+__device__ __forceinline__ PsdRot<T> psd_rotation(T app, T aqq, T apq, int p, int q, T eps, T floor_abs) {
+    PsdRot<T> rt;
+    rt.c = T(1);
+    rt.s = T(0);
+    rt.t = T(0);
+    rt.pq = p | (q << 16);
+    const T thr = fmax(eps * sqrt(fabs(app * aqq)), floor_abs);
+    if (fabs(apq) > thr) {
+        const T tau = (aqq - app) / (T(2) * apq);
+        const T at = fabs(tau);
+        const T root = at > T(1) ? at * sqrt(T(1) + (T(1) / at) / at) : sqrt(T(1) + at * at);
+        T t = T(1) / (at + root);
+        if (tau < T(0)) t = -t;
+        rt.c = T(1) / sqrt(T(1) + t * t);
+        rt.s = t * rt.c;
+        rt.t = t;
+    }
+    return rt;
+}
+
+// The same rotation with a shorter FP32 dependency chain, for the blocked
+// sweeps' subproblems: t from fast reciprocals (an inexact t still gives an
+// exact rotation, and only perturbs the zeroed a_pq by about eps |a_pq|),
+// c = 1 / sqrt(1 + t^2) from rsqrtf refined by one Newton-Raphson step
+// (y <- y (3 - x y^2) / 2), so c^2 + s^2 = 1 to about an ulp.  FP64 keeps
+// the IEEE path.
+template <typename T>
+__device__ __forceinline__ PsdRot<T> psd_rotation_fast(T app, T aqq, T apq, int p, int q, T eps, T floor_abs) {
+    return psd_rotation(app, aqq, apq, p, q, eps, floor_abs);
+}
+template <>
+__device__ __forceinline__ PsdRot<float> psd_rotation_fast<float>(float app, float aqq, float apq, int p, int q,
+                                                                  float eps, float floor_abs) {
+    PsdRot<float> rt;
+    rt.c = 1.f;
+    rt.s = 0.f;
+    rt.t = 0.f;
+    rt.pq = p | (q << 16);
+    const float thr = fmaxf(eps * sqrtf(fabsf(app * aqq)), floor_abs);
+    if (fabsf(apq) > thr) {
+        const float tau = __fdividef(aqq - app, 2.f * apq);
+        const float at = fabsf(tau);
+        // 1 / (|tau| + sqrt(1 + tau^2)); 1 / (2 |tau|) once tau^2 would overflow
+        float t = at < 1e18f ? __fdividef(1.f, at + (1.f + at * at) * rsqrtf(1.f + at * at)) : __fdividef(0.5f, at);
+        if (tau < 0.f) t = -t;
+        const float x = 1.f + t * t;
+        float c = rsqrtf(x);
+        c = c * (1.5f - 0.5f * x * c * c);
+        rt.c = c;
+        rt.s = t * c;
+        rt.t = t;
+    }
+    return rt;
+}
+
 // Cyclic Jacobi on the symmetric X (ne x ne), accumulating V <- V J on the
 // first nrows_v rows of V.  Returns the number of sweeps run.
 //
@@ -333,24 +412,8 @@ __device__ __forceinline__ int psd_jacobi(T *X, T *V, int ne, int ld, int nrows_
             for (int k = tid; k < h; k += nt) {
                 int p, q;
                 psd_pair(r, k, ne, p, q);
-                const T app = X[p * ld + p], aqq = X[q * ld + q], apq = X[p * ld + q];
-                PsdRot<T> rt;
-                rt.c = T(1);
-                rt.s = T(0);
-                rt.t = T(0);
-                rt.pq = p | (q << 16);
-                const T thr = fmax(eps * sqrt(fabs(app * aqq)), floor_abs);
-                if (fabs(apq) > thr) {
-                    const T tau = (aqq - app) / (T(2) * apq);
-                    const T at = fabs(tau);
-                    const T root = at > T(1) ? at * sqrt(T(1) + (T(1) / at) / at) : sqrt(T(1) + at * at);
-                    T t = T(1) / (at + root);
-                    if (tau < T(0)) t = -t;
-                    rt.c = T(1) / sqrt(T(1) + t * t);
-                    rt.s = t * rt.c;
-                    rt.t = t;
-                    *fl = 1;
-                }
+                const PsdRot<T> rt = psd_rotation(X[p * ld + p], X[q * ld + q], X[p * ld + q], p, q, eps, floor_abs);
+                if (rt.s != T(0)) *fl = 1;
                 sm.rot[k] = rt;
             }
             if (tid == 0) sm.flags[(round + 1) & 1] = 0;
@@ -403,6 +466,257 @@ __device__ __forceinline__ int psd_jacobi(T *X, T *V, int ne, int ld, int nrows_
                             vr[p] = rk.c * vp - rk.s * vq;
                             vr[q] = rk.s * vp + rk.c * vq;
                         }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (!any || psd_off2(X, ne, ld, sm.red) <= stop2) break;
+    }
+    return sweeps;
+}
+
+// ---- blocked Jacobi (orders above kPsdBlockedMin)
+constexpr int kPsdB = 8;                    // indices per block
+constexpr int kPsdR = 2 * kPsdB;            // order of a block pair's subproblem
+constexpr int kPsdSld = kPsdR + 1;          // leading dimension of S
+// per block pair in W: S (16 x 17), Q (16 x 16, rows 16-byte aligned), the
+// 8 rotation records of the current subproblem round
+constexpr int kPsdSlice = kPsdR * kPsdSld + kPsdR * kPsdR + 4 * kPsdB;
+
+// Index of the subproblem's local index a (0..15) in the block pair (bI, bJ).
+__device__ __forceinline__ int psd_sub_index(int a, int bI, int bJ) {
+    return a < kPsdB ? bI * kPsdB + a : bJ * kPsdB + (a - kPsdB);
+}
+
+// Four consecutive entries from a 16-byte aligned shared or global address.
+__device__ __forceinline__ void psd_load4(const float *p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+}
+__device__ __forceinline__ void psd_load4(const double *p, double (&v)[4]) {
+    const double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+}
+
+// Rounds of cyclic Jacobi, by one warp, on the 16 x 16 symmetric S
+// (leading dimension kPsdSld), accumulating Q <- Q J.  full: one sweep over
+// all 120 index pairs (15 round-robin rounds); else the 64 pairs across the
+// two blocks (8 rounds, pairs (a, 8 + (a + m) mod 8) in round m).  Returns
+// (in every lane) whether any rotation was applied.
+template <typename T>
+__device__ __forceinline__ bool psd_sub_sweep(T *S, T *Q, PsdRot<T> *rot, int lane, bool full, T eps, T floor_abs) {
+    constexpr int h = kPsdB, rw = h + 1;
+    bool any = false;
+    const int nrounds = full ? kPsdR - 1 : kPsdB;
+    for (int ir = 0; ir < nrounds; ++ir) {
+        bool mine = false;
+        if (lane < h) {
+            int p, q;
+            if (full) {
+                psd_pair(ir, lane, kPsdR, p, q);
+            } else {
+                p = lane;
+                q = kPsdB + ((lane + ir) & (kPsdB - 1));
+            }
+            const PsdRot<T> rt =
+                psd_rotation_fast(S[p * kPsdSld + p], S[q * kPsdSld + q], S[p * kPsdSld + q], p, q, eps, floor_abs);
+            mine = rt.s != T(0);
+            rot[lane] = rt;
+        }
+        const bool round_any = __any_sync(0xffffffffu, mine);
+        __syncwarp();
+        if (!round_any) continue;
+        any = true;
+        // both sides on the 2 x 2 blocks (i >= j) of the lower triangle,
+        // folded into h/2 rows of h + 1 blocks, mirrored
+        for (int idx = lane; idx < (h / 2) * rw; idx += 32) {
+            const int fr = idx / rw, cc = idx - fr * rw;
+            const bool lo = cc <= fr;
+            const int i = lo ? fr : h - 1 - fr, j = lo ? cc : cc - fr - 1;
+            const PsdRot<T> ri = rot[i], rj = rot[j];
+            if (ri.s == T(0) && rj.s == T(0)) continue;
+            const int pi = ri.pq & 0xffff, qi = ri.pq >> 16, pj = rj.pq & 0xffff, qj = rj.pq >> 16;
+            if (i == j) {
+                const T apq = S[pi * kPsdSld + qi];
+                S[pi * kPsdSld + pi] -= ri.t * apq;
+                S[qi * kPsdSld + qi] += ri.t * apq;
+                S[pi * kPsdSld + qi] = T(0);
+                S[qi * kPsdSld + pi] = T(0);
+                continue;
+            }
+            const T a = S[pi * kPsdSld + pj], b = S[pi * kPsdSld + qj];
+            const T c = S[qi * kPsdSld + pj], d = S[qi * kPsdSld + qj];
+            const T a1 = ri.c * a - ri.s * c, b1 = ri.c * b - ri.s * d;
+            const T c1 = ri.s * a + ri.c * c, d1 = ri.s * b + ri.c * d;
+            const T a2 = rj.c * a1 - rj.s * b1, b2 = rj.s * a1 + rj.c * b1;
+            const T c2 = rj.c * c1 - rj.s * d1, d2 = rj.s * c1 + rj.c * d1;
+            S[pi * kPsdSld + pj] = a2;
+            S[pi * kPsdSld + qj] = b2;
+            S[qi * kPsdSld + pj] = c2;
+            S[qi * kPsdSld + qj] = d2;
+            S[pj * kPsdSld + pi] = a2;
+            S[qj * kPsdSld + pi] = b2;
+            S[pj * kPsdSld + qi] = c2;
+            S[qj * kPsdSld + qi] = d2;
+        }
+        // Q <- Q J: lane owns row lane % 16 and every other pair (disjoint
+        // columns: all loads first)
+        {
+            T *qr = Q + (lane & (kPsdR - 1)) * kPsdR;
+            PsdRot<T> rk[h / 2];
+            T vp[h / 2], vq[h / 2];
+#pragma unroll
+            for (int m = 0; m < h / 2; ++m) {
+                rk[m] = rot[(lane >> 4) + 2 * m];
+                vp[m] = qr[rk[m].pq & 0xffff];
+                vq[m] = qr[rk[m].pq >> 16];
+            }
+#pragma unroll
+            for (int m = 0; m < h / 2; ++m) {
+                qr[rk[m].pq & 0xffff] = rk[m].c * vp[m] - rk[m].s * vq[m];
+                qr[rk[m].pq >> 16] = rk[m].s * vp[m] + rk[m].c * vq[m];
+            }
+        }
+        __syncwarp();
+    }
+    return any;
+}
+
+// Blocked cyclic Jacobi on the symmetric X (ne x ne, ne a multiple of 16),
+// accumulating V <- V J on its first nrows_v rows; W (at least
+// ne / 16 * kPsdSlice entries, 16-byte aligned) holds the block pairs'
+// subproblems.  Returns the number of sweeps run.
+template <typename T>
+__device__ __forceinline__ int psd_jacobi_blocked(T *X, T *V, T *W, int ne, int ld, int nrows_v, const PsdSmall<T> &sm,
+                                                  T fro) {
+    constexpr int CPT = sizeof(T) == 4 ? 2 : 1;     // columns (rows) per thread in the panel products
+    const int nb = ne / kPsdB, npairs = nb / 2;
+    const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const T eps = PsdEps<T>::v;
+    const T floor_abs = eps * fro / static_cast<T>(ne);
+    const T stop2 = (PsdEps<T>::off_tol * fro) * (PsdEps<T>::off_tol * fro);
+    if (psd_off2(X, ne, ld, sm.red) <= stop2) return 0;
+    if (tid == 0) {
+        sm.flags[0] = 0;
+        sm.flags[1] = 0;
+    }
+    __syncthreads();
+    int sweeps = 0, round = 0;
+    while (sweeps < kPsdMaxSweeps) {
+        ++sweeps;
+        bool any = false;
+        for (int br = 0; br < nb - 1; ++br, ++round) {
+            int *fl = sm.flags + (round & 1);
+            // subproblems: one warp per block pair
+            for (int k = warp; k < npairs; k += nw) {
+                int bI, bJ;
+                psd_pair(br, k, nb, bI, bJ);
+                T *S = W + (size_t)k * kPsdSlice, *Q = S + kPsdR * kPsdSld;
+                PsdRot<T> *rot = reinterpret_cast<PsdRot<T> *>(Q + kPsdR * kPsdR);
+                for (int e = lane; e < kPsdR * kPsdR; e += 32) {
+                    const int a = e >> 4, b = e & (kPsdR - 1);
+                    const int ga = psd_sub_index(a, bI, bJ), gb = psd_sub_index(b, bI, bJ);
+                    // the lower triangle of X, so S is exactly symmetric
+                    S[a * kPsdSld + b] = ga >= gb ? X[(size_t)ga * ld + gb] : X[(size_t)gb * ld + ga];
+                    Q[e] = a == b ? T(1) : T(0);
+                }
+                __syncwarp();
+                // the first block round of a sweep also covers the pairs
+                // inside each block (every block is in one of its pairs)
+                if (psd_sub_sweep(S, Q, rot, lane, br == 0, eps, floor_abs) && lane == 0) *fl = 1;
+            }
+            if (tid == 0) sm.flags[(round + 1) & 1] = 0;
+            __syncthreads();
+            const bool rot = *fl != 0;
+            any = any || rot;
+            if (rot) {
+                // rows: X[R, c] <- sum_a Q[a][r] X[R_a, c] for every column c
+                const int gpr = ne / CPT;
+                for (int u = tid; u < npairs * gpr; u += nt) {
+                    const int k = u / gpr, g = u - k * gpr;
+                    int bI, bJ;
+                    psd_pair(br, k, nb, bI, bJ);
+                    const T *Q = W + (size_t)k * kPsdSlice + kPsdR * kPsdSld;
+                    T acc[kPsdR][CPT];
+#pragma unroll
+                    for (int r = 0; r < kPsdR; ++r)
+#pragma unroll
+                        for (int m = 0; m < CPT; ++m) acc[r][m] = T(0);
+#pragma unroll 4
+                    for (int a = 0; a < kPsdR; ++a) {
+                        const int ga = psd_sub_index(a, bI, bJ);
+                        T x[CPT];
+#pragma unroll
+                        for (int m = 0; m < CPT; ++m) x[m] = X[(size_t)ga * ld + g + m * gpr];
+#pragma unroll
+                        for (int r4 = 0; r4 < kPsdR; r4 += 4) {
+                            T q[4];
+                            psd_load4(Q + a * kPsdR + r4, q);
+#pragma unroll
+                            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                                for (int m = 0; m < CPT; ++m) acc[r4 + r][m] = fma(q[r], x[m], acc[r4 + r][m]);
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < kPsdR; ++r) {
+                        const int gr = psd_sub_index(r, bI, bJ);
+#pragma unroll
+                        for (int m = 0; m < CPT; ++m) X[(size_t)gr * ld + g + m * gpr] = acc[r][m];
+                    }
+                }
+                __syncthreads();
+                // columns: M[row, R] <- sum_a M[row, R_a] Q[a][r] for the rows
+                // of X and of V; X's diagonal block takes the rotated S
+                const int gx = ne / CPT, gv = (nrows_v + CPT - 1) / CPT, gtot = gx + gv;
+                for (int u = tid; u < npairs * gtot; u += nt) {
+                    const int k = u / gtot, g = u - k * gtot;
+                    const bool isx = g < gx;
+                    T *M = isx ? X : V;
+                    const int g0 = isx ? g : g - gx, span = isx ? gx : gv, rows = isx ? ne : nrows_v;
+                    int bI, bJ;
+                    psd_pair(br, k, nb, bI, bJ);
+                    const T *S = W + (size_t)k * kPsdSlice, *Q = S + kPsdR * kPsdSld;
+                    T acc[kPsdR][CPT];
+#pragma unroll
+                    for (int r = 0; r < kPsdR; ++r)
+#pragma unroll
+                        for (int m = 0; m < CPT; ++m) acc[r][m] = T(0);
+#pragma unroll 4
+                    for (int a = 0; a < kPsdR; ++a) {
+                        const int ga = psd_sub_index(a, bI, bJ);
+                        T y[CPT];
+#pragma unroll
+                        for (int m = 0; m < CPT; ++m) {
+                            const int row = g0 + m * span;
+                            y[m] = row < rows ? M[(size_t)row * ld + ga] : T(0);
+                        }
+#pragma unroll
+                        for (int r4 = 0; r4 < kPsdR; r4 += 4) {
+                            T q[4];
+                            psd_load4(Q + a * kPsdR + r4, q);
+#pragma unroll
+                            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                                for (int m = 0; m < CPT; ++m) acc[r4 + r][m] = fma(y[m], q[r], acc[r4 + r][m]);
+                        }
+                    }
+#pragma unroll
+                    for (int m = 0; m < CPT; ++m) {
+                        const int row = g0 + m * span;
+                        if (row >= rows) continue;
+                        const int rb = row / kPsdB;
+                        const int loc = !isx ? -1 : rb == bI ? row - bI * kPsdB : rb == bJ ? kPsdB + row - bJ * kPsdB : -1;
+#pragma unroll
+                        for (int r = 0; r < kPsdR; ++r)
+                            M[(size_t)row * ld + psd_sub_index(r, bI, bJ)] = loc >= 0 ? S[loc * kPsdSld + r] : acc[r][m];
                     }
                 }
             }
@@ -484,7 +798,8 @@ __device__ __forceinline__ void psd_project_block(IO &io, int n, T *X, T *V, T *
         f2 += x * x;
     }
     f2 = psd_block_sum(f2, sm.red);
-    const int sweeps = psd_jacobi(X, V, ne, ld, n, sm, sqrt(f2));
+    const int sweeps = ne > kPsdBlockedMin ? psd_jacobi_blocked(X, V, W, ne, ld, n, sm, sqrt(f2))
+                                           : psd_jacobi(X, V, ne, ld, n, sm, sqrt(f2));
     // ---- eigenvalues, positive set, conditioning
     for (int j = threadIdx.x; j < ne; j += blockDim.x) sm.lam[j] = X[(size_t)j * ld + j];
     __syncthreads();

@@ -42,7 +42,7 @@ def project_batch(env, cone, V, dual=1):
     return out.cpu().numpy(), d2
 
 
-@pytest.mark.parametrize("order", [1, 2, 3, 4, 5, 8, 17, 40, 96, 97, 128])
+@pytest.mark.parametrize("order", [1, 2, 3, 4, 5, 8, 17, 40, 48, 49, 64, 96, 97, 128, 200])
 def test_project_orders(env, order):
     rng = np.random.default_rng(order)
     cone = synth.Cone(s=(order,))
@@ -55,16 +55,17 @@ def test_project_orders(env, order):
     assert abs(d2 - want) <= 1e-10 * max(1.0, want)
 
 
-def test_project_special_matrices(env):
+@pytest.mark.parametrize("k", [12, 64])          # scalar and blocked Jacobi
+def test_project_special_matrices(env, k):
     rng = np.random.default_rng(11)
-    k = 12
     Q, _ = np.linalg.qr(rng.standard_normal((k, k)))
     lam_pos = rng.uniform(0.5, 2.0, k)
+    h = k // 2
     cases = {
         "psd": (Q * lam_pos) @ Q.T,                                   # unchanged
         "negdef": -(Q * lam_pos) @ Q.T,                               # -> 0
-        "repeated": (Q * np.r_[[1.0] * 6, [-1.0] * 6]) @ Q.T,         # -> Q1 Q1^T
-        "spread": (Q * (10.0 ** np.linspace(-7, 0, k) * np.r_[[1, -1] * 6])) @ Q.T,
+        "repeated": (Q * np.r_[[1.0] * h, [-1.0] * h]) @ Q.T,         # -> Q1 Q1^T
+        "spread": (Q * (10.0 ** np.linspace(-7, 0, k) * np.r_[[1, -1] * h])) @ Q.T,
         "zero": np.zeros((k, k)),
     }
     cone = synth.Cone(s=(k,))
@@ -73,7 +74,7 @@ def test_project_special_matrices(env):
     want = {
         "psd": sym_svec(cases["psd"]),
         "negdef": np.zeros(cone.m),
-        "repeated": sym_svec(Q[:, :6] @ Q[:, :6].T),
+        "repeated": sym_svec(Q[:, :h] @ Q[:, :h].T),
     }
     for (name, M), g, v in zip(cases.items(), got, V):
         ref = want.get(name, cones.proj_psd(v, k))
@@ -116,6 +117,12 @@ def test_sdp_trajectory_fp64_mixed_cones(env):
     trajectory_parity(scs, synth.random_cone(21, n=30, cone=cone))
 
 
+def test_sdp_trajectory_fp64_blocked(env):
+    """Order 56 (padded to 64): the blocked Jacobi with X, V, W on chip."""
+    torch, scs = env
+    trajectory_parity(scs, small_sdp(4, order=56, n_psd=2, n_ill=1, n=60, n_nonneg=10, density=0.05), iters=30)
+
+
 def test_sdp_trajectory_fp64_global_scratch(env):
     """Order 100 in FP64 does not fit on chip: X, W in global scratch and V in
     its persistent storage."""
@@ -124,17 +131,21 @@ def test_sdp_trajectory_fp64_global_scratch(env):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_sdp_solve(env, precision):
+@pytest.mark.parametrize("order,n_psd", [(10, 4), (60, 2)])      # scalar and blocked Jacobi
+def test_sdp_solve(env, precision, order, n_psd):
     torch, scs = env
-    P = small_sdp(2, order=10, n_psd=4, n_ill=1, n=120, n_nonneg=40, density=0.1)
+    P = small_sdp(2, order=order, n_psd=n_psd, n_ill=1, n=120, n_nonneg=40, density=0.1)
     ref = admm.solve(P.A, P.b, P.c, P.cone, same_settings())
     with scs.Solver(P.A, P.b, P.c, P.cone, precision=precision) as g:
         st, x, y, s, info = g.solve()
         calls, sweeps, fp64 = g.psd_counters()
     assert st == 1, st
-    check_solution(P, x, y, s, cone_tol=1e-7 if precision == 0 else 1e-5)
+    # FP32: the sweeps stop at ||off(X)||_F <= 1e-6 ||X||_F <= 1e-6 sqrt(order)
+    # ||X||_2, and the FP32 rounding of the eigenvector products adds about
+    # as much to the dual iterate s
+    check_solution(P, x, y, s, cone_tol=1e-7 if precision == 0 else max(1e-5, 3e-6 * np.sqrt(order)))
     assert_objective_parity(P, precision, info, x, y, s, ref)
-    assert calls == 4 * info["iters"]
+    assert calls == n_psd * info["iters"]
     assert 0 < sweeps < 10 * calls     # warm-started blocks often need no sweep at all
     if precision == 0:
         assert fp64 == 0         # the FP64 engine has nothing to promote
