@@ -223,12 +223,13 @@ def psd_flops(orders, sweeps_per_block):
     the eigenvalues (ne^3).  Orders up to 48 (ne = n rounded up to 4): a
     sweep is ne - 1 rounds of 12 h^2 + 6 n h flops (h = ne / 2: both sides of
     the lower 2 x 2 blocks and the rows of V).  Above (ne = n rounded up to
-    16, nb = ne / 8 blocks): a sweep is nb - 1 block rounds, each with one
-    15-round sweep of every block pair's 16 x 16 subproblem (36 2 x 2 blocks
-    of 24 flops and 16 x 8 Q updates of 6 flops a round) and the panel
-    products X[R, :] <- Q^T X[R, :], X[:, R] <- X[:, R] Q (32 ne^2 flops
-    each over all pairs) and V[:, R] <- V[:, R] Q (32 n ne), counted as the
-    kernel performs them."""
+    16, nb = ne / 8 blocks, P = ne / 16 block pairs): a sweep is nb - 1
+    block rounds, each with the rotations of every block pair's 16 x 16
+    subproblem (15 rounds in the first block round of a sweep, 8 in the
+    others; a round is 36 2 x 2 blocks of 24 flops and 16 x 8 Q updates of 6
+    flops), the P (P - 1) / 2 off-diagonal blocks Q_k^T X_kl Q_l (two
+    16 x 16 x 16 products each) and V[:, R] <- V[:, R] Q (32 n ne flops over
+    all pairs), counted as the kernel performs them."""
     tot = 0.0
     for n in orders:
         if n <= 48:
@@ -238,8 +239,9 @@ def psd_flops(orders, sweeps_per_block):
         else:
             ne = (n + 15) // 16 * 16
             nb, npairs = ne // 8, ne // 16
-            sub = 15 * (36 * 24.0 + 16 * 8 * 6.0)
-            sweep = (nb - 1) * (npairs * sub + 64.0 * ne * ne + 32.0 * n * ne)
+            rnd = 36 * 24.0 + 16 * 8 * 6.0
+            sub = npairs * rnd * (15 + 8 * (nb - 2))
+            sweep = sub + (nb - 1) * (npairs * (npairs - 1) / 2 * 4.0 * 16 ** 3 + 32.0 * n * ne)
         tot += 8.0 * ne ** 3 + sweeps_per_block * sweep + 1.0 * ne ** 3
     return tot
 

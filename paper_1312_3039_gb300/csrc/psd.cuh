@@ -41,10 +41,11 @@
 // subproblem S = X[R, R] (R: the pair's 16 indices), accumulating its
 // rotations in Q (16 x 16, S <- Q^T S Q).  The pairs of a block round are
 // disjoint, so the round's transformation is J = Q_1 (+) Q_2 (+) ... on
-// disjoint index sets: X <- J^T X J and V <- V J, applied as the row panel
-// product X[R, :] <- Q^T X[R, :], then the column panel products
-// X[:, R] <- X[:, R] Q and V[:, R] <- V[:, R] Q, with the diagonal block
-// X[R, R] taken from the rotated S.  The stopping test is the same.
+// disjoint index sets: X <- J^T X J and V <- V J.  X stays symmetric: its
+// diagonal block X[R_k, R_k] is the rotated S of pair k, and the block of
+// two pairs k > l is Q_k^T X[R_k, R_l] Q_l (one warp, written with its
+// mirror); V[:, R] <- V[:, R] Q is a column panel product.  The stopping
+// test is the same.
 //
 // Warm start (the iteration's blocks change little from one ADMM step to
 // the next): V from the previous projection is first made orthogonal again
@@ -356,7 +357,10 @@ __device__ __forceinline__ PsdRot<float> psd_rotation_fast<float>(float app, flo
     rt.s = 0.f;
     rt.t = 0.f;
     rt.pq = p | (q << 16);
-    const float thr = fmaxf(eps * sqrtf(fabsf(app * aqq)), floor_abs);
+    // the threshold needs no exact root; x rsqrt(x) is NaN for x = 0, which
+    // fmaxf drops
+    const float x0 = fabsf(app * aqq);
+    const float thr = fmaxf(eps * (x0 * rsqrtf(x0)), floor_abs);
     if (fabsf(apq) > thr) {
         const float tau = __fdividef(aqq - app, 2.f * apq);
         const float at = fabsf(tau);
@@ -480,9 +484,13 @@ __device__ __forceinline__ int psd_jacobi(T *X, T *V, int ne, int ld, int nrows_
 constexpr int kPsdB = 8;                    // indices per block
 constexpr int kPsdR = 2 * kPsdB;            // order of a block pair's subproblem
 constexpr int kPsdSld = kPsdR + 1;          // leading dimension of S
-// per block pair in W: S (16 x 17), Q (16 x 16, rows 16-byte aligned), the
-// 8 rotation records of the current subproblem round
-constexpr int kPsdSlice = kPsdR * kPsdSld + kPsdR * kPsdR + 4 * kPsdB;
+// per block pair in W: S (16 x 17); Q while the rounds run (16 x 17: a
+// column of 16 rows hits 16 banks); Q for the panel products (16 x 16, rows
+// 16-byte aligned for vector loads); the 8 rotation records of a round
+constexpr int kPsdOffQi = kPsdR * kPsdSld;
+constexpr int kPsdOffQ = 2 * kPsdR * kPsdSld;
+constexpr int kPsdOffRot = kPsdOffQ + kPsdR * kPsdR;
+constexpr int kPsdSlice = kPsdOffRot + 4 * kPsdB;
 
 // Index of the subproblem's local index a (0..15) in the block pair (bI, bJ).
 __device__ __forceinline__ int psd_sub_index(int a, int bI, int bJ) {
@@ -506,15 +514,21 @@ __device__ __forceinline__ void psd_load4(const double *p, double (&v)[4]) {
 }
 
 // Rounds of cyclic Jacobi, by one warp, on the 16 x 16 symmetric S
-// (leading dimension kPsdSld), accumulating Q <- Q J.  full: one sweep over
+// (leading dimension kPsdSld), accumulating Q <- Q J (leading dimension
+// kPsdSld).  full: one sweep over
 // all 120 index pairs (15 round-robin rounds); else the 64 pairs across the
 // two blocks (8 rounds, pairs (a, 8 + (a + m) mod 8) in round m).  Returns
 // (in every lane) whether any rotation was applied.
 template <typename T>
 __device__ __forceinline__ bool psd_sub_sweep(T *S, T *Q, PsdRot<T> *rot, int lane, bool full, T eps, T floor_abs) {
-    constexpr int h = kPsdB, rw = h + 1;
+    constexpr int h = kPsdB;
     bool any = false;
     const int nrounds = full ? kPsdR - 1 : kPsdB;
+    // this lane's 2 x 2 block (i, j), i > j, of the round's 8 pairs
+    // (lanes 0..27; lane = i (i - 1) / 2 + j); the pairs' own blocks are
+    // updated by the lanes that compute their rotations
+    const int bi = lane < h * (h - 1) / 2 ? static_cast<int>((1.f + sqrtf(8.f * lane + 1.f)) * 0.5f) : 0;
+    const int bj = lane - bi * (bi - 1) / 2;
     for (int ir = 0; ir < nrounds; ++ir) {
         bool mine = false;
         if (lane < h) {
@@ -525,51 +539,47 @@ __device__ __forceinline__ bool psd_sub_sweep(T *S, T *Q, PsdRot<T> *rot, int la
                 p = lane;
                 q = kPsdB + ((lane + ir) & (kPsdB - 1));
             }
-            const PsdRot<T> rt =
-                psd_rotation_fast(S[p * kPsdSld + p], S[q * kPsdSld + q], S[p * kPsdSld + q], p, q, eps, floor_abs);
+            const T app = S[p * kPsdSld + p], aqq = S[q * kPsdSld + q], apq = S[p * kPsdSld + q];
+            const PsdRot<T> rt = psd_rotation_fast(app, aqq, apq, p, q, eps, floor_abs);
             mine = rt.s != T(0);
             rot[lane] = rt;
+            if (mine) {
+                // the pair's own block: zero s_pq exactly
+                S[p * kPsdSld + p] = app - rt.t * apq;
+                S[q * kPsdSld + q] = aqq + rt.t * apq;
+                S[p * kPsdSld + q] = T(0);
+                S[q * kPsdSld + p] = T(0);
+            }
         }
         const bool round_any = __any_sync(0xffffffffu, mine);
         __syncwarp();
         if (!round_any) continue;
         any = true;
-        // both sides on the 2 x 2 blocks (i >= j) of the lower triangle,
-        // folded into h/2 rows of h + 1 blocks, mirrored
-        for (int idx = lane; idx < (h / 2) * rw; idx += 32) {
-            const int fr = idx / rw, cc = idx - fr * rw;
-            const bool lo = cc <= fr;
-            const int i = lo ? fr : h - 1 - fr, j = lo ? cc : cc - fr - 1;
-            const PsdRot<T> ri = rot[i], rj = rot[j];
-            if (ri.s == T(0) && rj.s == T(0)) continue;
-            const int pi = ri.pq & 0xffff, qi = ri.pq >> 16, pj = rj.pq & 0xffff, qj = rj.pq >> 16;
-            if (i == j) {
-                const T apq = S[pi * kPsdSld + qi];
-                S[pi * kPsdSld + pi] -= ri.t * apq;
-                S[qi * kPsdSld + qi] += ri.t * apq;
-                S[pi * kPsdSld + qi] = T(0);
-                S[qi * kPsdSld + pi] = T(0);
-                continue;
+        // both sides on the lower 2 x 2 blocks of two different pairs, mirrored
+        if (lane < h * (h - 1) / 2) {
+            const PsdRot<T> ri = rot[bi], rj = rot[bj];
+            if (ri.s != T(0) || rj.s != T(0)) {
+                const int pi = ri.pq & 0xffff, qi = ri.pq >> 16, pj = rj.pq & 0xffff, qj = rj.pq >> 16;
+                const T a = S[pi * kPsdSld + pj], b = S[pi * kPsdSld + qj];
+                const T c = S[qi * kPsdSld + pj], d = S[qi * kPsdSld + qj];
+                const T a1 = ri.c * a - ri.s * c, b1 = ri.c * b - ri.s * d;
+                const T c1 = ri.s * a + ri.c * c, d1 = ri.s * b + ri.c * d;
+                const T a2 = rj.c * a1 - rj.s * b1, b2 = rj.s * a1 + rj.c * b1;
+                const T c2 = rj.c * c1 - rj.s * d1, d2 = rj.s * c1 + rj.c * d1;
+                S[pi * kPsdSld + pj] = a2;
+                S[pi * kPsdSld + qj] = b2;
+                S[qi * kPsdSld + pj] = c2;
+                S[qi * kPsdSld + qj] = d2;
+                S[pj * kPsdSld + pi] = a2;
+                S[qj * kPsdSld + pi] = b2;
+                S[pj * kPsdSld + qi] = c2;
+                S[qj * kPsdSld + qi] = d2;
             }
-            const T a = S[pi * kPsdSld + pj], b = S[pi * kPsdSld + qj];
-            const T c = S[qi * kPsdSld + pj], d = S[qi * kPsdSld + qj];
-            const T a1 = ri.c * a - ri.s * c, b1 = ri.c * b - ri.s * d;
-            const T c1 = ri.s * a + ri.c * c, d1 = ri.s * b + ri.c * d;
-            const T a2 = rj.c * a1 - rj.s * b1, b2 = rj.s * a1 + rj.c * b1;
-            const T c2 = rj.c * c1 - rj.s * d1, d2 = rj.s * c1 + rj.c * d1;
-            S[pi * kPsdSld + pj] = a2;
-            S[pi * kPsdSld + qj] = b2;
-            S[qi * kPsdSld + pj] = c2;
-            S[qi * kPsdSld + qj] = d2;
-            S[pj * kPsdSld + pi] = a2;
-            S[qj * kPsdSld + pi] = b2;
-            S[pj * kPsdSld + qi] = c2;
-            S[qj * kPsdSld + qi] = d2;
         }
         // Q <- Q J: lane owns row lane % 16 and every other pair (disjoint
         // columns: all loads first)
         {
-            T *qr = Q + (lane & (kPsdR - 1)) * kPsdR;
+            T *qr = Q + (lane & (kPsdR - 1)) * kPsdSld;
             PsdRot<T> rk[h / 2];
             T vp[h / 2], vq[h / 2];
 #pragma unroll
@@ -590,9 +600,11 @@ __device__ __forceinline__ bool psd_sub_sweep(T *S, T *Q, PsdRot<T> *rot, int la
 }
 
 // Blocked cyclic Jacobi on the symmetric X (ne x ne, ne a multiple of 16),
-// accumulating V <- V J on its first nrows_v rows; W (at least
-// ne / 16 * kPsdSlice entries, 16-byte aligned) holds the block pairs'
-// subproblems.  Returns the number of sweeps run.
+// accumulating V <- V J on its first nrows_v rows; W (ne (ne + 1) entries,
+// 16-byte aligned) holds the block pairs' subproblems (ne / 16 * kPsdSlice
+// entries) and 16 x 17 scratch tiles for the warps that compute the
+// off-diagonal blocks, as many as fit (at least 3 for ne >= 64).  Returns
+// the number of sweeps run.
 template <typename T>
 __device__ __forceinline__ int psd_jacobi_blocked(T *X, T *V, T *W, int ne, int ld, int nrows_v, const PsdSmall<T> &sm,
                                                   T fro) {
@@ -618,72 +630,111 @@ __device__ __forceinline__ int psd_jacobi_blocked(T *X, T *V, T *W, int ne, int 
             for (int k = warp; k < npairs; k += nw) {
                 int bI, bJ;
                 psd_pair(br, k, nb, bI, bJ);
-                T *S = W + (size_t)k * kPsdSlice, *Q = S + kPsdR * kPsdSld;
-                PsdRot<T> *rot = reinterpret_cast<PsdRot<T> *>(Q + kPsdR * kPsdR);
+                T *S = W + (size_t)k * kPsdSlice, *Qi = S + kPsdOffQi, *Q = S + kPsdOffQ;
+                PsdRot<T> *rot = reinterpret_cast<PsdRot<T> *>(S + kPsdOffRot);
                 for (int e = lane; e < kPsdR * kPsdR; e += 32) {
                     const int a = e >> 4, b = e & (kPsdR - 1);
                     const int ga = psd_sub_index(a, bI, bJ), gb = psd_sub_index(b, bI, bJ);
                     // the lower triangle of X, so S is exactly symmetric
                     S[a * kPsdSld + b] = ga >= gb ? X[(size_t)ga * ld + gb] : X[(size_t)gb * ld + ga];
-                    Q[e] = a == b ? T(1) : T(0);
+                    Qi[a * kPsdSld + b] = a == b ? T(1) : T(0);
                 }
                 __syncwarp();
                 // the first block round of a sweep also covers the pairs
                 // inside each block (every block is in one of its pairs)
-                if (psd_sub_sweep(S, Q, rot, lane, br == 0, eps, floor_abs) && lane == 0) *fl = 1;
+                if (psd_sub_sweep(S, Qi, rot, lane, br == 0, eps, floor_abs) && lane == 0) *fl = 1;
+                for (int e = lane; e < kPsdR * kPsdR; e += 32) Q[e] = Qi[(e >> 4) * kPsdSld + (e & (kPsdR - 1))];
             }
             if (tid == 0) sm.flags[(round + 1) & 1] = 0;
             __syncthreads();
             const bool rot = *fl != 0;
             any = any || rot;
             if (rot) {
-                // rows: X[R, c] <- sum_a Q[a][r] X[R_a, c] for every column c
-                const int gpr = ne / CPT;
-                for (int u = tid; u < npairs * gpr; u += nt) {
-                    const int k = u / gpr, g = u - k * gpr;
-                    int bI, bJ;
-                    psd_pair(br, k, nb, bI, bJ);
-                    const T *Q = W + (size_t)k * kPsdSlice + kPsdR * kPsdSld;
-                    T acc[kPsdR][CPT];
+                // X <- J^T X J, symmetric: the diagonal block of each pair is
+                // its rotated S; the block of pairs k > l is
+                // Q_k^T X[R_k, R_l] Q_l (one warp: T = X[R_k, R_l] Q_l into
+                // the warp's scratch, then Q_k^T T), written with its mirror
+                const int nblk = npairs * (npairs - 1) / 2;
+                T *scratch = W + (size_t)npairs * kPsdSlice;
+                // warps with a scratch tile in W (at least 3: ne >= 64)
+                const int nsw = min(min(nw, nblk), (ne * ld - npairs * kPsdSlice) / (kPsdR * kPsdSld));
+                for (int t = warp; warp < nsw && t < nblk; t += nsw) {
+                    int k = 1;
+                    while ((k + 1) * k / 2 <= t) ++k;       // t = k (k - 1) / 2 + l, l < k
+                    const int l = t - k * (k - 1) / 2;
+                    int kI, kJ, lI, lJ;
+                    psd_pair(br, k, nb, kI, kJ);
+                    psd_pair(br, l, nb, lI, lJ);
+                    const T *Qk = W + (size_t)k * kPsdSlice + kPsdOffQ;
+                    const T *Ql = W + (size_t)l * kPsdSlice + kPsdOffQ;
+                    T *Tw = scratch + (size_t)warp * kPsdR * kPsdSld;
+                    const int i = lane & (kPsdR - 1), c0 = (lane >> 4) * kPsdB;
+                    // T[i][c] = sum_b X[R_k(i), R_l(b)] Q_l[b][c], c in [c0, c0 + 8)
+                    {
+                        const T *xr = X + (size_t)psd_sub_index(i, kI, kJ) * ld;
+                        T acc[kPsdB];
 #pragma unroll
-                    for (int r = 0; r < kPsdR; ++r)
-#pragma unroll
-                        for (int m = 0; m < CPT; ++m) acc[r][m] = T(0);
+                        for (int c = 0; c < kPsdB; ++c) acc[c] = T(0);
 #pragma unroll 4
-                    for (int a = 0; a < kPsdR; ++a) {
-                        const int ga = psd_sub_index(a, bI, bJ);
-                        T x[CPT];
+                        for (int b = 0; b < kPsdR; ++b) {
+                            const T x = xr[psd_sub_index(b, lI, lJ)];
+                            T q[4], q2[4];
+                            psd_load4(Ql + b * kPsdR + c0, q);
+                            psd_load4(Ql + b * kPsdR + c0 + 4, q2);
 #pragma unroll
-                        for (int m = 0; m < CPT; ++m) x[m] = X[(size_t)ga * ld + g + m * gpr];
+                            for (int c = 0; c < 4; ++c) {
+                                acc[c] = fma(x, q[c], acc[c]);
+                                acc[c + 4] = fma(x, q2[c], acc[c + 4]);
+                            }
+                        }
 #pragma unroll
-                        for (int r4 = 0; r4 < kPsdR; r4 += 4) {
-                            T q[4];
-                            psd_load4(Q + a * kPsdR + r4, q);
+                        for (int c = 0; c < kPsdB; ++c) Tw[i * kPsdSld + c0 + c] = acc[c];
+                    }
+                    __syncwarp();
+                    // Y[r][c] = sum_i Q_k[i][r] T[i][c]: lane owns column c = lane % 16
+                    // and rows r in [c0, c0 + 8)
+                    {
+                        const int c = i, r0 = c0;
+                        T acc[kPsdB];
 #pragma unroll
-                            for (int r = 0; r < 4; ++r)
+                        for (int r = 0; r < kPsdB; ++r) acc[r] = T(0);
+#pragma unroll 4
+                        for (int ii = 0; ii < kPsdR; ++ii) {
+                            const T tv = Tw[ii * kPsdSld + c];
+                            T q[4], q2[4];
+                            psd_load4(Qk + ii * kPsdR + r0, q);
+                            psd_load4(Qk + ii * kPsdR + r0 + 4, q2);
 #pragma unroll
-                                for (int m = 0; m < CPT; ++m) acc[r4 + r][m] = fma(q[r], x[m], acc[r4 + r][m]);
+                            for (int r = 0; r < 4; ++r) {
+                                acc[r] = fma(q[r], tv, acc[r]);
+                                acc[r + 4] = fma(q2[r], tv, acc[r + 4]);
+                            }
+                        }
+                        const int gc = psd_sub_index(c, lI, lJ);
+#pragma unroll
+                        for (int r = 0; r < kPsdB; ++r) {
+                            const int gr = psd_sub_index(r0 + r, kI, kJ);
+                            X[(size_t)gr * ld + gc] = acc[r];
+                            X[(size_t)gc * ld + gr] = acc[r];
                         }
                     }
-#pragma unroll
-                    for (int r = 0; r < kPsdR; ++r) {
-                        const int gr = psd_sub_index(r, bI, bJ);
-#pragma unroll
-                        for (int m = 0; m < CPT; ++m) X[(size_t)gr * ld + g + m * gpr] = acc[r][m];
-                    }
+                    __syncwarp();
                 }
-                __syncthreads();
-                // columns: M[row, R] <- sum_a M[row, R_a] Q[a][r] for the rows
-                // of X and of V; X's diagonal block takes the rotated S
-                const int gx = ne / CPT, gv = (nrows_v + CPT - 1) / CPT, gtot = gx + gv;
-                for (int u = tid; u < npairs * gtot; u += nt) {
-                    const int k = u / gtot, g = u - k * gtot;
-                    const bool isx = g < gx;
-                    T *M = isx ? X : V;
-                    const int g0 = isx ? g : g - gx, span = isx ? gx : gv, rows = isx ? ne : nrows_v;
+                // diagonal blocks
+                for (int e = tid; e < npairs * kPsdR * kPsdR; e += nt) {
+                    const int k = e >> 8, a = (e >> 4) & (kPsdR - 1), b = e & (kPsdR - 1);
                     int bI, bJ;
                     psd_pair(br, k, nb, bI, bJ);
-                    const T *S = W + (size_t)k * kPsdSlice, *Q = S + kPsdR * kPsdSld;
+                    X[(size_t)psd_sub_index(a, bI, bJ) * ld + psd_sub_index(b, bI, bJ)] =
+                        W[(size_t)k * kPsdSlice + a * kPsdSld + b];
+                }
+                // V[row, R] <- sum_a V[row, R_a] Q[a][r]
+                const int gv = (nrows_v + CPT - 1) / CPT;
+                for (int u = tid; u < npairs * gv; u += nt) {
+                    const int k = u / gv, g0 = u - k * gv;
+                    int bI, bJ;
+                    psd_pair(br, k, nb, bI, bJ);
+                    const T *Q = W + (size_t)k * kPsdSlice + kPsdOffQ;
                     T acc[kPsdR][CPT];
 #pragma unroll
                     for (int r = 0; r < kPsdR; ++r)
@@ -695,8 +746,8 @@ __device__ __forceinline__ int psd_jacobi_blocked(T *X, T *V, T *W, int ne, int 
                         T y[CPT];
 #pragma unroll
                         for (int m = 0; m < CPT; ++m) {
-                            const int row = g0 + m * span;
-                            y[m] = row < rows ? M[(size_t)row * ld + ga] : T(0);
+                            const int row = g0 + m * gv;
+                            y[m] = row < nrows_v ? V[(size_t)row * ld + ga] : T(0);
                         }
 #pragma unroll
                         for (int r4 = 0; r4 < kPsdR; r4 += 4) {
@@ -710,13 +761,10 @@ __device__ __forceinline__ int psd_jacobi_blocked(T *X, T *V, T *W, int ne, int 
                     }
 #pragma unroll
                     for (int m = 0; m < CPT; ++m) {
-                        const int row = g0 + m * span;
-                        if (row >= rows) continue;
-                        const int rb = row / kPsdB;
-                        const int loc = !isx ? -1 : rb == bI ? row - bI * kPsdB : rb == bJ ? kPsdB + row - bJ * kPsdB : -1;
+                        const int row = g0 + m * gv;
+                        if (row >= nrows_v) continue;
 #pragma unroll
-                        for (int r = 0; r < kPsdR; ++r)
-                            M[(size_t)row * ld + psd_sub_index(r, bI, bJ)] = loc >= 0 ? S[loc * kPsdSld + r] : acc[r][m];
+                        for (int r = 0; r < kPsdR; ++r) V[(size_t)row * ld + psd_sub_index(r, bI, bJ)] = acc[r][m];
                     }
                 }
             }
