@@ -605,6 +605,52 @@ __device__ __forceinline__ bool psd_sub_sweep(T *S, T *Q, PsdRot<T> *rot, int la
 // entries) and 16 x 17 scratch tiles for the warps that compute the
 // off-diagonal blocks, as many as fit (at least 3 for ne >= 64).  Returns
 // the number of sweeps run.
+// V[row, R] <- sum_a V[row, R_a] Q[a][r] for every block pair of block
+// round br (Q at offset qoff of each pair's slice of W), over the first
+// nrows_v rows; units (pair, row group) from t0 in steps of tstride.
+template <typename T, int CPT>
+__device__ __forceinline__ void psd_v_panel(T *V, const T *W, int slice, int qoff, int ld, int nb, int npairs, int br,
+                                            int nrows_v, int t0, int tstride) {
+    const int gv = (nrows_v + CPT - 1) / CPT;
+    for (int u = t0; u < npairs * gv; u += tstride) {
+        const int k = u / gv, g0 = u - k * gv;
+        int bI, bJ;
+        psd_pair(br, k, nb, bI, bJ);
+        const T *Q = W + (size_t)k * slice + qoff;
+        T acc[kPsdR][CPT];
+#pragma unroll
+        for (int r = 0; r < kPsdR; ++r)
+#pragma unroll
+            for (int m = 0; m < CPT; ++m) acc[r][m] = T(0);
+#pragma unroll 4
+        for (int a = 0; a < kPsdR; ++a) {
+            const int ga = psd_sub_index(a, bI, bJ);
+            T y[CPT];
+#pragma unroll
+            for (int m = 0; m < CPT; ++m) {
+                const int row = g0 + m * gv;
+                y[m] = row < nrows_v ? V[(size_t)row * ld + ga] : T(0);
+            }
+#pragma unroll
+            for (int r4 = 0; r4 < kPsdR; r4 += 4) {
+                T q[4];
+                psd_load4(Q + a * kPsdR + r4, q);
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int m = 0; m < CPT; ++m) acc[r4 + r][m] = fma(y[m], q[r], acc[r4 + r][m]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < CPT; ++m) {
+            const int row = g0 + m * gv;
+            if (row >= nrows_v) continue;
+#pragma unroll
+            for (int r = 0; r < kPsdR; ++r) V[(size_t)row * ld + psd_sub_index(r, bI, bJ)] = acc[r][m];
+        }
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ int psd_jacobi_blocked(T *X, T *V, T *W, int ne, int ld, int nrows_v, const PsdSmall<T> &sm,
                                                   T fro) {
@@ -614,6 +660,11 @@ __device__ __forceinline__ int psd_jacobi_blocked(T *X, T *V, T *W, int ne, int 
     const T eps = PsdEps<T>::v;
     const T floor_abs = eps * fro / static_cast<T>(ne);
     const T stop2 = (PsdEps<T>::off_tol * fro) * (PsdEps<T>::off_tol * fro);
+    // V update one block round late on the warps without a subproblem when
+    // there are such warps and W holds a second copy of every pair's Q
+    const bool defer = npairs < nw && npairs * (kPsdSlice + kPsdR * kPsdR) + kPsdR * kPsdSld <= ne * ld;
+    const int slice = defer ? kPsdSlice + kPsdR * kPsdR : kPsdSlice;
+    int vpend = -1;            // block round whose V update is pending
     if (psd_off2(X, ne, ld, sm.red) <= stop2) return 0;
     if (tid == 0) {
         sm.flags[0] = 0;
@@ -630,7 +681,7 @@ __device__ __forceinline__ int psd_jacobi_blocked(T *X, T *V, T *W, int ne, int 
             for (int k = warp; k < npairs; k += nw) {
                 int bI, bJ;
                 psd_pair(br, k, nb, bI, bJ);
-                T *S = W + (size_t)k * kPsdSlice, *Qi = S + kPsdOffQi, *Q = S + kPsdOffQ;
+                T *S = W + (size_t)k * slice, *Qi = S + kPsdOffQi, *Q = S + kPsdOffQ;
                 PsdRot<T> *rot = reinterpret_cast<PsdRot<T> *>(S + kPsdOffRot);
                 for (int e = lane; e < kPsdR * kPsdR; e += 32) {
                     const int a = e >> 4, b = e & (kPsdR - 1);
@@ -645,6 +696,9 @@ __device__ __forceinline__ int psd_jacobi_blocked(T *X, T *V, T *W, int ne, int 
                 if (psd_sub_sweep(S, Qi, rot, lane, br == 0, eps, floor_abs) && lane == 0) *fl = 1;
                 for (int e = lane; e < kPsdR * kPsdR; e += 32) Q[e] = Qi[(e >> 4) * kPsdSld + (e & (kPsdR - 1))];
             }
+            if (vpend >= 0 && warp >= npairs)
+                psd_v_panel<T, CPT>(V, W, slice, kPsdSlice, ld, nb, npairs, vpend, nrows_v, tid - npairs * 32,
+                                    nt - npairs * 32);
             if (tid == 0) sm.flags[(round + 1) & 1] = 0;
             __syncthreads();
             const bool rot = *fl != 0;
@@ -655,9 +709,9 @@ __device__ __forceinline__ int psd_jacobi_blocked(T *X, T *V, T *W, int ne, int 
                 // Q_k^T X[R_k, R_l] Q_l (one warp: T = X[R_k, R_l] Q_l into
                 // the warp's scratch, then Q_k^T T), written with its mirror
                 const int nblk = npairs * (npairs - 1) / 2;
-                T *scratch = W + (size_t)npairs * kPsdSlice;
+                T *scratch = W + (size_t)npairs * slice;
                 // warps with a scratch tile in W (at least 3: ne >= 64)
-                const int nsw = min(min(nw, nblk), (ne * ld - npairs * kPsdSlice) / (kPsdR * kPsdSld));
+                const int nsw = min(min(nw, nblk), (ne * ld - npairs * slice) / (kPsdR * kPsdSld));
                 for (int t = warp; warp < nsw && t < nblk; t += nsw) {
                     int k = 1;
                     while ((k + 1) * k / 2 <= t) ++k;       // t = k (k - 1) / 2 + l, l < k
@@ -665,8 +719,8 @@ __device__ __forceinline__ int psd_jacobi_blocked(T *X, T *V, T *W, int ne, int 
                     int kI, kJ, lI, lJ;
                     psd_pair(br, k, nb, kI, kJ);
                     psd_pair(br, l, nb, lI, lJ);
-                    const T *Qk = W + (size_t)k * kPsdSlice + kPsdOffQ;
-                    const T *Ql = W + (size_t)l * kPsdSlice + kPsdOffQ;
+                    const T *Qk = W + (size_t)k * slice + kPsdOffQ;
+                    const T *Ql = W + (size_t)l * slice + kPsdOffQ;
                     T *Tw = scratch + (size_t)warp * kPsdR * kPsdSld;
                     const int i = lane & (kPsdR - 1), c0 = (lane >> 4) * kPsdB;
                     // T[i][c] = sum_b X[R_k(i), R_l(b)] Q_l[b][c], c in [c0, c0 + 8)
@@ -726,51 +780,27 @@ __device__ __forceinline__ int psd_jacobi_blocked(T *X, T *V, T *W, int ne, int 
                     int bI, bJ;
                     psd_pair(br, k, nb, bI, bJ);
                     X[(size_t)psd_sub_index(a, bI, bJ) * ld + psd_sub_index(b, bI, bJ)] =
-                        W[(size_t)k * kPsdSlice + a * kPsdSld + b];
+                        W[(size_t)k * slice + a * kPsdSld + b];
                 }
-                // V[row, R] <- sum_a V[row, R_a] Q[a][r]
-                const int gv = (nrows_v + CPT - 1) / CPT;
-                for (int u = tid; u < npairs * gv; u += nt) {
-                    const int k = u / gv, g0 = u - k * gv;
-                    int bI, bJ;
-                    psd_pair(br, k, nb, bI, bJ);
-                    const T *Q = W + (size_t)k * kPsdSlice + kPsdOffQ;
-                    T acc[kPsdR][CPT];
-#pragma unroll
-                    for (int r = 0; r < kPsdR; ++r)
-#pragma unroll
-                        for (int m = 0; m < CPT; ++m) acc[r][m] = T(0);
-#pragma unroll 4
-                    for (int a = 0; a < kPsdR; ++a) {
-                        const int ga = psd_sub_index(a, bI, bJ);
-                        T y[CPT];
-#pragma unroll
-                        for (int m = 0; m < CPT; ++m) {
-                            const int row = g0 + m * gv;
-                            y[m] = row < nrows_v ? V[(size_t)row * ld + ga] : T(0);
-                        }
-#pragma unroll
-                        for (int r4 = 0; r4 < kPsdR; r4 += 4) {
-                            T q[4];
-                            psd_load4(Q + a * kPsdR + r4, q);
-#pragma unroll
-                            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                                for (int m = 0; m < CPT; ++m) acc[r4 + r][m] = fma(y[m], q[r], acc[r4 + r][m]);
-                        }
+                if (defer) {
+                    // keep this round's Q for the V update, which the warps
+                    // without a subproblem run during the next block round
+                    for (int e = tid; e < npairs * kPsdR * kPsdR; e += nt) {
+                        const int k = e >> 8;
+                        W[(size_t)k * slice + kPsdSlice + (e & 255)] = W[(size_t)k * slice + kPsdOffQ + (e & 255)];
                     }
-#pragma unroll
-                    for (int m = 0; m < CPT; ++m) {
-                        const int row = g0 + m * gv;
-                        if (row >= nrows_v) continue;
-#pragma unroll
-                        for (int r = 0; r < kPsdR; ++r) V[(size_t)row * ld + psd_sub_index(r, bI, bJ)] = acc[r][m];
-                    }
+                } else {
+                    psd_v_panel<T, CPT>(V, W, slice, kPsdOffQ, ld, nb, npairs, br, nrows_v, tid, nt);
                 }
             }
+            vpend = defer && rot ? br : -1;
             __syncthreads();
         }
         if (!any || psd_off2(X, ne, ld, sm.red) <= stop2) break;
+    }
+    if (vpend >= 0) {
+        psd_v_panel<T, CPT>(V, W, slice, kPsdSlice, ld, nb, npairs, vpend, nrows_v, tid, nt);
+        __syncthreads();
     }
     return sweeps;
 }
