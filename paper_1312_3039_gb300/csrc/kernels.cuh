@@ -558,7 +558,8 @@ struct PsdEngineIO {
     }
 };
 
-// kSm: X, V, W in shared memory (else X, W in P.work and V in place in P.V)
+// kSm: X, V, W in shared memory (else X, W in P.work and V in place in P.V,
+// with the blocked sweeps' subproblems in shared memory when they fit)
 template <typename T, bool kSm>
 __global__ void __launch_bounds__(kPsdThreads, 1) psd_project_kernel(ProjArgs<T> a, PsdDev<T> P, PsdStats st) {
     extern __shared__ __align__(16) unsigned char psd_smem[];
@@ -567,7 +568,7 @@ __global__ void __launch_bounds__(kPsdThreads, 1) psd_project_kernel(ProjArgs<T>
     const int ne = psd_ne(n), ld = ne + 1;
     const PsdSmall<T> sm = psd_small_tables<T>(psd_smem, P.ne_max);
     T *keep = P.V + P.voff[b];
-    T *X, *V, *W;
+    T *X, *V, *W, *Wsub = nullptr;
     if constexpr (kSm) {
         X = reinterpret_cast<T *>(psd_smem + P.small_bytes);
         V = X + ne * ld;
@@ -576,9 +577,11 @@ __global__ void __launch_bounds__(kPsdThreads, 1) psd_project_kernel(ProjArgs<T>
         X = P.work + (size_t)b * 2 * P.work_stride;
         W = X + P.work_stride;
         V = keep;
+        // the blocked sweeps' subproblems on chip when they fit
+        if (psd_sub_on_chip<T>(P.ne_max)) Wsub = reinterpret_cast<T *>(psd_smem + P.small_bytes);
     }
     PsdEngineIO<T> io{&a, static_cast<T>(a.S->gamma), static_cast<T>(a.S->relax), a.n + P.off[b], T(0)};
-    psd_project_block<T>(io, n, X, V, W, keep, sm, st, P.fp64_cond);
+    psd_project_block<T>(io, n, X, V, W, keep, sm, st, P.fp64_cond, Wsub);
     const double dd = psd_block_sum(static_cast<double>(io.dd), sm.red);
     if (threadIdx.x == 0) P.dd[b] = dd;
 }

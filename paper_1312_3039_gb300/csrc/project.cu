@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kPsdThreads, 1) psd_batch_kernel(const double 
         const int blk = static_cast<int>(pr % nblk);
         const int n = ord[blk];
         const int ne = psd_ne(n), ld = ne + 1;
-        double *X, *V, *W;
+        double *X, *V, *W, *Wsub = nullptr;
         if constexpr (kSm) {
             X = reinterpret_cast<double *>(psd_smem + small_bytes);
             V = X + ne * ld;
@@ -158,9 +158,10 @@ __global__ void __launch_bounds__(kPsdThreads, 1) psd_batch_kernel(const double 
             X = work + (size_t)blockIdx.x * 3 * work_stride;
             V = X + work_stride;
             W = V + work_stride;
+            if (psd_sub_on_chip<double>(ne_max)) Wsub = reinterpret_cast<double *>(psd_smem + small_bytes);
         }
         PsdBatchIO io{v, out, vec * m + off[blk], 0.0};
-        psd_project_block<double>(io, n, X, V, W, nullptr, sm, PsdStats{nullptr, nullptr, nullptr}, 0.0);
+        psd_project_block<double>(io, n, X, V, W, nullptr, sm, PsdStats{nullptr, nullptr, nullptr}, 0.0, Wsub);
         acc += io.dd;
     }
     acc = psd_block_sum(acc, sm.red);

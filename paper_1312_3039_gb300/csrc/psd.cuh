@@ -86,6 +86,19 @@ template <> struct PsdEps<double> {
 // Blocks of order above kPsdBlockedMin run the blocked eigensolver, which
 // needs ne to be a multiple of 16 (pairs of 8-index blocks).
 constexpr int kPsdBlockedMin = 48;
+// ---- blocked Jacobi layout (orders above kPsdBlockedMin)
+constexpr int kPsdB = 8;                    // indices per block
+constexpr int kPsdR = 2 * kPsdB;            // order of a block pair's subproblem
+constexpr int kPsdSld = kPsdR + 1;          // leading dimension of S
+// per block pair in W: S (16 x 17); Q while the rounds run (16 x 17: a
+// column of 16 rows hits 16 banks); Q for the panel products (16 x 16, rows
+// 16-byte aligned for vector loads); the 8 rotation records of a round
+constexpr int kPsdOffQi = kPsdR * kPsdSld;
+constexpr int kPsdOffQ = 2 * kPsdR * kPsdSld;
+constexpr int kPsdOffRot = kPsdOffQ + kPsdR * kPsdR;
+constexpr int kPsdSlice = kPsdOffRot + 4 * kPsdB;
+
+// Padded order: a multiple of 4, or of 16 above kPsdBlockedMin.
 __host__ __device__ inline int psd_ne(int n) {
     return n < 4 ? 4 : n <= kPsdBlockedMin ? (n + 3) & ~3 : (n + 15) & ~15;
 }
@@ -113,14 +126,31 @@ template <typename T>
 __host__ __device__ inline size_t psd_mats_bytes(int ne) {
     return 3 * (size_t)ne * (ne + 1) * sizeof(T);
 }
+// Entries the blocked sweeps of an order-ne block need for its block pairs'
+// subproblems (slices with the second Q) and the warps' scratch tiles.
+__host__ __device__ inline int64_t psd_sub_elems(int ne) {
+    if (ne <= kPsdBlockedMin) return 0;
+    const int64_t npairs = ne / (2 * kPsdB), nblk = npairs * (npairs - 1) / 2;
+    const int64_t tiles = nblk < kPsdThreads / 32 ? nblk : kPsdThreads / 32;
+    return npairs * (kPsdSlice + kPsdR * kPsdR) + tiles * kPsdR * kPsdSld;
+}
+// Whether, with X, V, W in global scratch, the subproblem area of the
+// largest block (ne) fits in shared memory after the small tables.
+template <typename T>
+__host__ __device__ inline bool psd_sub_on_chip(int ne) {
+    return ne > kPsdBlockedMin && psd_small_bytes<T>(ne) + psd_sub_elems(ne) * sizeof(T) <= (size_t)kPsdSmemCap;
+}
+
 // Dynamic shared memory of a launch whose largest block has order n_max;
-// `smem_mats` tells whether the three matrices fit on chip.
+// `smem_mats` tells whether the three matrices fit on chip (else the
+// blocked sweeps' subproblem area does when it fits).
 template <typename T>
 inline size_t psd_smem_bytes(int n_max, bool &smem_mats) {
     const int ne = psd_ne(n_max);
     const size_t small = psd_small_bytes<T>(ne), mats = psd_mats_bytes<T>(ne);
     smem_mats = small + mats <= (size_t)kPsdSmemCap;
-    return smem_mats ? small + mats : small;
+    if (smem_mats) return small + mats;
+    return small + (psd_sub_on_chip<T>(ne) ? psd_sub_elems(ne) * sizeof(T) : 0);
 }
 
 // Pair k of round r of the round-robin tournament on ne players (ne even):
@@ -481,16 +511,6 @@ __device__ __forceinline__ int psd_jacobi(T *X, T *V, int ne, int ld, int nrows_
 }
 
 // ---- blocked Jacobi (orders above kPsdBlockedMin)
-constexpr int kPsdB = 8;                    // indices per block
-constexpr int kPsdR = 2 * kPsdB;            // order of a block pair's subproblem
-constexpr int kPsdSld = kPsdR + 1;          // leading dimension of S
-// per block pair in W: S (16 x 17); Q while the rounds run (16 x 17: a
-// column of 16 rows hits 16 banks); Q for the panel products (16 x 16, rows
-// 16-byte aligned for vector loads); the 8 rotation records of a round
-constexpr int kPsdOffQi = kPsdR * kPsdSld;
-constexpr int kPsdOffQ = 2 * kPsdR * kPsdSld;
-constexpr int kPsdOffRot = kPsdOffQ + kPsdR * kPsdR;
-constexpr int kPsdSlice = kPsdOffRot + 4 * kPsdB;
 
 // Index of the subproblem's local index a (0..15) in the block pair (bI, bJ).
 __device__ __forceinline__ int psd_sub_index(int a, int bI, int bJ) {
@@ -600,11 +620,12 @@ __device__ __forceinline__ bool psd_sub_sweep(T *S, T *Q, PsdRot<T> *rot, int la
 }
 
 // Blocked cyclic Jacobi on the symmetric X (ne x ne, ne a multiple of 16),
-// accumulating V <- V J on its first nrows_v rows; W (ne (ne + 1) entries,
-// 16-byte aligned) holds the block pairs' subproblems (ne / 16 * kPsdSlice
-// entries) and 16 x 17 scratch tiles for the warps that compute the
-// off-diagonal blocks, as many as fit (at least 3 for ne >= 64).  Returns
-// the number of sweeps run.
+// accumulating V <- V J on its first nrows_v rows; W (wcap entries, 16-byte
+// aligned: the block's own W of ne (ne + 1) entries, or a shared-memory area
+// of psd_sub_elems(ne)) holds the block pairs' subproblems (ne / 16 slices)
+// and 16 x 17 scratch tiles for the warps that compute the off-diagonal
+// blocks, as many as fit (at least 3 for ne >= 64).  Returns the number of
+// sweeps run.
 // V[row, R] <- sum_a V[row, R_a] Q[a][r] for every block pair of block
 // round br (Q at offset qoff of each pair's slice of W), over the first
 // nrows_v rows; units (pair, row group) from t0 in steps of tstride.
@@ -652,8 +673,8 @@ __device__ __forceinline__ void psd_v_panel(T *V, const T *W, int slice, int qof
 }
 
 template <typename T>
-__device__ __forceinline__ int psd_jacobi_blocked(T *X, T *V, T *W, int ne, int ld, int nrows_v, const PsdSmall<T> &sm,
-                                                  T fro) {
+__device__ __forceinline__ int psd_jacobi_blocked(T *X, T *V, T *W, int64_t wcap, int ne, int ld, int nrows_v,
+                                                  const PsdSmall<T> &sm, T fro) {
     constexpr int CPT = sizeof(T) == 4 ? 2 : 1;     // columns (rows) per thread in the panel products
     const int nb = ne / kPsdB, npairs = nb / 2;
     const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
@@ -662,7 +683,7 @@ __device__ __forceinline__ int psd_jacobi_blocked(T *X, T *V, T *W, int ne, int 
     const T stop2 = (PsdEps<T>::off_tol * fro) * (PsdEps<T>::off_tol * fro);
     // V update one block round late on the warps without a subproblem when
     // there are such warps and W holds a second copy of every pair's Q
-    const bool defer = npairs < nw && npairs * (kPsdSlice + kPsdR * kPsdR) + kPsdR * kPsdSld <= ne * ld;
+    const bool defer = npairs < nw && npairs * (kPsdSlice + kPsdR * kPsdR) + kPsdR * kPsdSld <= wcap;
     const int slice = defer ? kPsdSlice + kPsdR * kPsdR : kPsdSlice;
     int vpend = -1;            // block round whose V update is pending
     if (psd_off2(X, ne, ld, sm.red) <= stop2) return 0;
@@ -711,7 +732,8 @@ __device__ __forceinline__ int psd_jacobi_blocked(T *X, T *V, T *W, int ne, int 
                 const int nblk = npairs * (npairs - 1) / 2;
                 T *scratch = W + (size_t)npairs * slice;
                 // warps with a scratch tile in W (at least 3: ne >= 64)
-                const int nsw = min(min(nw, nblk), (ne * ld - npairs * slice) / (kPsdR * kPsdSld));
+                const int nsw = static_cast<int>(min(static_cast<int64_t>(min(nw, nblk)),
+                                                     (wcap - npairs * slice) / (kPsdR * kPsdSld)));
                 for (int t = warp; warp < nsw && t < nblk; t += nsw) {
                     int k = 1;
                     while ((k + 1) * k / 2 <= t) ++k;       // t = k (k - 1) / 2 + l, l < k
@@ -815,10 +837,12 @@ struct PsdStats {
 // Project one block.  io.in(s) returns svec entry s of the point to project;
 // io.out(s, p) receives svec entry s of the projection.  X, V, W: matrix
 // storage (shared or global); Vkeep: where the eigenvectors persist between
-// calls (nullptr: cold start, nothing kept; equal to V: kept in place).
+// calls (nullptr: cold start, nothing kept; equal to V: kept in place);
+// Wsub: psd_sub_elems(ne) entries of shared memory for the blocked sweeps'
+// subproblems when X, V, W are in global memory (nullptr: they use W).
 template <typename T, typename IO>
 __device__ __forceinline__ void psd_project_block(IO &io, int n, T *X, T *V, T *W, T *Vkeep, const PsdSmall<T> &sm,
-                                  PsdStats stats, double fp64_cond) {
+                                  PsdStats stats, double fp64_cond, T *Wsub = nullptr) {
     const int ne = psd_ne(n), ld = ne + 1;
     const int64_t len = psd_svec_len(n);
     const T isq2 = T(0.70710678118654752440);
@@ -876,8 +900,10 @@ __device__ __forceinline__ void psd_project_block(IO &io, int n, T *X, T *V, T *
         f2 += x * x;
     }
     f2 = psd_block_sum(f2, sm.red);
-    const int sweeps = ne > kPsdBlockedMin ? psd_jacobi_blocked(X, V, W, ne, ld, n, sm, sqrt(f2))
-                                           : psd_jacobi(X, V, ne, ld, n, sm, sqrt(f2));
+    const int sweeps = ne > kPsdBlockedMin
+                           ? psd_jacobi_blocked(X, V, Wsub ? Wsub : W, Wsub ? psd_sub_elems(ne) : (int64_t)ne * ld, ne,
+                                                ld, n, sm, sqrt(f2))
+                           : psd_jacobi(X, V, ne, ld, n, sm, sqrt(f2));
     // ---- eigenvalues, positive set, conditioning
     for (int j = threadIdx.x; j < ne; j += blockDim.x) sm.lam[j] = X[(size_t)j * ld + j];
     __syncthreads();

@@ -131,7 +131,9 @@ def test_sdp_trajectory_fp64_global_scratch(env):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("order,n_psd", [(10, 4), (60, 2), (100, 1)])   # scalar, blocked, blocked with V a round late
+# scalar Jacobi; blocked; blocked with V a round late; order 150: the
+# matrices in global scratch, the blocked sweeps' subproblems on chip
+@pytest.mark.parametrize("order,n_psd", [(10, 4), (60, 2), (100, 1), (150, 1)])
 def test_sdp_solve(env, precision, order, n_psd):
     torch, scs = env
     P = small_sdp(2, order=order, n_psd=n_psd, n_ill=1, n=120, n_nonneg=40, density=0.1)
