@@ -328,12 +328,29 @@ class Engine : public EngineBase {
         };
         const int occ_a = std::min(occ(spmv_kernel<T, T, T, EpiAInit<T>>), occ(spmv_kernel<T, T, T, EpiACG<T>>));
         const int occ_at = std::min(occ(spmv_kernel<T, T, T, EpiAtInit<T>>), occ(spmv_kernel<T, T, T, EpiAtCG<T>>));
-        SpmvLayout<double> LA = spmv_layout(P.a_rowptr, P.a_col, P.a_val, sms_ * occ_a);
-        SpmvLayout<double> LAt = spmv_layout(P.at_rowptr, P.at_col, P.at_val, sms_ * occ_at);
-        int32_t *a_rowptr = upload(LA.rowptr), *a_col = upload(LA.col), *a_rowid = upload(LA.rowid);
-        double *a_val64 = upload(LA.val);
-        int32_t *at_rowptr = upload(LAt.rowptr), *at_col = upload(LAt.col), *at_rowid = upload(LAt.rowid);
-        double *at_val64 = upload(LAt.val);
+        // the layouts are planned on the host (row order, row starts,
+        // regions, tiles); the plain CSR arrays are uploaded and their rows
+        // gathered into stored order on the device
+        SpmvLayout<double> LA = spmv_layout(P.a_rowptr, P.a_col, P.a_val, sms_ * occ_a, 0, false);
+        SpmvLayout<double> LAt = spmv_layout(P.at_rowptr, P.at_col, P.at_val, sms_ * occ_at, 0, false);
+        int32_t *a_rowptr = upload(LA.rowptr), *a_rowid = upload(LA.rowid);
+        int32_t *at_rowptr = upload(LAt.rowptr), *at_rowid = upload(LAt.rowid);
+        int32_t *a_col = dalloc<int32_t>(nnz_), *at_col = dalloc<int32_t>(nnz_);
+        double *a_val64 = dalloc<double>(nnz_), *at_val64 = dalloc<double>(nnz_);
+        auto gather = [&](const std::vector<int32_t> &rp, const std::vector<int32_t> &cl, const std::vector<double> &vl,
+                          const int32_t *rowid, const int32_t *dst_rp, int rows, int32_t *dst_col, double *dst_val) {
+            int32_t *srp = upload(rp), *scl = upload(cl);
+            double *svl = upload(vl);
+            gather_rows_kernel<<<grid_for((int64_t)rows * 32), kBlock, 0, stream_>>>(rows, rowid, srp, scl, svl, dst_rp,
+                                                                                   dst_col, dst_val);
+            SCS_CUDA(cudaGetLastError());
+            SCS_CUDA(cudaStreamSynchronize(stream_));
+            dfree(srp);
+            dfree(scl);
+            dfree(svl);
+        };
+        gather(P.a_rowptr, P.a_col, P.a_val, a_rowid, a_rowptr, m_, a_col, a_val64);
+        gather(P.at_rowptr, P.at_col, P.at_val, at_rowid, at_rowptr, n_, at_col, at_val64);
         const int32_t *a_tiles = upload(LA.tile_row), *at_tiles = upload(LAt.tile_row);
         S_ = dalloc<Scalars>(1);
         SCS_CUDA(cudaMemsetAsync(S_, 0, sizeof(Scalars), stream_));

@@ -734,6 +734,24 @@ __global__ void __launch_bounds__(kBlock) output_kernel(int n, int m, int status
 // ---------------------------------------------------------------------------
 // setup kernels (FP64): equilibration (Sec. 5) and conversions
 // ---------------------------------------------------------------------------
+// Rows of a CSR matrix gathered into its stored layout: stored row w is
+// source row rowid[w] (one warp per row, lanes stride the row).
+static __global__ void gather_rows_kernel(int rows, const int32_t *__restrict__ rowid,
+                                          const int32_t *__restrict__ src_rp, const int32_t *__restrict__ src_col,
+                                          const double *__restrict__ src_val, const int32_t *__restrict__ dst_rp,
+                                          int32_t *__restrict__ dst_col, double *__restrict__ dst_val) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t w = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; w < rows; w += warps) {
+        const int r = rowid[w];
+        const int s0 = src_rp[r], len = src_rp[r + 1] - s0, d0 = dst_rp[w];
+        for (int k = lane; k < len; k += 32) {
+            dst_col[d0 + k] = src_col[s0 + k];
+            dst_val[d0 + k] = src_val[s0 + k];
+        }
+    }
+}
+
 static __global__ void row_sumsq_kernel(const int32_t *__restrict__ rowptr, const double *__restrict__ val,
                                         const int32_t *__restrict__ rowid, int rows, double *__restrict__ out) {
     const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5, lane = threadIdx.x & 31;

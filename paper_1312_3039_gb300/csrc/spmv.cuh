@@ -299,10 +299,12 @@ struct SpmvLayout {
 };
 
 // threads: host threads for the copy into stored order (0: up to 16, one for
-// matrices under 2^20 nonzeros); the layout is the same for any count
+// matrices under 2^20 nonzeros); the layout is the same for any count.
+// copy = false plans the layout only (rowid, rowptr, regions, tiles) and
+// leaves col and val empty, for a gather of the rows on the device.
 template <typename V>
 inline SpmvLayout<V> spmv_layout(const std::vector<int32_t> &rp, const std::vector<int32_t> &cl,
-                                 const std::vector<V> &vl, int ctas, int threads = 0) {
+                                 const std::vector<V> &vl, int ctas, int threads = 0, bool copy = true) {
     SpmvLayout<V> L;
     const int32_t rows = (int32_t)rp.size() - 1;
     std::vector<int> cls(rows);
@@ -319,44 +321,46 @@ inline SpmvLayout<V> spmv_layout(const std::vector<int32_t> &rp, const std::vect
     for (int32_t r = 0; r < rows; ++r) L.rowid[pos[cls[r]]++] = r;
     const size_t nnz = cl.size();
     L.rowptr.assign(rows + 1, 0);
-    L.col.resize(nnz);
-    L.val.resize(nnz);
     for (int32_t i = 0; i < rows; ++i) {
         const int32_t r = L.rowid[i];
         L.rowptr[i + 1] = L.rowptr[i] + (rp[r + 1] - rp[r]);
     }
-    // the copies (one random jump per row into the source arrays) over ranges
-    // of stored rows with about equal nonzeros
-    auto copy_rows = [&](int32_t a, int32_t b) {
-        for (int32_t i = a; i < b; ++i) {
-            const int32_t r = L.rowid[i];
-            std::copy(cl.begin() + rp[r], cl.begin() + rp[r + 1], L.col.begin() + L.rowptr[i]);
-            std::copy(vl.begin() + rp[r], vl.begin() + rp[r + 1], L.val.begin() + L.rowptr[i]);
+    if (copy) {
+        L.col.resize(nnz);
+        L.val.resize(nnz);
+        // the copies (one random jump per row into the source arrays) over ranges
+        // of stored rows with about equal nonzeros
+        auto copy_rows = [&](int32_t a, int32_t b) {
+            for (int32_t i = a; i < b; ++i) {
+                const int32_t r = L.rowid[i];
+                std::copy(cl.begin() + rp[r], cl.begin() + rp[r + 1], L.col.begin() + L.rowptr[i]);
+                std::copy(vl.begin() + rp[r], vl.begin() + rp[r + 1], L.val.begin() + L.rowptr[i]);
+            }
+        };
+        int T = threads;
+        if (T <= 0) {
+            const unsigned hc = std::thread::hardware_concurrency();
+            T = nnz < (size_t(1) << 20) ? 1 : (int)std::min<unsigned>(16, hc > 0 ? hc : 1);
         }
-    };
-    int T = threads;
-    if (T <= 0) {
-        const unsigned hc = std::thread::hardware_concurrency();
-        T = nnz < (size_t(1) << 20) ? 1 : (int)std::min<unsigned>(16, hc > 0 ? hc : 1);
+        std::vector<int32_t> cut(1, 0);
+        for (int k = 1; k < T; ++k) {
+            const int64_t target = (int64_t)nnz * k / T;
+            const int32_t b = (int32_t)(std::lower_bound(L.rowptr.begin() + cut.back(), L.rowptr.end() - 1, target) -
+                                        L.rowptr.begin());
+            cut.push_back(std::max(cut.back(), std::min(b, rows)));
+        }
+        cut.push_back(rows);
+        std::vector<std::thread> pool;
+        size_t started = 1;                   // range 0 runs on this thread
+        try {
+            for (; started + 1 < cut.size(); ++started) pool.emplace_back(copy_rows, cut[started], cut[started + 1]);
+        } catch (...) {
+            // no more threads: the remaining ranges run here
+        }
+        copy_rows(cut[0], cut[1]);
+        for (size_t k = started; k + 1 < cut.size(); ++k) copy_rows(cut[k], cut[k + 1]);
+        for (auto &t : pool) t.join();
     }
-    std::vector<int32_t> cut(1, 0);
-    for (int k = 1; k < T; ++k) {
-        const int64_t target = (int64_t)nnz * k / T;
-        const int32_t b = (int32_t)(std::lower_bound(L.rowptr.begin() + cut.back(), L.rowptr.end() - 1, target) -
-                                    L.rowptr.begin());
-        cut.push_back(std::max(cut.back(), std::min(b, rows)));
-    }
-    cut.push_back(rows);
-    std::vector<std::thread> pool;
-    size_t started = 1;                   // range 0 runs on this thread
-    try {
-        for (; started + 1 < cut.size(); ++started) pool.emplace_back(copy_rows, cut[started], cut[started + 1]);
-    } catch (...) {
-        // no more threads: the remaining ranges run here
-    }
-    copy_rows(cut[0], cut[1]);
-    for (size_t k = started; k + 1 < cut.size(); ++k) copy_rows(cut[k], cut[k + 1]);
-    for (auto &t : pool) t.join();
     // regions: maximal runs of stored rows with the same lanes per row
     SpmvRegions &R = L.reg;
     R.n = 0;
