@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "engine_base.h"
+#include "host_par.h"
 #include "psd.cuh"
 
 struct scs_work {
@@ -34,42 +35,12 @@ void scs::set_last_error(const std::string &s) { set_error(s); }
 
 namespace {
 
-// Threads for a host pass over `work` stored entries: one below 2^20, else
-// up to 16 (the passes are bound by memory bandwidth well before that).
-int host_threads(int64_t work) {
-    if (work < (int64_t(1) << 20)) return 1;
-    const unsigned hc = std::thread::hardware_concurrency();
-    return static_cast<int>(std::min<unsigned>(16, hc > 0 ? hc : 1));
-}
-
-// f(0) .. f(T - 1): part 0 on this thread, the others on new threads; a part
-// whose thread cannot be started runs here after part 0.  f must not throw.
-template <typename F>
-void run_parts(int T, F f) {
-    std::vector<std::thread> pool;
-    int started = 1;
-    try {
-        for (; started < T; ++started) pool.emplace_back(f, started);
-    } catch (...) {
-        // no more threads: the remaining parts run here
-    }
-    f(0);
-    for (int t = started; t < T; ++t) f(t);
-    for (auto &th : pool) th.join();
-}
+using scs::host_threads;
+using scs::run_parts;
 
 // T + 1 column boundaries splitting the stored entries of a CSC matrix into
 // parts of about equal size.
-std::vector<int32_t> column_cuts(const int64_t *colptr, int32_t n, int T) {
-    std::vector<int32_t> cut(1, 0);
-    for (int t = 1; t < T; ++t) {
-        const int64_t target = colptr[n] * t / T;
-        const int32_t j = static_cast<int32_t>(std::lower_bound(colptr + cut.back(), colptr + n, target) - colptr);
-        cut.push_back(std::max(cut.back(), std::min(j, n)));
-    }
-    cut.push_back(n);
-    return cut;
-}
+std::vector<int32_t> column_cuts(const int64_t *colptr, int32_t n, int T) { return scs::weight_cuts(colptr, n, T); }
 
 // Canonical CSC (row indices strictly increasing in every column) from any
 // CSC: each column sorted by row (stable), entries with equal row summed in

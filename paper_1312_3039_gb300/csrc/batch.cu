@@ -31,6 +31,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -38,6 +39,7 @@
 #include "../../include/scs_gpu.h"
 #include "common.cuh"
 #include "engine_base.h"
+#include "host_par.h"
 
 namespace scs {
 namespace batch {
@@ -930,31 +932,35 @@ class BatchEngine : public BatchBase {
         return d;
     }
 
-    // rows of one stored CSR, longest first (stable), appended to the arrays
-    static void append_rows(const std::vector<int32_t> &rp, const std::vector<int32_t> &col,
-                            const std::vector<double> &val, int rows, std::vector<int32_t> &grp,
-                            std::vector<int32_t> &grid, std::vector<int32_t> &gcol, std::vector<double> &gval,
-                            std::vector<int32_t> &lens) {
+    // rows of one program's stored CSR, longest first (stable), written at
+    // row0 / nz0 of the concatenated arrays (rp[row0] already holds nz0)
+    static void place_rows(const std::vector<int32_t> &rp, const std::vector<int32_t> &col,
+                           const std::vector<double> &val, int rows, int64_t row0, int64_t nz0,
+                           std::vector<int32_t> &grp, std::vector<int32_t> &grid, std::vector<int32_t> &gcol,
+                           std::vector<double> &gval, std::vector<int32_t> &lens) {
         std::vector<int32_t> idx(rows);
         std::iota(idx.begin(), idx.end(), 0);
         std::stable_sort(idx.begin(), idx.end(),
                          [&](int a, int b) { return rp[a + 1] - rp[a] > rp[b + 1] - rp[b]; });
+        int64_t w = nz0;
         for (int r = 0; r < rows; ++r) {
             const int i = idx[r];
-            grid.push_back(i);
-            lens.push_back(rp[i + 1] - rp[i]);
-            for (int k = rp[i]; k < rp[i + 1]; ++k) {
-                gcol.push_back(col[k]);
-                gval.push_back(val[k]);
-            }
-            grp.push_back(static_cast<int32_t>(gcol.size()));
+            const int len = rp[i + 1] - rp[i];
+            grid[row0 + r] = i;
+            lens[row0 + r] = len;
+            std::copy(col.begin() + rp[i], col.begin() + rp[i + 1], gcol.begin() + w);
+            std::copy(val.begin() + rp[i], val.begin() + rp[i + 1], gval.begin() + w);
+            w += len;
+            grp[row0 + r + 1] = static_cast<int32_t>(w);
         }
     }
 
     void layout(const std::vector<HostProblem> &P) {
         count_ = static_cast<int>(P.size());
-        std::vector<int32_t> a_rp{0}, a_rid, a_col, at_rp{0}, at_rid, at_col, soc_off, soc_len;
-        std::vector<double> a_val, at_val, b, c;
+        // offsets of every program in the concatenated arrays (one pass),
+        // then the programs' rows copied on threads
+        std::vector<int64_t> a_r0(count_ + 1, 0), at_r0(count_ + 1, 0), a_nz0(count_ + 1, 0), at_nz0(count_ + 1, 0);
+        std::vector<int64_t> q0(count_ + 1, 0), wpre(count_ + 1, 0);
         int64_t xn = 0, ym = 0, un = 0;
         size_t smem = 0;
         meta_.resize(count_);
@@ -966,30 +972,58 @@ class BatchEngine : public BatchBase {
             M.z = H.z;
             M.l = H.l;
             M.nq = static_cast<int>(H.q.size());
-            M.soc0 = static_cast<int>(soc_off.size());
-            int off = H.z + H.l;
-            for (int32_t qs : H.q) {
-                soc_off.push_back(off);
-                soc_len.push_back(qs);
-                off += qs;
-            }
-            M.a_row0 = static_cast<int>(a_rid.size());
-            append_rows(H.a_rowptr, H.a_col, H.a_val, H.m, a_rp, a_rid, a_col, a_val, a_len_);
-            M.at_row0 = static_cast<int>(at_rid.size());
-            append_rows(H.at_rowptr, H.at_col, H.at_val, H.n, at_rp, at_rid, at_col, at_val, at_len_);
+            M.soc0 = static_cast<int>(q0[i]);
+            M.a_row0 = static_cast<int>(a_r0[i]);
+            M.at_row0 = static_cast<int>(at_r0[i]);
             M.xo = static_cast<int>(xn);
             M.yo = static_cast<int>(ym);
             M.uo = static_cast<int>(un);
+            q0[i + 1] = q0[i] + static_cast<int64_t>(H.q.size());
+            a_r0[i + 1] = a_r0[i] + H.m;
+            at_r0[i + 1] = at_r0[i] + H.n;
+            a_nz0[i + 1] = a_nz0[i] + static_cast<int64_t>(H.a_col.size());
+            at_nz0[i + 1] = at_nz0[i] + static_cast<int64_t>(H.at_col.size());
+            wpre[i + 1] = wpre[i] + static_cast<int64_t>(H.a_col.size()) + H.m + H.n;
             xn += H.n;
             ym += H.m;
             un += H.n + H.m + 1;
-            b.insert(b.end(), H.b.begin(), H.b.end());
-            c.insert(c.end(), H.c.begin(), H.c.end());
             smem = std::max(smem, team_bytes<T>(H.n, H.m));
             work_.push_back(static_cast<double>(H.nnz) + H.n + H.m);
         }
-        if (a_col.size() >= ((size_t)1 << 31) || un >= ((int64_t)1 << 31))
+        if (a_nz0[count_] >= ((int64_t)1 << 31) || un >= ((int64_t)1 << 31) || a_r0[count_] >= ((int64_t)1 << 31))
             throw CudaError("batch too large for 32-bit offsets", SCS_UNSUPPORTED);
+        std::vector<int32_t> a_rp(a_r0[count_] + 1, 0), a_rid(a_r0[count_]), a_col(a_nz0[count_]);
+        std::vector<int32_t> at_rp(at_r0[count_] + 1, 0), at_rid(at_r0[count_]), at_col(at_nz0[count_]);
+        std::vector<int32_t> soc_off(q0[count_]), soc_len(q0[count_]);
+        std::vector<double> a_val(a_nz0[count_]), at_val(at_nz0[count_]), b(ym), c(xn);
+        a_len_.assign(a_r0[count_], 0);
+        at_len_.assign(at_r0[count_], 0);
+        const int nth = std::max(1, std::min(host_threads(wpre[count_]), count_));
+        const std::vector<int32_t> cut = weight_cuts(wpre.data(), count_, nth);
+        std::vector<char> failed(nth, 0);
+        run_parts(nth, [&](int t) {
+            try {
+                for (int i = cut[t]; i < cut[t + 1]; ++i) {
+                    const HostProblem &H = P[i];
+                    const Meta &M = meta_[i];
+                    int off = H.z + H.l;
+                    for (size_t j = 0; j < H.q.size(); ++j) {
+                        soc_off[q0[i] + j] = off;
+                        soc_len[q0[i] + j] = H.q[j];
+                        off += H.q[j];
+                    }
+                    place_rows(H.a_rowptr, H.a_col, H.a_val, H.m, a_r0[i], a_nz0[i], a_rp, a_rid, a_col, a_val, a_len_);
+                    place_rows(H.at_rowptr, H.at_col, H.at_val, H.n, at_r0[i], at_nz0[i], at_rp, at_rid, at_col,
+                               at_val, at_len_);
+                    std::copy(H.b.begin(), H.b.end(), b.begin() + M.yo);
+                    std::copy(H.c.begin(), H.c.end(), c.begin() + M.xo);
+                }
+            } catch (...) {
+                failed[t] = 1;
+            }
+        });
+        for (char f : failed)
+            if (f) throw std::bad_alloc();
         xn_ = xn;
         ym_ = ym;
         un_ = un;
@@ -1238,18 +1272,49 @@ scs_batch *scs_batch_init(int32_t count, const scs_csc *A, const double *b, cons
     std::vector<scs::HostProblem> P;
     if (!e) {
         P.resize(count);
-        int64_t yo = 0, xo = 0;
-        for (int32_t i = 0; i < count && !e; ++i) {
-            if (k[i].ns > 0 || k[i].ep > 0 || k[i].ed > 0 || k[i].np > 0) {
-                scs::set_last_error("batched programs take zero, nonnegative and second-order cones only");
-                e = SCS_UNSUPPORTED;
+        // offsets of each program's b and c; from the first program with a
+        // non-positive size on they mean nothing, so only the programs before
+        // it are validated on threads (parts of about equal nonzeros)
+        std::vector<int64_t> yo(count + 1, 0), xo(count + 1, 0), pre(count + 1, 0);
+        int32_t nvalid = count;
+        for (int32_t i = 0; i < count; ++i) {
+            if (A[i].m <= 0 || A[i].n <= 0) {
+                nvalid = i;
                 break;
             }
-            e = scs::validate_and_build(&A[i], b + yo, c + xo, &k[i], P[i]);
-            if (e) scs::set_last_error("program " + std::to_string(i) + ": " + scs_last_error());
-            yo += A[i].m;
-            xo += A[i].n;
+            yo[i + 1] = yo[i] + A[i].m;
+            xo[i + 1] = xo[i] + A[i].n;
+            pre[i + 1] = pre[i] + 1 + (A[i].colptr ? std::max<int64_t>(0, A[i].colptr[A[i].n]) : 0);
         }
+        std::vector<int32_t> rc(count, 0);
+        std::vector<std::string> msg(count);
+        auto check = [&](int32_t i) {
+            try {
+                if (k[i].ns > 0 || k[i].ep > 0 || k[i].ed > 0 || k[i].np > 0) {
+                    rc[i] = SCS_UNSUPPORTED;
+                    msg[i] = "batched programs take zero, nonnegative and second-order cones only";
+                    return;
+                }
+                rc[i] = scs::validate_and_build(&A[i], b + yo[i], c + xo[i], &k[i], P[i]);
+                if (rc[i]) msg[i] = scs_last_error();
+            } catch (...) {
+                rc[i] = SCS_DEVICE_ERROR;
+            }
+        };
+        const int T = std::max(1, std::min(scs::host_threads(pre[nvalid]), static_cast<int>(nvalid)));
+        const std::vector<int32_t> cut = scs::weight_cuts(pre.data(), nvalid, T);
+        scs::run_parts(T, [&](int t) {
+            for (int32_t i = cut[t]; i < cut[t + 1]; ++i) check(i);
+        });
+        if (nvalid < count) check(nvalid);         // fails: a non-positive size (or its cone)
+        // the error of the first failing program, as a program-by-program
+        // check would report it
+        for (int32_t i = 0; i <= std::min(nvalid, count - 1) && !e; ++i)
+            if (rc[i]) {
+                e = rc[i];
+                scs::set_last_error("program " + std::to_string(i) + ": " +
+                                    (msg[i].empty() ? std::string("host allocation failed") : msg[i]));
+            }
     }
     if (!e) {
         e = batch_guarded([&]() -> int32_t {

@@ -312,6 +312,35 @@ def test_long_rows_and_empty_rows(scs):
     trajectory_parity(scs, P, iters=25)
 
 
+def test_noncanonical_csc_input(scs):
+    """A CSC with rows out of order inside columns and every entry split into
+    two exact halves (v/2 + v/2 = v) builds the same CSR layouts as the
+    canonical CSC: the FP64 iterates agree to rounding."""
+    rng = np.random.default_rng(17)
+    P = synth.random_cone(23, n=40, cone=synth.Cone(z=5, l=30, q=(4, 6), ep=2), density=0.2)
+    A = sp.csc_matrix(P.A)
+    A.sum_duplicates()
+    ptr, idx, val = [0], [], []
+    for j in range(A.shape[1]):
+        rows = np.repeat(A.indices[A.indptr[j]:A.indptr[j + 1]], 2)
+        vals = np.repeat(A.data[A.indptr[j]:A.indptr[j + 1]] * 0.5, 2)
+        order = rng.permutation(len(rows))
+        idx.extend(rows[order])
+        val.extend(vals[order])
+        ptr.append(len(idx))
+    A2 = sp.csc_matrix((np.array(val), np.array(idx, dtype=np.int32), np.array(ptr)), shape=A.shape)
+    assert not A2.has_canonical_format and A2.nnz == 2 * A.nnz
+    kw = dict(TIGHT)
+    with scs.Solver(A, P.b, P.c, P.cone, **kw) as g1, scs.Solver(A2, P.b, P.c, P.cone, **kw) as g2:
+        for _ in range(3):
+            g1.iterate(10)
+            g2.iterate(10)
+            u1, v1 = g1.iterates()
+            u2, v2 = g2.iterates()
+            np.testing.assert_allclose(u2, u1, rtol=0, atol=1e-13 * np.abs(u1).max())
+            np.testing.assert_allclose(v2, v1, rtol=0, atol=1e-13 * max(np.abs(v1).max(), 1e-300))
+
+
 def test_tiny_and_ragged(scs):
     """n = 1 and odd sizes that leave ragged tails in every kernel."""
     for seed, (n, cone) in enumerate([(1, synth.Cone(z=1, l=2)),
