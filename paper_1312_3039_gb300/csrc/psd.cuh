@@ -370,11 +370,14 @@ __device__ __forceinline__ PsdRot<T> psd_rotation(T app, T aqq, T apq, int p, in
 }
 
 // The same rotation with a shorter FP32 dependency chain, for the blocked
-// sweeps' subproblems: t from fast reciprocals (an inexact t still gives an
-// exact rotation, and only perturbs the zeroed a_pq by about eps |a_pq|),
-// c = 1 / sqrt(1 + t^2) from rsqrtf refined by one Newton-Raphson step
-// (y <- y (3 - x y^2) / 2), so c^2 + s^2 = 1 to about an ulp.  FP64 keeps
-// the IEEE path.
+// sweeps' subproblems, whose entries are scaled to magnitude <= 1 (exactly,
+// by a power of two): the skip test compares squares; with d = a_qq - a_pp,
+// t = 2 a_pq sgn(d) / (|d| + sqrt(d^2 + 4 a_pq^2)) is the root of the
+// IEEE formula's t = sgn(tau) / (|tau| + sqrt(1 + tau^2)), from rsqrtf and
+// a fast reciprocal (an inexact t still gives an exact rotation, and only
+// perturbs the zeroed a_pq by about eps |a_pq|); c = 1 / sqrt(1 + t^2) from
+// rsqrtf refined by one Newton-Raphson step (y <- y (3 - x y^2) / 2), so
+// c^2 + s^2 = 1 to about an ulp.  FP64 keeps the IEEE path.
 template <typename T>
 __device__ __forceinline__ PsdRot<T> psd_rotation_fast(T app, T aqq, T apq, int p, int q, T eps, T floor_abs) {
     return psd_rotation(app, aqq, apq, p, q, eps, floor_abs);
@@ -387,17 +390,13 @@ __device__ __forceinline__ PsdRot<float> psd_rotation_fast<float>(float app, flo
     rt.s = 0.f;
     rt.t = 0.f;
     rt.pq = p | (q << 16);
-    // the threshold needs no exact root; x rsqrt(x) is NaN for x = 0, which
-    // fmaxf drops
-    const float x0 = fabsf(app * aqq);
-    const float thr = fmaxf(eps * (x0 * rsqrtf(x0)), floor_abs);
-    if (fabsf(apq) > thr) {
-        const float tau = __fdividef(aqq - app, 2.f * apq);
-        const float at = fabsf(tau);
-        // 1 / (|tau| + sqrt(1 + tau^2)); 1 / (2 |tau|) once tau^2 would overflow
-        float t = at < 1e18f ? __fdividef(1.f, at + (1.f + at * at) * rsqrtf(1.f + at * at)) : __fdividef(0.5f, at);
-        if (tau < 0.f) t = -t;
-        const float x = 1.f + t * t;
+    const float apq2 = apq * apq;
+    if (apq2 > fmaxf(eps * eps * fabsf(app * aqq), floor_abs * floor_abs)) {
+        const float d = aqq - app, ad = fabsf(d);
+        const float r2 = fmaf(4.f * apq, apq, d * d);
+        float t = __fdividef(2.f * apq, ad + r2 * rsqrtf(r2));
+        if (d < 0.f) t = -t;
+        const float x = fmaf(t, t, 1.f);
         float c = rsqrtf(x);
         c = c * (1.5f - 0.5f * x * c * c);
         rt.c = c;
@@ -681,6 +680,10 @@ __device__ __forceinline__ int psd_jacobi_blocked(T *X, T *V, T *W, int64_t wcap
     const T eps = PsdEps<T>::v;
     const T floor_abs = eps * fro / static_cast<T>(ne);
     const T stop2 = (PsdEps<T>::off_tol * fro) * (PsdEps<T>::off_tol * fro);
+    // subproblems scaled by sc = 2^-e, fro in [2^(e-1), 2^e): entries <= 1
+    int fe = 0;
+    frexp(fro, &fe);
+    const T sc = ldexp(T(1), -fe), isc = ldexp(T(1), fe);
     // V update one block round late on the warps without a subproblem when
     // there are such warps and W holds a second copy of every pair's Q
     const bool defer = npairs < nw && npairs * (kPsdSlice + kPsdR * kPsdR) + kPsdR * kPsdSld <= wcap;
@@ -707,14 +710,15 @@ __device__ __forceinline__ int psd_jacobi_blocked(T *X, T *V, T *W, int64_t wcap
                 for (int e = lane; e < kPsdR * kPsdR; e += 32) {
                     const int a = e >> 4, b = e & (kPsdR - 1);
                     const int ga = psd_sub_index(a, bI, bJ), gb = psd_sub_index(b, bI, bJ);
-                    // the lower triangle of X, so S is exactly symmetric
-                    S[a * kPsdSld + b] = ga >= gb ? X[(size_t)ga * ld + gb] : X[(size_t)gb * ld + ga];
+                    // the lower triangle of X, so S is exactly symmetric;
+                    // scaled by a power of two to magnitude <= 1
+                    S[a * kPsdSld + b] = sc * (ga >= gb ? X[(size_t)ga * ld + gb] : X[(size_t)gb * ld + ga]);
                     Qi[a * kPsdSld + b] = a == b ? T(1) : T(0);
                 }
                 __syncwarp();
                 // the first block round of a sweep also covers the pairs
                 // inside each block (every block is in one of its pairs)
-                if (psd_sub_sweep(S, Qi, rot, lane, br == 0, eps, floor_abs) && lane == 0) *fl = 1;
+                if (psd_sub_sweep(S, Qi, rot, lane, br == 0, eps, floor_abs * sc) && lane == 0) *fl = 1;
                 for (int e = lane; e < kPsdR * kPsdR; e += 32) Q[e] = Qi[(e >> 4) * kPsdSld + (e & (kPsdR - 1))];
             }
             if (vpend >= 0 && warp >= npairs)
@@ -802,7 +806,7 @@ __device__ __forceinline__ int psd_jacobi_blocked(T *X, T *V, T *W, int64_t wcap
                     int bI, bJ;
                     psd_pair(br, k, nb, bI, bJ);
                     X[(size_t)psd_sub_index(a, bI, bJ) * ld + psd_sub_index(b, bI, bJ)] =
-                        W[(size_t)k * slice + a * kPsdSld + b];
+                        isc * W[(size_t)k * slice + a * kPsdSld + b];
                 }
                 if (defer) {
                     // keep this round's Q for the V update, which the warps
