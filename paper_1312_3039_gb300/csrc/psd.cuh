@@ -36,16 +36,21 @@
 // work is dense panel products instead of two CTA barriers per round: the
 // ne indices are split into nb = ne / 8 blocks, and a block round pairs
 // the blocks by the round-robin tournament (nb - 1 block rounds a sweep).
-// For each block pair one warp runs one cyclic sweep (15 rounds of 8
-// disjoint rotations, same rotation and skip rules) on the 16 x 16
-// subproblem S = X[R, R] (R: the pair's 16 indices), accumulating its
-// rotations in Q (16 x 16, S <- Q^T S Q).  The pairs of a block round are
-// disjoint, so the round's transformation is J = Q_1 (+) Q_2 (+) ... on
-// disjoint index sets: X <- J^T X J and V <- V J.  X stays symmetric: its
-// diagonal block X[R_k, R_k] is the rotated S of pair k, and the block of
-// two pairs k > l is Q_k^T X[R_k, R_l] Q_l (one warp, written with its
-// mirror); V[:, R] <- V[:, R] Q is a column panel product.  The stopping
-// test is the same.
+// For each block pair one warp rotates, in rounds of 8 disjoint pairs with
+// the same rotation and skip rules, the index pairs of the 16 x 16
+// subproblem S = X[R, R] (R: the pair's 16 indices) that the sweep has not
+// rotated yet: all 120 in the first block round of a sweep (every block is
+// in one of its pairs), the 64 pairs across the two blocks in the others,
+// so a sweep rotates every index pair once.  The rotations accumulate in Q
+// (S <- Q^T S Q); S is scaled exactly by a power of two to entries <= 1.
+// The pairs of a block round are disjoint, so the round's transformation
+// is J = Q_1 (+) Q_2 (+) ... on disjoint index sets: X <- J^T X J and
+// V <- V J.  X stays symmetric: its diagonal block X[R_k, R_k] is the
+// rotated S of pair k, and the block of two pairs k > l is
+// Q_k^T X[R_k, R_l] Q_l (one warp, written with its mirror);
+// V[:, R] <- V[:, R] Q is a column panel product, run one block round late
+// by the warps without a subproblem where W has room for a second Q.  The
+// stopping test is the same.
 //
 // Warm start (the iteration's blocks change little from one ADMM step to
 // the next): V from the previous projection is first made orthogonal again
