@@ -200,72 +200,91 @@ __device__ __forceinline__ T psd_block_sum(T v, double *red) {
 }
 
 // C = A^T B over the ne x ne output, inner index j in [0, kdim); rows of A
-// and B are contiguous (leading dimension ld).  Each thread owns a 4 x 4
-// tile with rows ti + r ne/4 and columns tk + c ne/4, so the lanes of a warp
-// read consecutive words of B and one broadcast word of A.  epi(i, k, acc).
-template <typename Acc, typename T, typename Epi>
-__device__ __forceinline__ void psd_gemm_atb(const T *A, const T *B, int ne, int ld, int kdim, Epi epi) {
-    const int q4 = ne >> 2;
-    const int tiles = q4 * q4;
+// and B are contiguous (leading dimension ld).  Each thread owns a TS x TS
+// tile with rows ti + r ne/TS and columns tk + c ne/TS, so the lanes of a
+// warp read consecutive words of B and broadcast words of A.  The products
+// are bound by shared-memory loads (2 TS FMAs per 2 TS loads), so FP32
+// takes 8 x 8 tiles where ne allows; FP64 keeps 4 x 4 (registers).
+// epi(i, k, acc).
+template <typename Acc, int TS, typename T, typename Epi>
+__device__ __forceinline__ void psd_gemm_atb_tiles(const T *A, const T *B, int ne, int ld, int kdim, Epi epi) {
+    const int q = ne / TS;
+    const int tiles = q * q;
     for (int t = threadIdx.x; t < tiles; t += blockDim.x) {
-        const int ti = t / q4, tk = t - ti * q4;
-        Acc acc[4][4];
+        const int ti = t / q, tk = t - ti * q;
+        Acc acc[TS][TS];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < TS; ++r)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[r][c] = Acc(0);
+            for (int c = 0; c < TS; ++c) acc[r][c] = Acc(0);
         for (int j = 0; j < kdim; ++j) {
             const T *a = A + (size_t)j * ld, *b = B + (size_t)j * ld;
-            Acc ar[4], bc[4];
+            Acc ar[TS], bc[TS];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) ar[r] = static_cast<Acc>(a[ti + r * q4]);
+            for (int r = 0; r < TS; ++r) ar[r] = static_cast<Acc>(a[ti + r * q]);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) bc[c] = static_cast<Acc>(b[tk + c * q4]);
+            for (int c = 0; c < TS; ++c) bc[c] = static_cast<Acc>(b[tk + c * q]);
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+            for (int r = 0; r < TS; ++r)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) acc[r][c] = fma(ar[r], bc[c], acc[r][c]);
+                for (int c = 0; c < TS; ++c) acc[r][c] = fma(ar[r], bc[c], acc[r][c]);
         }
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < TS; ++r)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) epi(ti + r * q4, tk + c * q4, acc[r][c]);
+            for (int c = 0; c < TS; ++c) epi(ti + r * q, tk + c * q, acc[r][c]);
     }
+}
+template <typename Acc, typename T, typename Epi>
+__device__ __forceinline__ void psd_gemm_atb(const T *A, const T *B, int ne, int ld, int kdim, Epi epi) {
+    if (sizeof(Acc) == 4 && ne % 8 == 0)
+        psd_gemm_atb_tiles<Acc, 8>(A, B, ne, ld, kdim, epi);
+    else
+        psd_gemm_atb_tiles<Acc, 4>(A, B, ne, ld, kdim, epi);
 }
 
 // P[i][k] = sum over the positive eigenvalues j of lam_j Vt[j][i] Vt[j][k]
-// (Vt = V^T, rows are eigenvectors), written into P (full square).
-template <typename Acc, typename T>
-__device__ __forceinline__ void psd_reconstruct(const T *Vt, const T *lam, const int *pos, int npos, T *P, int ne,
-                                                int ld) {
-    const int q4 = ne >> 2;
-    const int tiles = q4 * q4;
+// (Vt = V^T, rows are eigenvectors), written into P (full square); tiles as
+// in psd_gemm_atb.
+template <typename Acc, int TS, typename T>
+__device__ __forceinline__ void psd_reconstruct_tiles(const T *Vt, const T *lam, const int *pos, int npos, T *P,
+                                                      int ne, int ld) {
+    const int q = ne / TS;
+    const int tiles = q * q;
     for (int t = threadIdx.x; t < tiles; t += blockDim.x) {
-        const int ti = t / q4, tk = t - ti * q4;
-        Acc acc[4][4];
+        const int ti = t / q, tk = t - ti * q;
+        Acc acc[TS][TS];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < TS; ++r)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[r][c] = Acc(0);
+            for (int c = 0; c < TS; ++c) acc[r][c] = Acc(0);
         for (int jj = 0; jj < npos; ++jj) {
             const int j = pos[jj];
             const T *row = Vt + (size_t)j * ld;
             const Acc w = static_cast<Acc>(lam[j]);
-            Acc ar[4], bc[4];
+            Acc ar[TS], bc[TS];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) ar[r] = w * static_cast<Acc>(row[ti + r * q4]);
+            for (int r = 0; r < TS; ++r) ar[r] = w * static_cast<Acc>(row[ti + r * q]);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) bc[c] = static_cast<Acc>(row[tk + c * q4]);
+            for (int c = 0; c < TS; ++c) bc[c] = static_cast<Acc>(row[tk + c * q]);
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+            for (int r = 0; r < TS; ++r)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) acc[r][c] = fma(ar[r], bc[c], acc[r][c]);
+                for (int c = 0; c < TS; ++c) acc[r][c] = fma(ar[r], bc[c], acc[r][c]);
         }
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < TS; ++r)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) P[(size_t)(ti + r * q4) * ld + tk + c * q4] = static_cast<T>(acc[r][c]);
+            for (int c = 0; c < TS; ++c) P[(size_t)(ti + r * q) * ld + tk + c * q] = static_cast<T>(acc[r][c]);
     }
+}
+template <typename Acc, typename T>
+__device__ __forceinline__ void psd_reconstruct(const T *Vt, const T *lam, const int *pos, int npos, T *P, int ne,
+                                                int ld) {
+    if (sizeof(Acc) == 4 && ne % 8 == 0)
+        psd_reconstruct_tiles<Acc, 8>(Vt, lam, pos, npos, P, ne, ld);
+    else
+        psd_reconstruct_tiles<Acc, 4>(Vt, lam, pos, npos, P, ne, ld);
 }
 
 // dst = src^T (ne x ne)
