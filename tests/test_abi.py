@@ -122,6 +122,35 @@ def test_batch_inputs_refused_on_host(L):
     assert ei.value.code == scs.UNSUPPORTED
 
 
+def test_batch_refusal_names_the_first_failing_program(L):
+    """With enough programs that the host checks them on threads (over 2^20
+    stored entries in all), the refusal is still the first failing
+    program's, as a program-by-program check would report it."""
+    from paper_1312_3039_gb300 import scs, synth
+    good = synth.lp(2, n=200, m=400, n_zero=20, density=0.05)
+    assert good.A.nnz * 300 > 1 << 20
+    row_bad = sp.csc_matrix(good.A.copy())
+    row_bad.indices[5] = 10_000
+    nan_bad = sp.csc_matrix(good.A.copy())
+    nan_bad.data[7] = np.nan
+    base = [(good.A, good.b, good.c, good.cone)] * 300
+    progs = list(base)
+    progs[150] = (row_bad, good.b, good.c, good.cone)
+    progs[250] = (nan_bad, good.b, good.c, good.cone)
+    with pytest.raises(scs.ScsError) as ei:
+        scs.Batch(progs)
+    assert ei.value.code == scs.INVALID_INPUT
+    assert "program 150:" in str(ei.value) and "row index" in str(ei.value)
+    expc = synth.random_cone(3, n=12, cone=synth.Cone(l=6, ep=2))
+    progs = list(base)
+    progs[50] = (expc.A, expc.b, expc.c, expc.cone)
+    progs[100] = (nan_bad, good.b, good.c, good.cone)
+    with pytest.raises(scs.ScsError) as ei:
+        scs.Batch(progs)
+    assert ei.value.code == scs.UNSUPPORTED
+    assert "program 50:" in str(ei.value)
+
+
 def test_family_and_network_inputs_refused_on_host(L):
     """scs_family_init refuses cones other than zero / nonnegative / SOC and
     bad data on the host; scs_mlp_create refuses a batch that is not a
