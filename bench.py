@@ -587,16 +587,22 @@ def run_gb300(args):
         t0 = time.perf_counter()
         S2 = scs.Solver(P.A, P.b, P.c, P.cone, max_iters=args.steps, eps_pri=0.0, eps_dual=0.0, eps_gap=0.0,
                         eps_infeas=0.0, eps_unbdd=0.0, **common)
+        t1 = time.perf_counter()
         st, x, y, s, info = S2.solve()
+        t2 = time.perf_counter()
+        S2_setup = info.get("setup_s")
         S2.close()
         torch.cuda.synchronize()
-        el = max_over_ranks(time.perf_counter() - t0)
+        t3 = time.perf_counter()
+        el = max_over_ranks(t3 - t0)
         h2d = 8 * (P.n + 1) + 12 * P.A.nnz + 8 * P.m + 8 * P.n
         d2h = 8 * (P.n + 2 * P.m)
         e2e = {"value": sum_over_ranks(args.steps) / el, "unit": "iter/s",
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "seconds": el, "includes": "scs_init (host CSC->CSR, H2D, equilibration, M^-1 h) + scs_solve "
-                                          f"({args.steps} iterations) + D2H of x, y, s"}
+                                          f"({args.steps} iterations) + D2H of x, y, s",
+               "breakdown_s": {"scs_init": t1 - t0, "scs_solve": t2 - t1, "scs_finish": t3 - t2,
+                               "engine_setup": S2_setup}}
 
     cpu = None
     if cpu_proc is not None:

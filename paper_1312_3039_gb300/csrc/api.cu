@@ -151,7 +151,7 @@ void csc_to_csr(const int64_t *colptr, const int32_t *rowidx, const double *val,
 }  // namespace
 
 static int build_problem(const scs_csc *A, const double *b, const double *c, const scs_cone *k,
-                         scs::HostProblem &P) {
+                         scs::HostProblem &P, bool view_transpose) {
     if (!A || !b || !c || !k) { set_error("null argument"); return SCS_INVALID_INPUT; }
     if (A->m <= 0 || A->n <= 0) { set_error("m and n must be positive"); return SCS_INVALID_INPUT; }
     if (!A->colptr || (!A->rowidx && A->colptr[A->n] > 0) || (!A->val && A->colptr[A->n] > 0)) {
@@ -216,12 +216,19 @@ static int build_problem(const scs_csc *A, const double *b, const double *c, con
     const bool canonical = std::none_of(unsorted.begin(), unsorted.end(), [](char f) { return f != 0; });
     if (canonical) {
         P.at_rowptr.resize(n + 1);
-        P.at_col.resize(nnz_in);
-        P.at_val.resize(nnz_in);
+        if (view_transpose) {
+            P.at_col_view = A->rowidx;
+            P.at_val_view = A->val;
+        } else {
+            P.at_col.resize(nnz_in);
+            P.at_val.resize(nnz_in);
+        }
         run_parts(T, [&](int t) {
             const int64_t a = A->colptr[cut[t]], e = A->colptr[cut[t + 1]];
-            std::copy(A->rowidx + a, A->rowidx + e, P.at_col.begin() + a);
-            std::copy(A->val + a, A->val + e, P.at_val.begin() + a);
+            if (!view_transpose) {
+                std::copy(A->rowidx + a, A->rowidx + e, P.at_col.begin() + a);
+                std::copy(A->val + a, A->val + e, P.at_val.begin() + a);
+            }
             for (int32_t j = cut[t]; j < cut[t + 1]; ++j) P.at_rowptr[j + 1] = static_cast<int32_t>(A->colptr[j + 1]);
         });
         csc_to_csr(A->colptr, A->rowidx, A->val, m, n, T, P.a_rowptr, P.a_col, P.a_val);
@@ -247,9 +254,9 @@ static int build_problem(const scs_csc *A, const double *b, const double *c, con
 }
 
 int scs::validate_and_build(const scs_csc *A, const double *b, const double *c, const scs_cone *k,
-                            scs::HostProblem &P) {
+                            scs::HostProblem &P, bool view_transpose) {
     try {
-        return build_problem(A, b, c, k, P);
+        return build_problem(A, b, c, k, P, view_transpose);
     } catch (const std::bad_alloc &) {
         set_error("host allocation failed");
         return SCS_DEVICE_ERROR;
@@ -329,7 +336,9 @@ scs_work *scs_init(const scs_csc *A, const double *b, const double *c, const scs
         int r = validate_settings(s);
         if (r) return r;
         scs::HostProblem P;
-        r = validate_and_build(A, b, c, k, P);
+        // the engine uploads CSR(A^T) before scs_init returns: a canonical
+        // CSC's own arrays serve as its columns and values
+        r = validate_and_build(A, b, c, k, P, true);
         if (r) return r;
         w = new scs_work();
         w->device = s.device;

@@ -333,14 +333,21 @@ class Engine : public EngineBase {
         // gathered into stored order on the device
         SpmvLayout<double> LA = spmv_layout(P.a_rowptr, P.a_col, P.a_val, sms_ * occ_a, 0, false);
         SpmvLayout<double> LAt = spmv_layout(P.at_rowptr, P.at_col, P.at_val, sms_ * occ_at, 0, false);
+        // CSR(A^T): the host copies, or views of the caller's canonical CSC
+        const int32_t *at_cl = P.at_col_view ? P.at_col_view : P.at_col.data();
+        const double *at_vl = P.at_val_view ? P.at_val_view : P.at_val.data();
         int32_t *a_rowptr = upload(LA.rowptr), *a_rowid = upload(LA.rowid);
         int32_t *at_rowptr = upload(LAt.rowptr), *at_rowid = upload(LAt.rowid);
         int32_t *a_col = dalloc<int32_t>(nnz_), *at_col = dalloc<int32_t>(nnz_);
         double *a_val64 = dalloc<double>(nnz_), *at_val64 = dalloc<double>(nnz_);
-        auto gather = [&](const std::vector<int32_t> &rp, const std::vector<int32_t> &cl, const std::vector<double> &vl,
-                          const int32_t *rowid, const int32_t *dst_rp, int rows, int32_t *dst_col, double *dst_val) {
-            int32_t *srp = upload(rp), *scl = upload(cl);
-            double *svl = upload(vl);
+        auto gather = [&](const std::vector<int32_t> &rp, const int32_t *cl, const double *vl, const int32_t *rowid,
+                          const int32_t *dst_rp, int rows, int32_t *dst_col, double *dst_val) {
+            int32_t *srp = upload(rp), *scl = dalloc<int32_t>(nnz_);
+            double *svl = dalloc<double>(nnz_);
+            if (nnz_ > 0) {
+                SCS_CUDA(cudaMemcpyAsync(scl, cl, sizeof(int32_t) * nnz_, cudaMemcpyHostToDevice, stream_));
+                SCS_CUDA(cudaMemcpyAsync(svl, vl, sizeof(double) * nnz_, cudaMemcpyHostToDevice, stream_));
+            }
             gather_rows_kernel<<<grid_for((int64_t)rows * 32), kBlock, 0, stream_>>>(rows, rowid, srp, scl, svl, dst_rp,
                                                                                    dst_col, dst_val);
             SCS_CUDA(cudaGetLastError());
@@ -349,8 +356,8 @@ class Engine : public EngineBase {
             dfree(scl);
             dfree(svl);
         };
-        gather(P.a_rowptr, P.a_col, P.a_val, a_rowid, a_rowptr, m_, a_col, a_val64);
-        gather(P.at_rowptr, P.at_col, P.at_val, at_rowid, at_rowptr, n_, at_col, at_val64);
+        gather(P.a_rowptr, P.a_col.data(), P.a_val.data(), a_rowid, a_rowptr, m_, a_col, a_val64);
+        gather(P.at_rowptr, at_cl, at_vl, at_rowid, at_rowptr, n_, at_col, at_val64);
         const int32_t *a_tiles = upload(LA.tile_row), *at_tiles = upload(LAt.tile_row);
         S_ = dalloc<Scalars>(1);
         SCS_CUDA(cudaMemsetAsync(S_, 0, sizeof(Scalars), stream_));

@@ -29,6 +29,10 @@ struct HostProblem {
     int64_t nnz = 0;
     std::vector<int32_t> a_rowptr, a_col, at_rowptr, at_col;
     std::vector<double> a_val, at_val, b, c;
+    // CSR(A^T) columns and values as views of the caller's canonical CSC
+    // arrays (at_col, at_val left empty); valid while the building call runs
+    const int32_t *at_col_view = nullptr;
+    const double *at_val_view = nullptr;
     int32_t z = 0, l = 0, ep = 0, ed = 0;
     std::vector<double> pw;     // power-cone parameters (negative: dual power cone)
     std::vector<int32_t> q, s;
@@ -36,7 +40,10 @@ struct HostProblem {
 
 // Validate A (CSC), b, c and the cone and build the host CSR layouts
 // (api.cu); returns 0 or an SCS_* status after setting the error text.
-int validate_and_build(const scs_csc *A, const double *b, const double *c, const scs_cone *k, HostProblem &P);
+// view_transpose: when the CSC is canonical, leave CSR(A^T)'s columns and
+// values as views of its arrays instead of copies.
+int validate_and_build(const scs_csc *A, const double *b, const double *c, const scs_cone *k, HostProblem &P,
+                       bool view_transpose = false);
 // Error text returned by scs_last_error() on this thread.
 void set_last_error(const std::string &s);
 
