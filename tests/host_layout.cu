@@ -44,3 +44,21 @@ extern "C" int host_spmv_tiles(int rows, const int32_t *rowptr, const int32_t *c
     if (n) std::memcpy(out, L.tile_row.data(), sizeof(int32_t) * n);
     return n;
 }
+
+// 1 when the plan-only layout (copy = false, empty column and value arrays,
+// as the solver builds it before gathering rows on the device) has the same
+// row order, row starts, regions and tiles as the copying layout
+extern "C" int host_spmv_plan_matches(int rows, const int32_t *rowptr, const int32_t *col, int ctas) {
+    std::vector<int32_t> rp(rowptr, rowptr + rows + 1), cl(col, col + rowptr[rows]), none;
+    std::vector<double> vl(cl.size(), 1.0), nonev;
+    scs::SpmvLayout<double> A = scs::spmv_layout(rp, cl, vl, ctas);
+    scs::SpmvLayout<double> B = scs::spmv_layout(rp, none, nonev, ctas, 0, false);
+    if (!B.col.empty() || !B.val.empty()) return 0;
+    if (A.rowid != B.rowid || A.rowptr != B.rowptr || A.tile_row != B.tile_row) return 0;
+    if (A.reg.n != B.reg.n) return 0;
+    for (int k = 0; k < A.reg.n; ++k)
+        if (A.reg.row0[k] != B.reg.row0[k] || A.reg.row1[k] != B.reg.row1[k] || A.reg.lanes[k] != B.reg.lanes[k] ||
+            A.reg.cta0[k + 1] != B.reg.cta0[k + 1])
+            return 0;
+    return 1;
+}

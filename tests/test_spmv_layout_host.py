@@ -144,3 +144,19 @@ def test_threaded_copy_is_identical(lib):
     rows_of_src = np.repeat(np.arange(rows), np.diff(A.indptr))
     rows_of_stored = np.repeat(o_id, np.diff(o_rp))
     np.testing.assert_array_equal(rows_of_src[src], rows_of_stored)
+
+
+def test_plan_only_layout_matches_the_copying_one(lib):
+    """The solver plans its layouts without copying (copy = false) and
+    gathers the rows on the device: the plan (row order, row starts,
+    regions and their CTAs, tiles) is the copying layout's."""
+    rng = np.random.default_rng(9)
+    P = synth.mixed_small(0, scale=200)
+    cases = [sp.csr_matrix(synth.powerlaw_rows(rng, 30000, 9000, 300000, max_len=5000)), sp.csr_matrix(P.A),
+             sp.csr_matrix(P.A.T), sp.csr_matrix(np.array([[1.0, 0, 2], [0, 0, 0], [3, 4, 5]]))]
+    for A in cases:
+        rp = np.ascontiguousarray(A.indptr, dtype=np.int32)
+        cl = np.ascontiguousarray(A.indices, dtype=np.int32)
+        for ctas in (1, 7, 1216):
+            assert lib.host_spmv_plan_matches(A.shape[0], rp.ctypes.data_as(ctypes.c_void_p),
+                                              cl.ctypes.data_as(ctypes.c_void_p), ctas) == 1
