@@ -807,7 +807,9 @@ class FamilyEngine : public FamilyBase {
         graph_cols_ = A;
     }
     void build_graph() {
-        // cuBLAS sets up its workspace on a first call outside the capture
+        // one iteration outside the capture first: the products' one-time
+        // per-device set-up (the tensor-core kernel's shared-memory
+        // attribute, the SM count) runs there
         launch_iteration();
         SCS_CUDA(cudaStreamSynchronize(stream_));
         cold();
